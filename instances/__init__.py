@@ -1,0 +1,13 @@
+"""Seeded synthetic choice-based LP instances (inputs only).
+
+This package draws the random data of a choice-based LP under the generalized
+attraction model: prices, capacities, the product-resource incidence and the
+per-segment consideration sets with their attractions. It holds none of the
+solution method's arithmetic and is shared by the CPU oracle, the tests and the
+benchmark. Nothing here imports the oracle or the CUDA library.
+"""
+from .gam import (Instance, make_instance, tiny_mnl, mid_gam, huge_gam,
+                  paper_shaped, full_offer_demand, seeded_duals)
+
+__all__ = ["Instance", "make_instance", "tiny_mnl", "mid_gam", "huge_gam",
+           "paper_shaped", "full_offer_demand", "seeded_duals"]
