@@ -1,0 +1,355 @@
+#!/usr/bin/env python3
+"""SPFOM iteration benchmark on the mid GAM instance (1e4 products, 2000
+resources, 1e6 segments with 5-15 products each; seeded synthetic data).
+
+A step is ``--iters-per-step`` SPFOM iterations (default 64 = one KKT
+evaluation period), so every step covers margins, segment solves, the sales
+aggregate, the dual step, averaging and one KKT / restart evaluation. The JSON
+line reports iterations per second of the whole job, the segment kernel's HBM
+roofline fraction, the end-to-end rate through host buffers, the time to KKT
+<= 1e-4, and the FP64 oracle timed on the host as the CPU baseline.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Under torchrun (N > 1) every rank solves its own seeded instance (replicas;
+the iteration has no cross-GPU exchange here), timing is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-4 KKT (s) & SPFOM iters/s: GPU plain vs FP32/batched/learned"
+KERNEL_SRC = os.path.join(ROOT, "paper_2602_22421_gb300", "csrc", "spfom_kernels.cu")
+TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
+BYTES_PER_NNZ = 20      # seg_prod int32 + v f64 + (v - w) f64
+BYTES_PER_SEGMENT = 24  # seg_ptr int64 + lambda f64 + (v0 + sum w) f64
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--iters-per-step", type=int, default=64)
+    ap.add_argument("--segments", type=int, default=1_000_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(args, seed):
+    from instances import mid_gam
+    return mid_gam(seed, L=args.segments)
+
+
+def config_of(inst, args, extra=None):
+    import numpy as np
+    K = np.diff(inst.seg_ptr)
+    cfg = {"workload": f"mid GAM instance: n={inst.n} products, m={inst.m} resources (1-3 per product), "
+                       f"L={inst.L} segments, |C_l|~U{{{int(K.min())}..{int(K.max())}}}",
+           "n": inst.n, "m": inst.m, "L": inst.L, "nnz": inst.nnz,
+           "iterations_per_step": args.iters_per_step, "eval_every": 64,
+           "input_bytes": inst.nbytes(),
+           "l2": f"inputs {inst.nbytes() / 1e9:.2f} GB > L2 (129 MB); L2 not flushed between iterations",
+           "parallelism": "replicas" if args.gpus > 1 else "single GPU"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-i", str(index), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_traffic(nnz):
+    """DRAM bytes per segment-kernel launch from the committed ncu summary, if
+    it was taken on the current kernel source; scaled by nonzeros."""
+    if not os.path.exists(TRAFFIC):
+        return None, None
+    with open(TRAFFIC) as f:
+        d = json.load(f)
+    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    if d.get("kernel_source_sha256") != sha:
+        return None, "kernel changed since the ncu capture"
+    return d["dram_bytes_per_launch"] * nnz / d["nnz"], d.get("capture")
+
+
+def cpu_baseline(inst, seconds):
+    """The FP64 oracle as it stands, single thread, full iterations of the
+    same instance for about `seconds` (at least 2 iterations)."""
+    from oracle import Oracle, Params
+    run = Oracle(inst).run(Params(kkt_tol=0.0))
+    run.step(1)
+    t0, it = time.perf_counter(), 0
+    while True:
+        run.step(1)
+        it += 1
+        el = time.perf_counter() - t0
+        if (el >= seconds and it >= 2) or el >= 3 * seconds:
+            break
+    return {"value": it / el, "unit": "iters/s", "cores": 1, "kind": "oracle",
+            "sample": f"{it} full iterations of the {inst.L}-segment instance ({el:.1f} s, single thread)"}
+
+
+def pinned_arrays(inst):
+    """Host copies of the instance in page-locked memory (the e2e inputs)."""
+    import numpy as np
+    import torch
+    from paper_2602_22421_gb300 import InstanceArrays
+    arrs = InstanceArrays(inst)
+    keep = {}
+    for k, a in arrs.keep.items():
+        if a is None:
+            keep[k] = None
+            continue
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        keep[k] = t
+    class _I:  # noqa: N801
+        pass
+    fake = _I()
+    for k, t in keep.items():
+        setattr(fake, k, None if t is None else t.numpy())
+    fake.n, fake.m, fake.L = inst.n, inst.m, inst.L
+    pinned = InstanceArrays(fake)
+    pinned.torch_keep = keep
+    return pinned
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0 or ws == 1:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from paper_2602_22421_gb300 import Solver
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def allmax(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    inst = workload(args, seed=1 + rank)
+    ips = args.iters_per_step
+    stream = torch.cuda.Stream()  # a real stream handle: the ctx runs on it, the events bracket it
+    # --- timed throughput: iterations never stop early (kkt_tol = 0) -------
+    s = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0)
+    s.step(args.warmup * ips)
+    barrier()
+    clk = Clocks(local) if rank == 0 else None
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    st = s.step(args.steps * ips)
+    e1.record(stream)
+    barrier()
+    clocks = clk.stop() if clk else None
+    ms = allmax(e0.elapsed_time(e1))
+    total_iters = ws * args.steps * ips
+    value = total_iters / (ms * 1e-3)
+    launches = st["kernel_launches"]
+    s.close()
+    # --- roofline of the segment kernel (event pair around every launch) ----
+    roof = None
+    if rank == 0:
+        sp = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, profile=1)
+        sp.step(2 * ips)
+        pst = sp.step(min(args.steps, 10) * ips)
+        sp.close()
+        per_launch = pst["seg_kernel_seconds"] / max(1, pst["seg_kernel_launches"])
+        alg = BYTES_PER_NNZ * inst.nnz + BYTES_PER_SEGMENT * inst.L
+        peak, src = measured_peaks()
+        achieved = alg / per_launch / 1e9
+        traffic, cap = kernel_traffic(inst.nnz)
+        roof = {"bound": "hbm", "kernel": "k_segments (iterate)", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch * 1e3,
+                "peak_source": f"{src} hbm_gbs", "traffic_note": cap}
+    # --- time to KKT <= 1e-4 -------------------------------------------------
+    ttk = None
+    if not args.no_solve:
+        sv = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=1e-4, max_iters=20000)
+        barrier()
+        w0 = time.perf_counter()
+        sst = sv.solve()
+        wall = time.perf_counter() - w0
+        ttk = {"seconds_device": sst["seconds"], "seconds_wall": wall, "iterations": sst["iters"],
+               "converged": bool(sst["converged"]), "kkt": sst["kkt"], "dual_obj": sst["dual_avg"],
+               "primal_obj": sst["primal_avg"], "restarts": sst["restarts"]}
+        sv.close()
+    # --- end to end through host buffers -------------------------------------
+    e2e = None
+    if not args.no_e2e:
+        pinned = pinned_arrays(inst)
+        se = Solver(None, stream=stream.cuda_stream, device=local, kkt_tol=0.0)
+        ysink = np.empty(inst.m)
+        se.load(pinned)
+        se.step(ips)
+        se.duals()
+        barrier()
+        k = max(3, min(args.steps, 20))
+        w0 = time.perf_counter()
+        for _ in range(k):
+            se.load(pinned)              # host -> device copy of the instance, validation
+            se.step(ips)
+            ysink[:] = se.duals()        # device -> host read of the result
+        barrier()
+        wall = allmax(time.perf_counter() - w0)
+        se.close()
+        e2e = {"value": ws * k * ips / wall, "unit": "iters/s", "steps": k,
+               "h2d_bytes_per_step": pinned.nbytes(), "d2h_bytes_per_step": inst.m * 8 + 160}
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(inst, args.cpu_seconds)
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+               "config": config_of(inst, args), "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
+               "roofline": roof, "cpu_baseline": cpu, "time_to_kkt_1e-4": ttk}
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def sub_instance(inst, Ls):
+    """The first Ls segments of inst, capacities scaled by their share of the
+    arrival mass (a bounded sample of the same workload)."""
+    from instances import Instance
+    e = int(inst.seg_ptr[Ls])
+    frac = float(inst.lam[:Ls].sum() / inst.lam.sum())
+    return Instance(n=inst.n, m=inst.m, L=Ls, r=inst.r, c=inst.c * frac, a_ptr=inst.a_ptr, a_idx=inst.a_idx,
+                    a_val=inst.a_val, seg_ptr=inst.seg_ptr[:Ls + 1].copy(), seg_prod=inst.seg_prod[:e],
+                    v=inst.v[:e], w=None if inst.w is None else inst.w[:e], lam=inst.lam[:Ls], v0=inst.v0[:Ls],
+                    name=inst.name + f"[:{Ls}]")
+
+
+def run_reference(args):
+    """The FP64 oracle as it stands on the host cores: each step runs
+    iters-per-step oracle iterations on the first 1e4 segments of the same
+    instance; the rate is scaled to full-instance iterations by nonzeros."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import Oracle, Params
+    inst = workload(args, seed=1)
+    Ls = min(inst.L, 10_000)
+    sub = sub_instance(inst, Ls)
+    run = Oracle(sub).run(Params(kkt_tol=0.0))
+    ips = args.iters_per_step
+    for _ in range(args.warmup):
+        run.step(ips)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run.step(ips)
+    el = time.perf_counter() - t0
+    scale = sub.nnz / inst.nnz
+    value = args.steps * ips / el * scale
+    sample = (f"{ips} oracle iterations per step on the first {Ls} of {inst.L} segments ({sub.nnz} of {inst.nnz} "
+              f"nonzeros); rate scaled by the nonzero share to full-instance iterations")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded generator)", "config": config_of(inst, args),
+           "cpu_baseline": {"value": value, "unit": "iters/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * spfom.h -- C ABI of the GB300 SPFOM library (libspfom.so).
+ *
+ * SPFOM solves the sales-based LP (Section 3.2, eqs. sales-based_obj ..
+ * sales-based_4) of a choice-based LP under the generalized attraction model
+ * (Section 3, choice probability pi') with the resource-incidence capacity row
+ * of Extension 2 (Section 5.2, eq. new_NRM_1) by projected dual ascent on the
+ * capacity prices (Section 4.1, Algorithm 2; regularised step eq.
+ * stronglycvxupdate of Section 4.2), every segment's inner problem being
+ * solved exactly at each step (Lemma 1; all segments together, i.e.
+ * Algorithm 3 with one batch holding every segment, or a Bernoulli sample).
+ *
+ * Letters: products j in [n] (price r_j), resources i in [m] (capacity c_i,
+ * dual price y_i), segments l in [L] (arrival rate lambda_l, consideration set
+ * C_l with nominal attractions v_lj and shadow attractions w_lj, no-purchase
+ * attraction v_l0). The paper's customers i, products j, prices eta_j,
+ * attractions w_ij / v_ij map to segments l, products j, resources i, y_i,
+ * v_lj / w_lj here.
+ *
+ * Conventions
+ *  - Every call returns spfom_status; nothing aborts or throws across the ABI.
+ *    spfom_last_error() gives a message for the last failing call on a ctx.
+ *  - Host arrays passed in are read during the call only and copied; the
+ *    library never keeps a caller pointer. Device memory is owned by the ctx
+ *    and freed by spfom_destroy().
+ *  - One ctx per host thread. All device work of a ctx runs on one CUDA
+ *    stream: the caller's (spfom_params.stream) or one the ctx creates.
+ *  - All floating-point inputs and outputs are IEEE binary64.
+ */
+#ifndef SPFOM_H
+#define SPFOM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPFOM_OK = 0,
+  SPFOM_EINVAL = 1,   /* invalid argument or instance (message says which) */
+  SPFOM_ENOMEM = 2,   /* device or host allocation failed */
+  SPFOM_ECUDA = 3,    /* a CUDA runtime call failed (message has the CUDA error) */
+  SPFOM_ESTATE = 4,   /* no instance loaded */
+  SPFOM_ETIMEOUT = 5, /* a bounded device wait gave up */
+  SPFOM_ENOTCONV = 6, /* spfom_solve reached max_iters above kkt_tol */
+  SPFOM_ENOTSUP = 7   /* valid but unsupported here (message says what) */
+} spfom_status;
+
+typedef struct spfom_ctx spfom_ctx;
+
+/* Iteration parameters. spfom_default_params() fills the defaults noted. */
+typedef struct {
+  int32_t precision;         /* 64 (default): the iteration in binary64 */
+  double tau;                /* dual step size; <= 0 (default): tau0 * mean(r) / mean(c) */
+  double tau0;               /* 0.1: the step of the Section 4.5 experiments, rescaled */
+  double mu;                 /* 0: step of Algorithm 2; > 0: eq. stronglycvxupdate */
+  double batch_frac;         /* 1: every segment every iteration; p in (0,1): each
+                                segment is re-solved with probability p (Algorithm 2's
+                                sampling), unsampled ones keep their last response */
+  uint64_t seed;             /* sampling seed (0) */
+  int64_t eval_every;        /* 64: KKT evaluation period; <= 0 never (solver addition) */
+  double restart_beta;       /* 0.2: restart when KKT <= beta * KKT at the last restart */
+  double restart_artificial; /* 0.36: or when the epoch holds this fraction of all iterations */
+  double restart_tau_decay;  /* 1.0: tau <- tau * decay at each restart */
+  double kkt_tol;            /* 1e-4: spfom_solve stops when KKT <= kkt_tol */
+  int64_t max_iters;         /* 100000: spfom_solve iteration cap */
+  int32_t device;            /* CUDA device ordinal (0) */
+  int32_t profile;           /* 0; nonzero: time every segment-kernel launch of spfom_step with
+                                a CUDA event pair (spfom_stats.seg_kernel_seconds) */
+  void* stream;              /* cudaStream_t to run on; NULL (default): the ctx creates one */
+} spfom_params;
+
+/* One choice-based LP. Host pointers (spfom_load_instance copies them).
+ * Layout: CSR over consideration sets. Segment l's products are
+ * seg_prod[seg_ptr[l] .. seg_ptr[l+1]) with attractions v[], w[] at the same
+ * positions; product j uses resources a_idx[a_ptr[j] .. a_ptr[j+1]) with
+ * coefficients a_val[] (NULL: all 1), i.e. the column j of the incidence
+ * matrix of eq. new_NRM_1. */
+typedef struct {
+  int32_t n, m;              /* products, resources */
+  int64_t L;                 /* segments */
+  const double* r;           /* [n] prices, finite */
+  const double* c;           /* [m] capacities, >= 0 and finite */
+  const int32_t* a_ptr;      /* [n+1] nondecreasing, a_ptr[0] = 0 */
+  const int32_t* a_idx;      /* [a_ptr[n]] resource ids in [0, m), distinct per product */
+  const double* a_val;       /* [a_ptr[n]] > 0, or NULL */
+  const int64_t* seg_ptr;    /* [L+1] nondecreasing, seg_ptr[0] = 0 */
+  const int32_t* seg_prod;   /* [seg_ptr[L]] product ids in [0, n), distinct per segment */
+  const double* v;           /* [seg_ptr[L]] nominal attraction v_lj > 0 */
+  const double* w;           /* [seg_ptr[L]] shadow attraction 0 <= w_lj <= v_lj, or NULL (MNL) */
+  const double* lam;         /* [L] arrival rate lambda_l >= 0 */
+  const double* v0;          /* [L] no-purchase attraction v_l0 > 0 */
+} spfom_instance;
+
+/* State after a call. "Averaged" quantities are over the current restart
+ * epoch: ybar averages the duals at which the epoch's responses were taken,
+ * gbar the consumption A x of those responses, Pbar their revenue r^T s. */
+typedef struct {
+  int64_t iters;       /* iterations done since the last load or reset */
+  int64_t restarts;
+  int64_t evals;       /* KKT evaluations done */
+  int64_t epoch_iters; /* iterations in the current restart epoch */
+  int32_t converged;   /* last KKT <= kkt_tol */
+  int32_t pad_;
+  double kkt, pinf, gap;   /* last evaluation: max(pinf, gap), ||(gbar-c)+||/(1+||c||),
+                              |Dual(ybar)-Pbar|/(1+|Dual(ybar)|+|Pbar|) */
+  double dual_avg;     /* Dual(ybar) = c^T ybar + sum_l z_l(ybar) at the last evaluation */
+  double primal_avg;   /* Pbar at the last evaluation */
+  double dual_iter;    /* c^T y + sum_l z_l(y) at the dual point of the last iteration
+                          (full batch only, NaN otherwise) */
+  double z_sum;        /* sum_l z_l at that point (full batch only) */
+  double revenue;      /* r^T s of the last iteration's responses */
+  double sum_revenue;  /* epoch sum of revenue */
+  double tau, mu;      /* current step size and regulariser */
+  double seconds;      /* device time of this call (CUDA events) */
+  double seg_kernel_seconds;   /* summed device time of this call's segment-kernel launches
+                                  of the iterations (params.profile only, else 0) */
+  int64_t seg_kernel_launches; /* those launches */
+  int64_t kernel_launches;     /* all kernels this call launched */
+} spfom_stats;
+
+/* Which vector spfom_vector() returns. */
+typedef enum {
+  SPFOM_VEC_Y = 0,       /* [m] current dual iterate */
+  SPFOM_VEC_YBAR = 1,    /* [m] epoch average of the duals (= y right after a restart) */
+  SPFOM_VEC_SUM_Y = 2,   /* [m] epoch sum of the duals */
+  SPFOM_VEC_SUM_G = 3,   /* [m] epoch sum of the consumption */
+  SPFOM_VEC_G = 4,       /* [m] consumption A s of the last iteration */
+  SPFOM_VEC_S = 5,       /* [n] product sales s = sum_l x_l of the last iteration */
+  SPFOM_VEC_MARGINS = 6  /* [n] margins r - A^T y used by the last iteration */
+} spfom_vector_id;
+
+/* Fill p with the defaults listed in spfom_params. */
+void spfom_default_params(spfom_params* p);
+
+/* Create a ctx on p->device (p NULL: defaults). EINVAL on bad parameters,
+ * ECUDA when the device or stream cannot be set up. *out is NULL on failure. */
+spfom_status spfom_create(const spfom_params* p, spfom_ctx** out);
+
+/* Validate and upload one instance (the data of Sections 3.2 and 5.2), replacing
+ * any previous one, and reset the iteration to y = 0. Rejects with EINVAL:
+ * sizes < 0, non-finite r, c < 0, v <= 0, w < 0 or w > v, v0 <= 0, lam < 0,
+ * a_val <= 0, ids out of range, a product repeated in a segment or a resource
+ * repeated in a product, non-monotone offsets. ENOTSUP: a consideration set
+ * larger than 32 products. The host arrays are not kept. */
+spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* inst);
+
+/* Restart the iteration from y0 (host [m], >= 0; NULL: zeros): clears the
+ * epoch sums, counters, the convergence flag, and restores tau and mu. */
+spfom_status spfom_reset(spfom_ctx* ctx, const double* y0);
+
+/* Run exactly `iters` SPFOM iterations (fewer if KKT falls below kkt_tol at an
+ * evaluation: later iterations are skipped on the device). Each iteration:
+ * margins r - A^T y; every (sampled) segment's exact inner solution (Section
+ * 4.1, Lemma 1); s = sum_l x_l, g = A s (eq. new_NRM_1), r^T s; the projected
+ * step y <- max(0, (1 - tau mu) y - tau (c - g)) (Algorithm 2 / eq.
+ * stronglycvxupdate); epoch sums; every eval_every iterations the KKT residual
+ * of the averages and the restart test. out (may be NULL) gets the state.
+ * Blocks until the work is done. ESTATE without an instance. */
+spfom_status spfom_step(spfom_ctx* ctx, int64_t iters, spfom_stats* out);
+
+/* spfom_reset(y0), then iterate until KKT <= kkt_tol (OK) or max_iters
+ * (ENOTCONV; the state is still filled in). */
+spfom_status spfom_solve(spfom_ctx* ctx, const double* y0, spfom_stats* out);
+
+/* Copy a state vector to host memory out ([m] or [n] doubles, caller-owned). */
+spfom_status spfom_vector(spfom_ctx* ctx, spfom_vector_id which, double* out);
+
+/* Bid prices (Section 5.1, bid-price control): averaged != 0 gives ybar, else y. */
+spfom_status spfom_duals(spfom_ctx* ctx, int32_t averaged, double* y_out);
+
+/* Evaluate the inner problems at a given dual point y (host [m], >= 0) without
+ * touching the iteration state: z_out (host [L] or NULL) gets every z_l(y),
+ * dual_out (or NULL) gets Dual(y) = c^T y + sum_l z_l(y) (eq. entro_obj with the
+ * inner maximisation done). */
+spfom_status spfom_evaluate(spfom_ctx* ctx, const double* y, double* z_out, double* dual_out);
+
+/* Read the current state without running anything. */
+spfom_status spfom_get_stats(spfom_ctx* ctx, spfom_stats* out);
+
+/* Free the ctx and all its device memory (NULL is a no-op). */
+void spfom_destroy(spfom_ctx* ctx);
+
+/* Message of the last failing call on ctx (never NULL). */
+const char* spfom_last_error(const spfom_ctx* ctx);
+
+/* Name of a status code (never NULL). */
+const char* spfom_status_string(spfom_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPFOM_H */

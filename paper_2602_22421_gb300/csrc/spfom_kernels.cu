@@ -1,0 +1,407 @@
+// SPFOM iteration kernels for sm_103a (binary64).
+//
+// One iteration (Algorithm 2 with every segment in the batch, or a Bernoulli
+// sample of them) is three launches on the ctx stream:
+//   k_margins    a1  m_j = r_j - sum_i a_ij y_i, clears the sales vector
+//   k_segments   a2  every segment's exact inner solution (Section 4.1, Lemma 1),
+//                a3  scatter of the sales into s (global atomics), sum_l z_l
+//   k_dual_step  a3  g = A s over the resource-major incidence, r^T s,
+//                a4  y <- max(0, (1 - tau mu) y - tau (c - g)) (eq. stronglycvxupdate),
+//                a5  epoch sums; the last block to finish folds the per-block
+//                    partial sums into the device scalars (no grid barrier)
+// and, every eval_every iterations, three more for the KKT residual and the
+// restart test (a6): margins at the epoch average, an evaluation-only segment
+// pass, and a one-block finish kernel.
+//
+// Inner problem of segment l at margins m (build letters; the paper's
+// customer i / product j / eta_j / w_ij / v_ij are l / j / y / v / w here):
+// vt_j = v_j - w_j and vt_0 = v_0 + sum_{C_l} w_j make the GAM denominator of
+// Section 3 read vt_0 + sum_{k in S} vt_k; the optimum over assortments S is a
+// prefix of the positive-margin products sorted by m v / vt (Lemma 1's greedy
+// order), namely the prefix maximising N/D with N = sum m v, D = vt_0 + sum vt
+// (the first one on ties). Sales are x_j = lambda v_j / D on that prefix.
+//
+// Layout: a sub-warp of W lanes (W a power of two >= the largest consideration
+// set) owns one segment at a time and each lane one product of it, so the
+// segment's CSR slice is read with contiguous loads. Keys are sorted as their
+// int64 bit images (all candidate keys are positive doubles, others are -1),
+// keeping the comparisons off the binary64 pipe, which on GB300 runs at about
+// 1/60 of the binary32 rate.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "spfom_internal.h"
+
+namespace spfom {
+
+namespace {
+
+constexpr int kSegThreads = 256;
+constexpr int kVecThreads = 256;
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long key) {
+  // SplitMix64 output function (Steele, Lea, Flood 2014) on key + golden gamma.
+  unsigned long long z = key + 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Sum of one double per thread over the block, in a fixed order.
+__device__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int k = 0; k < nw; ++k) tot += sh[k];
+  }
+  return tot;  // valid in thread 0
+}
+
+// ------------------------------------------------------------------ prep --
+__global__ void k_prep_items(long long nnz, const double* __restrict__ v, const double* __restrict__ w,
+                             double* __restrict__ vt) {
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p < nnz) vt[p] = w ? __dsub_rn(v[p], w[p]) : v[p];
+}
+
+// vt0 = v0 + sum of the segment's w in CSR order (one thread per segment).
+__global__ void k_prep_segments(long long L, const long long* __restrict__ seg_ptr, const double* __restrict__ v0,
+                                const double* __restrict__ w, double* __restrict__ vt0) {
+  long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l >= L) return;
+  double acc = v0[l];
+  if (w)
+    for (long long p = seg_ptr[l]; p < seg_ptr[l + 1]; ++p) acc = __dadd_rn(acc, w[p]);
+  vt0[l] = acc;
+}
+
+// ------------------------------------------------------------------- a1 --
+// Margins m_j = r_j - sum_i a_ij y_i over the product's resources in stored
+// order. avg != 0 uses the epoch average sum_y / count as y. Clears s when
+// given (full-batch iterations rebuild the sales from zero).
+__global__ void k_margins(Problem P, const double* __restrict__ y, const double* __restrict__ sum_y, int avg,
+                          double* __restrict__ marg, double* __restrict__ s_clear, const DevState* st) {
+  if (st && st->converged) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= P.n) return;
+  const double cnt = avg ? (double)st->count : 1.0;
+  double acc = 0.0;
+  for (int q = P.a_ptr[j]; q < P.a_ptr[j + 1]; ++q) {
+    const int i = P.a_idx[q];
+    const double a = P.a_val ? P.a_val[q] : 1.0;
+    const double yi = avg ? __ddiv_rn(sum_y[i], cnt) : y[i];
+    acc = __dadd_rn(acc, __dmul_rn(a, yi));
+  }
+  marg[j] = __dsub_rn(P.r[j], acc);
+  if (s_clear) s_clear[j] = 0.0;
+}
+
+// ------------------------------------------------------------------- a2 --
+enum SegMode { kIterate = 0, kEvalSum = 1, kEvalSeg = 2 };
+
+template <int W, int MODE, bool SAMPLED>
+__global__ void __launch_bounds__(kSegThreads) k_segments(Problem P, const double* __restrict__ marg,
+                                                          double* __restrict__ s, double* __restrict__ x_cur,
+                                                          double* __restrict__ z_seg, double* __restrict__ zpart,
+                                                          const DevState* st, unsigned long long seed,
+                                                          unsigned long long thr) {
+  if (st && MODE != kEvalSeg && st->converged) return;
+  __shared__ double sh[32];
+  const int lane = threadIdx.x & (W - 1);
+  const int gbase = (threadIdx.x & 31) & ~(W - 1);
+  const unsigned mask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << gbase);
+  const long long groups_per_block = kSegThreads / W;
+  const long long ngroups = (long long)gridDim.x * groups_per_block;
+  const long long t_next = SAMPLED ? st->t + 1 : 0;
+  double zacc = 0.0;
+  for (long long l = blockIdx.x * groups_per_block + threadIdx.x / W; l < P.L; l += ngroups) {
+    if (SAMPLED && splitmix64(seed ^ ((unsigned long long)t_next << 32) ^ (unsigned long long)l) >= thr) continue;
+    const long long b = P.seg_ptr[l];
+    const int K = (int)(P.seg_ptr[l + 1] - b);
+    const double lam = P.lam[l], vt0 = P.vt0[l];
+    int j = 0;
+    double v = 0.0, vt = 0.0, mv = 0.0;
+    long long key = -1;  // int64 image of the sort key; -1 = not a candidate
+    if (lane < K) {
+      j = P.seg_prod[b + lane];
+      v = P.v[b + lane];
+      vt = P.vt[b + lane];
+      const double mj = marg[j];
+      if (mj > 0.0) {
+        mv = __dmul_rn(mj, v);
+        key = __double_as_longlong(vt == 0.0 ? CUDART_INF : __ddiv_rn(mv, vt));
+      }
+    }
+    // Bitonic sort over the group: descending key, ties by lower CSR position.
+    int idx = lane;
+#pragma unroll
+    for (int k = 2; k <= W; k <<= 1) {
+#pragma unroll
+      for (int d = k >> 1; d > 0; d >>= 1) {
+        const long long ok = __shfl_xor_sync(mask, key, d, W);
+        const int oi = __shfl_xor_sync(mask, idx, d, W);
+        const bool other_first = (ok > key) || (ok == key && oi < idx);
+        const bool lower = (lane & d) == 0;
+        const bool desc = (lane & k) == 0;
+        if (desc == lower ? other_first : !other_first) {
+          key = ok;
+          idx = oi;
+        }
+      }
+    }
+    // Lane r now holds the rank-r product (original lane idx).
+    const int nc = __popc(__ballot_sync(mask, key >= 0) & mask);
+    const double mv_r = __shfl_sync(mask, mv, idx, W);
+    const double vt_r = __shfl_sync(mask, vt, idx, W);
+    const double v_r = __shfl_sync(mask, v, idx, W);
+    const int j_r = __shfl_sync(mask, j, idx, W);
+    double N = lane < nc ? mv_r : 0.0, Dp = lane < nc ? vt_r : 0.0;
+#pragma unroll
+    for (int d = 1; d < W; d <<= 1) {
+      const double tN = __shfl_up_sync(mask, N, d, W), tD = __shfl_up_sync(mask, Dp, d, W);
+      if (lane >= d) {
+        N += tN;
+        Dp += tD;
+      }
+    }
+    const double D = vt0 + Dp;
+    const double R = lane < nc ? __ddiv_rn(N, D) : 0.0;
+    long long best = __double_as_longlong(R);  // R >= 0: the bit image orders like the value
+    int bl = lane;
+#pragma unroll
+    for (int d = W >> 1; d > 0; d >>= 1) {
+      const long long ob = __shfl_xor_sync(mask, best, d, W);
+      const int ol = __shfl_xor_sync(mask, bl, d, W);
+      if (ob > best || (ob == best && ol < bl)) {
+        best = ob;
+        bl = ol;
+      }
+    }
+    const int kstar = best > 0 ? bl + 1 : 0;
+    const double bestD = __shfl_sync(mask, D, bl, W);
+    const double z = lam * __longlong_as_double(best);
+    if (MODE == kIterate) {
+      const double x = lane < kstar ? __ddiv_rn(__dmul_rn(lam, v_r), bestD) : 0.0;
+      if (SAMPLED) {
+        if (idx < K) {
+          const long long p = b + idx;
+          const double xo = x_cur[p];
+          if (x != xo) atomicAdd(s + j_r, x - xo);
+          x_cur[p] = x;
+        }
+      } else if (lane < kstar) {
+        atomicAdd(s + j_r, x);
+      }
+    }
+    if (lane == 0) {
+      zacc += z;
+      if (MODE == kEvalSeg) z_seg[l] = z;
+    }
+  }
+  const double tot = block_sum(zacc, sh);
+  if (threadIdx.x == 0) zpart[blockIdx.x] = tot;
+}
+
+// -------------------------------------------------------------- a3 .. a5 --
+__global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, RunConfig cfg, int full) {
+  DevState* st = Wk.st;
+  if (st->converged) return;
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const double tau = st->tau, shrink = __dsub_rn(1.0, __dmul_rn(st->tau, st->mu));
+  double cy = 0.0, pr = 0.0;
+  if (gid < P.m) {
+    double g = 0.0;
+    for (int q = P.at_ptr[gid]; q < P.at_ptr[gid + 1]; ++q) {
+      const double a = P.at_val ? P.at_val[q] : 1.0;
+      g = __dadd_rn(g, __dmul_rn(a, Wk.s[P.at_idx[q]]));
+    }
+    const double yo = Wk.y[gid], c = P.c[gid];
+    const double yn = __dsub_rn(__dmul_rn(shrink, yo), __dmul_rn(tau, __dsub_rn(c, g)));
+    Wk.y[gid] = yn > 0.0 ? yn : 0.0;
+    Wk.g[gid] = g;
+    Wk.sum_y[gid] = __dadd_rn(Wk.sum_y[gid], yo);
+    Wk.sum_g[gid] = __dadd_rn(Wk.sum_g[gid], g);
+    if (yo != 0.0) cy = __dmul_rn(c, yo);
+  }
+  if (gid < P.n) pr = __dmul_rn(P.r[gid], Wk.s[gid]);
+  const double bcy = block_sum(cy, sh);
+  const double bpr = block_sum(pr, sh);
+  if (threadIdx.x == 0) {
+    Wk.cypart[blockIdx.x] = bcy;
+    Wk.Ppart[blockIdx.x] = bpr;
+    __threadfence();
+    const unsigned prev = atomicAdd(&st->ticket, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  // Last block: fold the partial sums in block order.
+  __threadfence();
+  double zs = 0.0, cys = 0.0, Ps = 0.0;
+  for (int b = 0; b < Wk.seg_blocks; ++b) zs += __ldcg(Wk.zpart + b);
+  for (int b = 0; b < (int)gridDim.x; ++b) {
+    cys += __ldcg(Wk.cypart + b);
+    Ps += __ldcg(Wk.Ppart + b);
+  }
+  st->z_sum = full ? zs : CUDART_NAN;
+  st->dual_iter = full ? cys + zs : CUDART_NAN;
+  st->P = Ps;
+  st->sum_P += Ps;
+  st->count += 1;
+  st->t += 1;
+  st->ticket = 0;
+}
+
+// ------------------------------------------------------------------- a6 --
+// KKT residual of the epoch averages and the restart test (solver addition;
+// the paper's Remark in Section 4.2 notes SPFOM forms no residuals).
+__global__ void __launch_bounds__(1024) k_eval_finish(Problem P, Work Wk, RunConfig cfg) {
+  DevState* st = Wk.st;
+  if (st->converged) return;
+  __shared__ double sh[32];
+  __shared__ int restart;
+  const double cnt = (double)st->count;
+  double cy = 0.0, over2 = 0.0, c2 = 0.0;
+  for (int i = threadIdx.x; i < P.m; i += blockDim.x) {
+    const double yb = __ddiv_rn(Wk.sum_y[i], cnt), gb = __ddiv_rn(Wk.sum_g[i], cnt), c = P.c[i];
+    if (yb != 0.0) cy += __dmul_rn(c, yb);
+    const double o = __dsub_rn(gb, c);
+    if (o > 0.0) over2 += __dmul_rn(o, o);
+    c2 += __dmul_rn(c, c);
+  }
+  double zs = 0.0;
+  if (threadIdx.x == 0)
+    for (int b = 0; b < Wk.seg_blocks; ++b) zs += Wk.zpart_eval[b];
+  const double tcy = block_sum(cy, sh);
+  const double tover = block_sum(over2, sh);
+  const double tc2 = block_sum(c2, sh);
+  if (threadIdx.x == 0) {
+    const double Pbar = st->sum_P / cnt;
+    const double D = tcy + zs;
+    const double pinf = sqrt(tover) / (1.0 + sqrt(tc2));
+    const double gap = fabs(D - Pbar) / (1.0 + fabs(D) + fabs(Pbar));
+    const double kkt = pinf > gap ? pinf : gap;
+    st->pinf = pinf;
+    st->gap = gap;
+    st->kkt = kkt;
+    st->dual_avg = D;
+    st->primal_avg = Pbar;
+    st->evals += 1;
+    st->converged = kkt <= cfg.kkt_tol;
+    restart = !st->converged && (kkt <= cfg.restart_beta * st->kkt_anchor ||
+                                 (double)st->count >= cfg.restart_artificial * (double)st->t);
+  }
+  __syncthreads();
+  if (!restart) return;
+  for (int i = threadIdx.x; i < P.m; i += blockDim.x) {
+    Wk.y[i] = __ddiv_rn(Wk.sum_y[i], cnt);
+    Wk.sum_y[i] = 0.0;
+    Wk.sum_g[i] = 0.0;
+  }
+  if (threadIdx.x == 0) {
+    st->sum_P = 0.0;
+    st->count = 0;
+    st->kkt_anchor = st->kkt;
+    if (st->mu > 0.0) st->mu *= 0.5;
+    st->tau *= cfg.restart_tau_decay;
+    st->restarts += 1;
+  }
+}
+
+// Dual(y) = c^T y + sum_l z_l(y) for spfom_evaluate.
+__global__ void __launch_bounds__(1024) k_evaluate_finish(Problem P, Work Wk) {
+  __shared__ double sh[32];
+  double cy = 0.0;
+  for (int i = threadIdx.x; i < P.m; i += blockDim.x)
+    if (Wk.y_eval[i] != 0.0) cy += __dmul_rn(P.c[i], Wk.y_eval[i]);
+  const double tcy = block_sum(cy, sh);
+  if (threadIdx.x == 0) {
+    double zs = 0.0;
+    for (int b = 0; b < Wk.seg_blocks; ++b) zs += Wk.zpart_eval[b];
+    Wk.st->eval_out = tcy + zs;
+  }
+}
+
+template <int MODE, bool SAMPLED>
+cudaError_t launch_segments_w(const Problem& P, const Work& Wk, const double* marg, double* zpart,
+                              const DevState* st, const RunConfig& cfg, cudaStream_t s) {
+  const int g = Wk.seg_blocks;
+  switch (Wk.W) {
+#define SPFOM_SEG_CASE(WW)                                                                              \
+  case WW:                                                                                              \
+    k_segments<WW, MODE, SAMPLED><<<g, kSegThreads, 0, s>>>(P, marg, Wk.s, Wk.x_cur, Wk.z_seg, zpart, st, \
+                                                            cfg.seed, cfg.sample_thr);                 \
+    break;
+    SPFOM_SEG_CASE(1)
+    SPFOM_SEG_CASE(2)
+    SPFOM_SEG_CASE(4)
+    SPFOM_SEG_CASE(8)
+    SPFOM_SEG_CASE(16)
+    SPFOM_SEG_CASE(32)
+#undef SPFOM_SEG_CASE
+    default:
+      return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+int vec_grid(const Problem& P) {
+  const int n = P.n > P.m ? P.n : P.m;
+  return (n + kVecThreads - 1) / kVecThreads > 0 ? (n + kVecThreads - 1) / kVecThreads : 1;
+}
+
+}  // namespace
+
+cudaError_t launch_prep(const Problem& P, const double* w, const double* v0, double* vt, double* vt0,
+                        cudaStream_t s) {
+  if (P.nnz > 0) k_prep_items<<<(unsigned)((P.nnz + 255) / 256), 256, 0, s>>>(P.nnz, P.v, w, vt);
+  if (P.L > 0) k_prep_segments<<<(unsigned)((P.L + 255) / 256), 256, 0, s>>>(P.L, P.seg_ptr, v0, w, vt0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s,
+                             cudaEvent_t seg_begin, cudaEvent_t seg_end) {
+  const bool sampled = cfg.batch_frac < 1.0;
+  const int gv = vec_grid(P);
+  k_margins<<<(P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1, kVecThreads,
+              0, s>>>(P, Wk.y, nullptr, 0, Wk.marg, sampled ? nullptr : Wk.s, Wk.st);
+  if (seg_begin) cudaEventRecord(seg_begin, s);
+  cudaError_t e = sampled ? launch_segments_w<kIterate, true>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s)
+                          : launch_segments_w<kIterate, false>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s);
+  if (seg_end) cudaEventRecord(seg_end, s);
+  if (e != cudaSuccess) return e;
+  k_dual_step<<<gv, kVecThreads, 0, s>>>(P, Wk, cfg, sampled ? 0 : 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s) {
+  k_margins<<<(P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1, kVecThreads,
+              0, s>>>(P, nullptr, Wk.sum_y, 1, Wk.marg_eval, nullptr, Wk.st);
+  cudaError_t e = launch_segments_w<kEvalSum, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, Wk.st, cfg, s);
+  if (e != cudaSuccess) return e;
+  k_eval_finish<<<1, 1024, 0, s>>>(P, Wk, cfg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_evaluate_at(const Problem& P, const Work& Wk, bool want_seg, cudaStream_t s) {
+  RunConfig cfg{};
+  k_margins<<<(P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1, kVecThreads,
+              0, s>>>(P, Wk.y_eval, nullptr, 0, Wk.marg_eval, nullptr, nullptr);
+  cudaError_t e = want_seg ? launch_segments_w<kEvalSeg, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, nullptr, cfg, s)
+                           : launch_segments_w<kEvalSum, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, nullptr, cfg, s);
+  if (e != cudaSuccess) return e;
+  k_evaluate_finish<<<1, 1024, 0, s>>>(P, Wk);
+  return cudaGetLastError();
+}
+
+int kernel_launches_per_iteration() { return 3; }
+int kernel_launches_per_eval() { return 3; }
+
+}  // namespace spfom

@@ -1,0 +1,229 @@
+"""Python binding of libspfom.so (the C ABI of include/spfom.h).
+
+Argument marshalling only: every step of the iteration runs in the library's
+sm_103a kernels. The library must be built (``build.build()``); importing this
+module on a machine without it raises instead of falling back to anything.
+PyTorch, when present, only supplies the CUDA stream the ctx runs on.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "libspfom.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENOTCONV, ENOTSUP = range(8)
+VEC_Y, VEC_YBAR, VEC_SUM_Y, VEC_SUM_G, VEC_G, VEC_S, VEC_MARGINS = range(7)
+
+# Every function include/spfom.h declares.
+EXPORTS = ("spfom_default_params", "spfom_create", "spfom_load_instance", "spfom_reset", "spfom_step",
+           "spfom_solve", "spfom_vector", "spfom_duals", "spfom_evaluate", "spfom_get_stats", "spfom_destroy",
+           "spfom_last_error", "spfom_status_string")
+
+_f64p = C.POINTER(C.c_double)
+_i32p = C.POINTER(C.c_int32)
+_i64p = C.POINTER(C.c_int64)
+
+
+class Params(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("tau", C.c_double), ("tau0", C.c_double), ("mu", C.c_double),
+                ("batch_frac", C.c_double), ("seed", C.c_uint64), ("eval_every", C.c_int64),
+                ("restart_beta", C.c_double), ("restart_artificial", C.c_double),
+                ("restart_tau_decay", C.c_double), ("kkt_tol", C.c_double), ("max_iters", C.c_int64),
+                ("device", C.c_int32), ("profile", C.c_int32), ("stream", C.c_void_p)]
+
+
+class InstanceC(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("L", C.c_int64), ("r", _f64p), ("c", _f64p),
+                ("a_ptr", _i32p), ("a_idx", _i32p), ("a_val", _f64p), ("seg_ptr", _i64p), ("seg_prod", _i32p),
+                ("v", _f64p), ("w", _f64p), ("lam", _f64p), ("v0", _f64p)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int64), ("restarts", C.c_int64), ("evals", C.c_int64), ("epoch_iters", C.c_int64),
+                ("converged", C.c_int32), ("pad_", C.c_int32), ("kkt", C.c_double), ("pinf", C.c_double),
+                ("gap", C.c_double), ("dual_avg", C.c_double), ("primal_avg", C.c_double),
+                ("dual_iter", C.c_double), ("z_sum", C.c_double), ("revenue", C.c_double),
+                ("sum_revenue", C.c_double), ("tau", C.c_double), ("mu", C.c_double), ("seconds", C.c_double),
+                ("seg_kernel_seconds", C.c_double), ("seg_kernel_launches", C.c_int64),
+                ("kernel_launches", C.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad_"}
+
+
+class SpfomError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """Load libspfom.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB):
+            raise RuntimeError(f"{LIB} is missing: build it with paper_2602_22421_gb300.build.build()")
+        h = C.CDLL(LIB)
+        P = C.POINTER
+        h.spfom_default_params.argtypes = [P(Params)]
+        h.spfom_default_params.restype = None
+        h.spfom_create.argtypes = [P(Params), P(C.c_void_p)]
+        h.spfom_load_instance.argtypes = [C.c_void_p, P(InstanceC)]
+        h.spfom_reset.argtypes = [C.c_void_p, _f64p]
+        h.spfom_step.argtypes = [C.c_void_p, C.c_int64, P(Stats)]
+        h.spfom_solve.argtypes = [C.c_void_p, _f64p, P(Stats)]
+        h.spfom_vector.argtypes = [C.c_void_p, C.c_int, _f64p]
+        h.spfom_duals.argtypes = [C.c_void_p, C.c_int32, _f64p]
+        h.spfom_evaluate.argtypes = [C.c_void_p, _f64p, _f64p, _f64p]
+        h.spfom_get_stats.argtypes = [C.c_void_p, P(Stats)]
+        h.spfom_destroy.argtypes = [C.c_void_p]
+        h.spfom_destroy.restype = None
+        h.spfom_last_error.argtypes = [C.c_void_p]
+        h.spfom_last_error.restype = C.c_char_p
+        h.spfom_status_string.argtypes = [C.c_int]
+        h.spfom_status_string.restype = C.c_char_p
+        for f in ("spfom_create", "spfom_load_instance", "spfom_reset", "spfom_step", "spfom_solve", "spfom_vector",
+                  "spfom_duals", "spfom_evaluate", "spfom_get_stats"):
+            getattr(h, f).restype = C.c_int
+        _lib = h
+    return _lib
+
+
+def _p(a, t):
+    return None if a is None else a.ctypes.data_as(t)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    lib().spfom_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+class InstanceArrays:
+    """Contiguous host copies of an instance's arrays plus the C view of them."""
+
+    def __init__(self, inst):
+        self.keep = dict(
+            r=np.ascontiguousarray(inst.r, np.float64), c=np.ascontiguousarray(inst.c, np.float64),
+            a_ptr=np.ascontiguousarray(inst.a_ptr, np.int32), a_idx=np.ascontiguousarray(inst.a_idx, np.int32),
+            a_val=None if inst.a_val is None else np.ascontiguousarray(inst.a_val, np.float64),
+            seg_ptr=np.ascontiguousarray(inst.seg_ptr, np.int64),
+            seg_prod=np.ascontiguousarray(inst.seg_prod, np.int32), v=np.ascontiguousarray(inst.v, np.float64),
+            w=None if inst.w is None else np.ascontiguousarray(inst.w, np.float64),
+            lam=np.ascontiguousarray(inst.lam, np.float64), v0=np.ascontiguousarray(inst.v0, np.float64))
+        k = self.keep
+        self.c = InstanceC(inst.n, inst.m, inst.L, _p(k["r"], _f64p), _p(k["c"], _f64p), _p(k["a_ptr"], _i32p),
+                           _p(k["a_idx"], _i32p), _p(k["a_val"], _f64p), _p(k["seg_ptr"], _i64p),
+                           _p(k["seg_prod"], _i32p), _p(k["v"], _f64p), _p(k["w"], _f64p), _p(k["lam"], _f64p),
+                           _p(k["v0"], _f64p))
+
+    def nbytes(self) -> int:
+        return sum(a.nbytes for a in self.keep.values() if a is not None)
+
+
+class Solver:
+    """One spfom_ctx. ``Solver(inst, **params)`` creates it and loads ``inst``."""
+
+    def __init__(self, inst=None, stream: Optional[int] = None, **params):
+        self._lib = lib()
+        p = default_params(**params)
+        if p.stream is None:
+            p.stream = stream if stream is not None else _current_stream()
+        h = C.c_void_p()
+        self._check(self._lib.spfom_create(C.byref(p), C.byref(h)), ctx=None)
+        self._h = h
+        self.params = p
+        self.n = self.m = self.L = 0
+        if inst is not None:
+            self.load(inst)
+
+    def _check(self, st: int, ctx="self"):
+        if st != OK:
+            h = self._h if ctx == "self" else None
+            msg = self._lib.spfom_last_error(h).decode() if h else self._lib.spfom_status_string(st).decode()
+            raise SpfomError(st, msg)
+
+    def load(self, inst):
+        arrs = inst if isinstance(inst, InstanceArrays) else InstanceArrays(inst)
+        self._check(self._lib.spfom_load_instance(self._h, C.byref(arrs.c)))
+        self.n, self.m, self.L = arrs.c.n, arrs.c.m, arrs.c.L
+        return self
+
+    def reset(self, y0=None):
+        y = None if y0 is None else np.ascontiguousarray(y0, np.float64)
+        self._check(self._lib.spfom_reset(self._h, _p(y, _f64p)))
+
+    def step(self, iters: int) -> dict:
+        st = Stats()
+        self._check(self._lib.spfom_step(self._h, int(iters), C.byref(st)))
+        return st.as_dict()
+
+    def solve(self, y0=None) -> dict:
+        y = None if y0 is None else np.ascontiguousarray(y0, np.float64)
+        st = Stats()
+        rc = self._lib.spfom_solve(self._h, _p(y, _f64p), C.byref(st))
+        if rc not in (OK, ENOTCONV):
+            self._check(rc)
+        return st.as_dict()
+
+    def stats(self) -> dict:
+        st = Stats()
+        self._check(self._lib.spfom_get_stats(self._h, C.byref(st)))
+        return st.as_dict()
+
+    def vector(self, which: int) -> np.ndarray:
+        size = self.n if which in (VEC_S, VEC_MARGINS) else self.m
+        out = np.empty(max(size, 1))
+        self._check(self._lib.spfom_vector(self._h, which, _p(out, _f64p)))
+        return out[:size]
+
+    def duals(self, averaged: bool = False) -> np.ndarray:
+        out = np.empty(max(self.m, 1))
+        self._check(self._lib.spfom_duals(self._h, 1 if averaged else 0, _p(out, _f64p)))
+        return out[: self.m]
+
+    def evaluate(self, y, per_segment: bool = False):
+        y = np.ascontiguousarray(y, np.float64)
+        z = np.empty(max(self.L, 1)) if per_segment else None
+        d = C.c_double(0.0)
+        self._check(self._lib.spfom_evaluate(self._h, _p(y, _f64p), _p(z, _f64p), C.byref(d)))
+        return (d.value, z[: self.L]) if per_segment else d.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.spfom_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

@@ -1,0 +1,223 @@
+"""CUDA path against the FP64 oracle, through the C ABI (needs a GPU).
+
+Tolerance: the FP64 iterates must track the oracle to 1e-6 relative for the
+first 200 iterations (norm-relative: max_i |a_i - b_i| / max_i |b_i|). Both
+sides compute in binary64; they differ only in summation order (the GPU adds
+sales with atomics and scans prefixes as a tree), which moves results by a few
+ulps per iteration, so the bar has ample room while still catching any
+algorithmic difference (a wrong prefix, a dropped term, a missed restart).
+Per-segment values at a fixed dual point are compared at 1e-12.
+"""
+import numpy as np
+import pytest
+
+from instances import make_instance, mid_gam, seeded_duals, tiny_mnl
+from oracle import Oracle
+from oracle import Params as OracleParams
+
+pytestmark = pytest.mark.gpu
+
+ITER_RTOL = 1e-6
+VALUE_RTOL = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def Solver(inst, **kw):
+    from paper_2602_22421_gb300 import Solver as S
+    return S(inst, device=0, **kw)
+
+
+def nrel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    if a.size == 0:
+        return 0.0
+    scale = float(np.abs(b).max())
+    return float(np.abs(a - b).max()) / (scale if scale > 0 else 1.0)
+
+
+def small_gam():
+    return make_instance(n=30, m=8, L=600, kmin=3, kmax=8, gam=True, tightness=0.6, seed=5, name="small_gam")
+
+
+def edge_instance():
+    """Empty and 32-product consideration sets, zero arrival rates, items with
+    w = v, a segment count that leaves a ragged last tile."""
+    inst = make_instance(n=50, m=10, L=3001, kmin=0, kmax=32, gam=True, tightness=0.5, seed=11, name="edge")
+    rng = np.random.default_rng(12)
+    inst.lam[rng.uniform(size=inst.L) < 0.05] = 0.0
+    pick = rng.uniform(size=inst.nnz) < 0.05
+    inst.w[pick] = inst.v[pick]
+    return inst
+
+
+def mid_small():
+    return mid_gam(1, L=40_001, n=2000, m=400)
+
+
+CASES = {"tiny_mnl": lambda: tiny_mnl(0), "small_gam": small_gam, "edge": edge_instance, "mid_small": mid_small}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_iterates_track_oracle_200(name):
+    inst = CASES[name]()
+    o = Oracle(inst)
+    run = o.run(OracleParams())
+    done = 0
+    with Solver(inst) as s:
+        for t in (1, 2, 5, 63, 64, 65, 128, 129, 200):
+            while done < t:
+                marg_prev = o.margins(run.y)  # margins the coming iteration uses
+                run.step(1)
+                done += 1
+            st = s.step(t - st_iters(s))
+            ost = run.stats()
+            assert st["iters"] == ost["t"] == t
+            assert st["restarts"] == ost["restarts"] and st["evals"] == ost["evals"]
+            assert st["epoch_iters"] == ost["count"]
+            assert nrel(s.duals(), run.y) <= ITER_RTOL, (t, nrel(s.duals(), run.y))
+            assert nrel(s.vector(2), run.sum_y) <= ITER_RTOL
+            assert nrel(s.vector(3), run.sum_g) <= ITER_RTOL
+            assert nrel(s.vector(4), run.g) <= ITER_RTOL
+            assert nrel(s.vector(5), run.s) <= ITER_RTOL
+            assert nrel(s.vector(6), marg_prev) <= ITER_RTOL
+            assert st["revenue"] == pytest.approx(ost["P"], rel=ITER_RTOL)
+            assert st["z_sum"] == pytest.approx(ost["z_sum"], rel=ITER_RTOL)
+            assert st["dual_iter"] == pytest.approx(ost["dual_iter"], rel=ITER_RTOL)
+            assert st["tau"] == ost["tau_used"]
+            if ost["evals"]:
+                for k in ("kkt", "pinf", "gap"):
+                    assert st[k] == pytest.approx(ost[k], rel=1e-5, abs=1e-12), k
+                assert st["dual_avg"] == pytest.approx(ost["dual_avg"], rel=ITER_RTOL)
+                assert st["primal_avg"] == pytest.approx(ost["primal_avg"], rel=ITER_RTOL)
+
+
+def st_iters(s):
+    return s.stats()["iters"]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_evaluate_matches_oracle_per_segment(name):
+    inst = CASES[name]()
+    o = Oracle(inst)
+    with Solver(inst) as s:
+        for seed in (0, 1, 2):
+            y = np.zeros(inst.m) if seed == 0 else seeded_duals(inst.m, seed, float(np.mean(inst.r)) / 3)
+            ref = o.sweep(y)
+            dual, z = s.evaluate(y, per_segment=True)
+            np.testing.assert_allclose(z, ref["z"], rtol=VALUE_RTOL, atol=VALUE_RTOL * max(1.0, np.abs(ref["z"]).max()))
+            assert dual == pytest.approx(o.dual(y), rel=VALUE_RTOL)
+        # evaluation leaves the iteration state alone
+        assert s.stats()["iters"] == 0 and np.all(s.duals() == 0)
+
+
+def test_uncapacitated_duals_stay_zero():
+    inst = tiny_mnl(0, capacity="inf")
+    o = Oracle(inst)
+    with Solver(inst) as s:
+        st = s.step(100)
+        assert np.all(s.duals() == 0.0)
+        assert st["converged"] == 1 and st["iters"] == 64
+        assert st["dual_avg"] == pytest.approx(o.dual(np.zeros(inst.m)), rel=VALUE_RTOL)
+
+
+@pytest.mark.parametrize("p", [0.3, 0.05])
+def test_sampled_iterates_track_oracle(p):
+    inst = mid_gam(1, L=20_000, n=1000, m=200)
+    prm = dict(batch_frac=p, seed=42)
+    run = Oracle(inst).run(OracleParams(**prm))
+    with Solver(inst, **prm) as s:
+        for t in (1, 3, 64, 150):
+            run.step(t - run.stats()["t"])
+            st = s.step(t - st_iters(s))
+            assert st["iters"] == t and st["restarts"] == run.stats()["restarts"]
+            assert nrel(s.duals(), run.y) <= ITER_RTOL
+            assert nrel(s.vector(5), run.s) <= ITER_RTOL
+            assert np.isnan(st["z_sum"])
+
+
+@pytest.mark.parametrize("mu,decay", [(0.05, 1.0), (0.0, 0.5)])
+def test_regularised_and_decayed_steps_track_oracle(mu, decay):
+    inst = small_gam()
+    prm = dict(mu=mu, restart_tau_decay=decay, eval_every=16)
+    run = Oracle(inst).run(OracleParams(**prm))
+    run.step(200)
+    with Solver(inst, **prm) as s:
+        st = s.step(200)
+    assert st["restarts"] == run.stats()["restarts"] > 0
+    assert st["mu"] == run.stats()["mu_cur"] and st["tau"] == run.stats()["tau_used"]
+    assert nrel(s.duals(), run.y) <= ITER_RTOL
+
+
+def test_solve_reaches_tolerance_like_oracle():
+    inst = mid_gam(1, L=20_000, n=1000, m=200)
+    run = Oracle(inst).run(OracleParams())
+    for _ in range(200):
+        ost = run.step(64)
+        if ost["converged"]:
+            break
+    assert ost["converged"] == 1
+    with Solver(inst) as s:
+        st = s.solve()
+        assert st["converged"] == 1 and st["iters"] == ost["t"] and st["restarts"] == ost["restarts"]
+        assert st["dual_avg"] == pytest.approx(ost["dual_avg"], rel=1e-6)
+        assert st["kkt"] <= 1e-4
+        assert nrel(s.duals(averaged=True), run.ybar) <= ITER_RTOL
+
+
+def test_full_size_mid_instance_first_iterations():
+    """The 1e6-segment GAM instance in the benchmark's launch configuration:
+    three iterations element by element, and every segment's value at a
+    seeded dual point."""
+    inst = mid_gam(1)
+    o = Oracle(inst)
+    run = o.run(OracleParams())
+    run.step(3)
+    y = seeded_duals(inst.m, 7, float(np.mean(inst.r)) / 4)
+    ref = o.sweep(y)
+    with Solver(inst) as s:
+        st = s.step(3)
+        assert nrel(s.duals(), run.y) <= ITER_RTOL
+        assert nrel(s.vector(4), run.g) <= ITER_RTOL
+        assert nrel(s.vector(5), run.s) <= ITER_RTOL
+        assert st["dual_iter"] == pytest.approx(run.stats()["dual_iter"], rel=ITER_RTOL)
+        dual, z = s.evaluate(y, per_segment=True)
+        np.testing.assert_allclose(z, ref["z"], rtol=VALUE_RTOL, atol=VALUE_RTOL * np.abs(ref["z"]).max())
+        assert dual == pytest.approx(ref["zsum"] + float(inst.c @ y), rel=1e-10)
+
+
+def _bad(mut):
+    inst = tiny_mnl(0)
+    inst.v = inst.v.copy()
+    inst.seg_prod = inst.seg_prod.copy()
+    inst.a_idx = inst.a_idx.copy()
+    inst.v0 = inst.v0.copy()
+    mut(inst)
+    return inst
+
+
+@pytest.mark.parametrize("mut,status,needle", [
+    (lambda I: I.v.__setitem__(3, 0.0), 1, "v["),
+    (lambda I: I.v0.__setitem__(2, -1.0), 1, "v0["),
+    (lambda I: I.seg_prod.__setitem__(1, I.seg_prod[0]), 1, "repeated"),
+    (lambda I: I.a_idx.__setitem__(0, 99), 1, "out of range"),
+    (lambda I: setattr(I, "w", I.v * 1.5), 1, "w["),
+])
+def test_invalid_instances_are_rejected(mut, status, needle):
+    from paper_2602_22421_gb300 import SpfomError
+    inst = _bad(mut)
+    with pytest.raises(SpfomError) as ei:
+        Solver(inst)
+    assert ei.value.status == status and needle in str(ei.value)
+
+
+def test_large_consideration_set_is_unsupported():
+    from paper_2602_22421_gb300 import SpfomError
+    inst = make_instance(n=40, m=5, L=10, kmin=33, kmax=33, seed=3)
+    with pytest.raises(SpfomError) as ei:
+        Solver(inst)
+    assert ei.value.status == 7
