@@ -160,6 +160,8 @@ class Solver:
             self.load(inst)
 
     def _check(self, st: int, ctx="self"):
+        if ctx == "self" and not getattr(self, "_h", None):
+            raise SpfomError(ESTATE, "solver is closed")
         if st != OK:
             h = self._h if ctx == "self" else None
             msg = self._lib.spfom_last_error(h).decode() if h else self._lib.spfom_status_string(st).decode()

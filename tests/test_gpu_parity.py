@@ -148,9 +148,9 @@ def test_regularised_and_decayed_steps_track_oracle(mu, decay):
     run.step(200)
     with Solver(inst, **prm) as s:
         st = s.step(200)
-    assert st["restarts"] == run.stats()["restarts"] > 0
-    assert st["mu"] == run.stats()["mu_cur"] and st["tau"] == run.stats()["tau_used"]
-    assert nrel(s.duals(), run.y) <= ITER_RTOL
+        assert st["restarts"] == run.stats()["restarts"] > 0
+        assert st["mu"] == run.stats()["mu_cur"] and st["tau"] == run.stats()["tau_used"]
+        assert nrel(s.duals(), run.y) <= ITER_RTOL
 
 
 def test_solve_reaches_tolerance_like_oracle():
