@@ -68,6 +68,9 @@ typedef struct {
   int32_t device;            /* CUDA device ordinal (0) */
   int32_t profile;           /* 0; nonzero: time every segment-kernel launch of spfom_step with
                                 a CUDA event pair (spfom_stats.seg_kernel_seconds) */
+  int32_t path;              /* 0 (default): the certified-decision segment kernel whenever the
+                                instance allows it (sets of <= 32 products, n <= 25600, full
+                                batch), else the general kernel; 1: always the general kernel */
   void* stream;              /* cudaStream_t to run on; NULL (default): the ctx creates one */
 } spfom_params;
 
@@ -118,6 +121,10 @@ typedef struct {
                                   of the iterations (params.profile only, else 0) */
   int64_t seg_kernel_launches; /* those launches */
   int64_t kernel_launches;     /* all kernels this call launched */
+  int64_t fallback_segments;   /* segment solves since the last reset whose binary32 decision
+                                  was not certified and was redone in binary64 */
+  int32_t fast_path;           /* 1 when the certified-decision kernel runs the iterations */
+  int32_t pad2_;
 } spfom_stats;
 
 /* Which vector spfom_vector() returns. */

@@ -38,6 +38,7 @@ struct spfom_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> prof_ev;  // event pairs of profiled segment launches
   int sms = 0;
+  unsigned long long fallback_host = 0;
 };
 
 namespace {
@@ -163,6 +164,9 @@ spfom_status init_state(spfom_ctx* ctx, const double* y0) {
   SPFOM_CUDA(ctx, cudaMemsetAsync(W.s, 0, sizeof(double) * (P.n ? P.n : 1), ctx->stream));
   SPFOM_CUDA(ctx, cudaMemsetAsync(W.marg, 0, sizeof(double) * (P.n ? P.n : 1), ctx->stream));
   if (W.x_cur) SPFOM_CUDA(ctx, cudaMemsetAsync(W.x_cur, 0, sizeof(double) * (P.nnz ? P.nnz : 1), ctx->stream));
+  if (W.s_fx) SPFOM_CUDA(ctx, cudaMemsetAsync(W.s_fx, 0, sizeof(unsigned long long) * (P.n ? P.n : 1), ctx->stream));
+  if (W.fallbacks) SPFOM_CUDA(ctx, cudaMemsetAsync(W.fallbacks, 0, sizeof(unsigned long long), ctx->stream));
+  ctx->fallback_host = 0;
   DevState st{};
   st.tau = ctx->tau_init;
   st.mu = ctx->p.mu;
@@ -178,6 +182,8 @@ spfom_status init_state(spfom_ctx* ctx, const double* y0) {
 void fill_stats(const spfom_ctx* ctx, const DevState& st, double secs, spfom_stats* out) {
   if (!out) return;
   spfom_stats s{};
+  s.fallback_segments = (long long)ctx->fallback_host;
+  s.fast_path = (ctx->W.fast && ctx->cfg.batch_frac >= 1.0) ? 1 : 0;
   s.iters = st.t;
   s.restarts = st.restarts;
   s.evals = st.evals;
@@ -195,12 +201,14 @@ void fill_stats(const spfom_ctx* ctx, const DevState& st, double secs, spfom_sta
   s.tau = st.tau;
   s.mu = st.mu;
   s.seconds = secs;
-  (void)ctx;
   *out = s;
 }
 
 spfom_status read_state(spfom_ctx* ctx, DevState* st) {
   SPFOM_CUDA(ctx, cudaMemcpyAsync(st, ctx->W.st, sizeof *st, cudaMemcpyDeviceToHost, ctx->stream));
+  if (ctx->W.fallbacks)
+    SPFOM_CUDA(ctx, cudaMemcpyAsync(&ctx->fallback_host, ctx->W.fallbacks, sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, ctx->stream));
   SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return SPFOM_OK;
 }
@@ -361,8 +369,30 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   SPFOM_TRY(dalloc(ctx, &W.marg, (size_t)n));
   SPFOM_TRY(dalloc(ctx, &W.marg_eval, (size_t)n));
   SPFOM_TRY(dalloc(ctx, &W.z_seg, (size_t)L));
-  SPFOM_TRY(dalloc(ctx, &W.zpart, (size_t)W.seg_blocks));
-  SPFOM_TRY(dalloc(ctx, &W.zpart_eval, (size_t)W.seg_blocks));
+  // certified-decision kernel: plan, fixed-point scale 2^F with sum(lambda) * 2^F < 2^61
+  W.fast = false;
+  W.zparts_iter = W.zparts_eval = W.seg_blocks;
+  {
+    double mass = 0.0;
+    for (long long l = 0; l < L; ++l) mass += I->lam[l];
+    int e2 = 0;
+    std::frexp(mass > 1.0 ? mass : 1.0, &e2);  // mass < 2^e2
+    const int F = 61 - e2;
+    spfom::FastPlan plan{};
+    if (ctx->p.path == 0 && F >= 30 && spfom::fast_plan(n, kmax, ctx->sms, &plan)) {
+      W.fast = true;
+      W.plan = plan;
+      W.fx_scale = std::ldexp(1.0, F);
+      W.inv_fx_scale = std::ldexp(1.0, -F);
+      W.zparts_iter = plan.grid;
+      W.zparts_eval = plan.grid_eval;
+      SPFOM_TRY(dalloc(ctx, &W.part, (size_t)plan.grid * (size_t)(n > 0 ? n : 1)));
+      SPFOM_TRY(dalloc(ctx, &W.s_fx, (size_t)n));
+    }
+    SPFOM_TRY(dalloc(ctx, &W.fallbacks, 1));
+  }
+  SPFOM_TRY(dalloc(ctx, &W.zpart, (size_t)std::max(W.seg_blocks, W.zparts_iter)));
+  SPFOM_TRY(dalloc(ctx, &W.zpart_eval, (size_t)std::max(W.seg_blocks, W.zparts_eval)));
   SPFOM_TRY(dalloc(ctx, &W.cypart, (size_t)W.vec_blocks));
   SPFOM_TRY(dalloc(ctx, &W.Ppart, (size_t)W.vec_blocks));
   W.x_cur = nullptr;
@@ -420,7 +450,7 @@ spfom_status spfom_step(spfom_ctx* ctx, int64_t iters, spfom_stats* out) {
                                             prof ? ctx->prof_ev[2 * k] : nullptr,
                                             prof ? ctx->prof_ev[2 * k + 1] : nullptr);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "iteration launch");
-    launches += spfom::kernel_launches_per_iteration();
+    launches += spfom::kernel_launches_per_iteration(ctx->W, ctx->cfg);
     ++t;
     if (E > 0 && t % E == 0) {
       e = spfom::launch_eval(ctx->P, ctx->W, ctx->cfg, ctx->stream);

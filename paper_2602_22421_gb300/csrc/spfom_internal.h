@@ -1,5 +1,6 @@
-// Internal types shared by the kernels (spfom_kernels.cu) and the C ABI
-// (spfom_api.cu). Not installed; the public interface is include/spfom.h.
+// Internal types shared by the kernels (spfom_kernels.cu,
+// spfom_segments_fast.cu) and the C ABI (spfom_api.cu). Not installed; the
+// public interface is include/spfom.h.
 #pragma once
 #include <cuda_runtime.h>
 #include <cstdint>
@@ -41,6 +42,18 @@ struct Problem {
   const double* vt0;     // [L] v0 + sum_{C_l} w
 };
 
+constexpr int kFastThreads = 512;
+constexpr int kFastMaxSmem = 200 * 1024;
+
+// Launch plan of the certified-decision segment kernel.
+struct FastPlan {
+  int W;              // lanes per segment (4 products per lane)
+  int smem;           // bytes of the per-block product accumulator
+  int grid;           // blocks of the iterate launch (= number of partial sums)
+  int grid_eval;      // blocks of the evaluation launch
+  int reduce_chunks;  // grid.y of k_reduce_products
+};
+
 // Work buffers of one ctx.
 struct Work {
   double* y;
@@ -52,15 +65,33 @@ struct Work {
   double* marg_eval;
   double* y_eval;      // dual point handed to spfom_evaluate
   double* z_seg;       // [L] per-segment values of spfom_evaluate
-  double* zpart;       // [seg_blocks]
-  double* zpart_eval;  // [seg_blocks]
+  double* zpart;       // per-block partial sums of z (iterate)
+  double* zpart_eval;  // per-block partial sums of z (evaluation)
   double* cypart;      // [vec_blocks]
   double* Ppart;       // [vec_blocks]
   double* x_cur;       // [nnz] current responses (sampling only)
   DevState* st;
-  int seg_blocks;
+  int seg_blocks;      // blocks of the general segment kernel
   int vec_blocks;
-  int W;               // lanes per segment (power of two >= max |C_l|)
+  int W;               // lanes per segment of the general kernel (power of two >= max |C_l|)
+  int zparts_iter, zparts_eval;  // valid entries of zpart / zpart_eval
+  // certified-decision path (spfom_segments_fast.cu)
+  bool fast;
+  FastPlan plan;
+  unsigned long long* part;       // [plan.grid][n] per-block fixed-point product sales
+  unsigned long long* s_fx;       // [n] fixed-point product sales
+  unsigned long long* fallbacks;  // running count of segments decided in binary64
+  double fx_scale, inv_fx_scale;  // 2^F and 2^-F
+};
+
+struct FastArgs {
+  Problem P;
+  const double* marg;
+  unsigned long long* part;
+  double* zpart;
+  const DevState* st;
+  double fx_scale;
+  unsigned long long* fallbacks;
 };
 
 struct RunConfig {
@@ -78,7 +109,13 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
                              cudaEvent_t seg_begin = nullptr, cudaEvent_t seg_end = nullptr);
 cudaError_t launch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s);
 cudaError_t launch_evaluate_at(const Problem& P, const Work& Wk, bool want_seg, cudaStream_t s);
-int kernel_launches_per_iteration();
+int kernel_launches_per_iteration(const Work& Wk, const RunConfig& cfg);
 int kernel_launches_per_eval();
+
+// spfom_segments_fast.cu
+bool fast_plan(int n, int kmax, int sms, FastPlan* plan);
+cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s);
+cudaError_t launch_reduce_products(const Problem& P, const FastPlan& plan, const unsigned long long* part,
+                                   unsigned long long* s_fx, const DevState* st, cudaStream_t s);
 
 }  // namespace spfom

@@ -85,7 +85,8 @@ __global__ void k_prep_segments(long long L, const long long* __restrict__ seg_p
 // order. avg != 0 uses the epoch average sum_y / count as y. Clears s when
 // given (full-batch iterations rebuild the sales from zero).
 __global__ void k_margins(Problem P, const double* __restrict__ y, const double* __restrict__ sum_y, int avg,
-                          double* __restrict__ marg, double* __restrict__ s_clear, const DevState* st) {
+                          double* __restrict__ marg, double* __restrict__ s_clear,
+                          unsigned long long* __restrict__ sfx_clear, const DevState* st) {
   if (st && st->converged) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= P.n) return;
@@ -99,6 +100,7 @@ __global__ void k_margins(Problem P, const double* __restrict__ y, const double*
   }
   marg[j] = __dsub_rn(P.r[j], acc);
   if (s_clear) s_clear[j] = 0.0;
+  if (sfx_clear) sfx_clear[j] = 0ull;
 }
 
 // ------------------------------------------------------------------- a2 --
@@ -216,11 +218,14 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const double tau = st->tau, shrink = __dsub_rn(1.0, __dmul_rn(st->tau, st->mu));
   double cy = 0.0, pr = 0.0;
+  const bool fx = Wk.fast && full;
   if (gid < P.m) {
     double g = 0.0;
     for (int q = P.at_ptr[gid]; q < P.at_ptr[gid + 1]; ++q) {
       const double a = P.at_val ? P.at_val[q] : 1.0;
-      g = __dadd_rn(g, __dmul_rn(a, Wk.s[P.at_idx[q]]));
+      const int j = P.at_idx[q];
+      const double sj = fx ? __dmul_rn(__ull2double_rn(Wk.s_fx[j]), Wk.inv_fx_scale) : Wk.s[j];
+      g = __dadd_rn(g, __dmul_rn(a, sj));
     }
     const double yo = Wk.y[gid], c = P.c[gid];
     const double yn = __dsub_rn(__dmul_rn(shrink, yo), __dmul_rn(tau, __dsub_rn(c, g)));
@@ -230,7 +235,14 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
     Wk.sum_g[gid] = __dadd_rn(Wk.sum_g[gid], g);
     if (yo != 0.0) cy = __dmul_rn(c, yo);
   }
-  if (gid < P.n) pr = __dmul_rn(P.r[gid], Wk.s[gid]);
+  if (gid < P.n) {
+    double sj = Wk.s[gid];
+    if (fx) {
+      sj = __dmul_rn(__ull2double_rn(Wk.s_fx[gid]), Wk.inv_fx_scale);
+      Wk.s[gid] = sj;
+    }
+    pr = __dmul_rn(P.r[gid], sj);
+  }
   const double bcy = block_sum(cy, sh);
   const double bpr = block_sum(pr, sh);
   if (threadIdx.x == 0) {
@@ -245,7 +257,7 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
   // Last block: fold the partial sums in block order.
   __threadfence();
   double zs = 0.0, cys = 0.0, Ps = 0.0;
-  for (int b = 0; b < Wk.seg_blocks; ++b) zs += __ldcg(Wk.zpart + b);
+  for (int b = 0; b < Wk.zparts_iter; ++b) zs += __ldcg(Wk.zpart + b);
   for (int b = 0; b < (int)gridDim.x; ++b) {
     cys += __ldcg(Wk.cypart + b);
     Ps += __ldcg(Wk.Ppart + b);
@@ -278,7 +290,7 @@ __global__ void __launch_bounds__(1024) k_eval_finish(Problem P, Work Wk, RunCon
   }
   double zs = 0.0;
   if (threadIdx.x == 0)
-    for (int b = 0; b < Wk.seg_blocks; ++b) zs += Wk.zpart_eval[b];
+    for (int b = 0; b < Wk.zparts_eval; ++b) zs += Wk.zpart_eval[b];
   const double tcy = block_sum(cy, sh);
   const double tover = block_sum(over2, sh);
   const double tc2 = block_sum(c2, sh);
@@ -369,22 +381,40 @@ cudaError_t launch_prep(const Problem& P, const double* w, const double* v0, dou
 cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s,
                              cudaEvent_t seg_begin, cudaEvent_t seg_end) {
   const bool sampled = cfg.batch_frac < 1.0;
+  const bool fast = Wk.fast && !sampled;
   const int gv = vec_grid(P);
-  k_margins<<<(P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1, kVecThreads,
-              0, s>>>(P, Wk.y, nullptr, 0, Wk.marg, sampled ? nullptr : Wk.s, Wk.st);
+  const int gn = (P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1;
+  k_margins<<<gn, kVecThreads, 0, s>>>(P, Wk.y, nullptr, 0, Wk.marg, (sampled || fast) ? nullptr : Wk.s,
+                                       fast ? Wk.s_fx : nullptr, Wk.st);
   if (seg_begin) cudaEventRecord(seg_begin, s);
-  cudaError_t e = sampled ? launch_segments_w<kIterate, true>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s)
-                          : launch_segments_w<kIterate, false>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s);
+  cudaError_t e;
+  if (fast) {
+    FastArgs A{P, Wk.marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks};
+    e = launch_seg_fast(A, Wk.plan, true, s);
+  } else {
+    e = sampled ? launch_segments_w<kIterate, true>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s)
+                : launch_segments_w<kIterate, false>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s);
+  }
   if (seg_end) cudaEventRecord(seg_end, s);
   if (e != cudaSuccess) return e;
+  if (fast) {
+    e = launch_reduce_products(P, Wk.plan, Wk.part, Wk.s_fx, Wk.st, s);
+    if (e != cudaSuccess) return e;
+  }
   k_dual_step<<<gv, kVecThreads, 0, s>>>(P, Wk, cfg, sampled ? 0 : 1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s) {
-  k_margins<<<(P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1, kVecThreads,
-              0, s>>>(P, nullptr, Wk.sum_y, 1, Wk.marg_eval, nullptr, Wk.st);
-  cudaError_t e = launch_segments_w<kEvalSum, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, Wk.st, cfg, s);
+  const int gn = (P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1;
+  k_margins<<<gn, kVecThreads, 0, s>>>(P, nullptr, Wk.sum_y, 1, Wk.marg_eval, nullptr, nullptr, Wk.st);
+  cudaError_t e;
+  if (Wk.fast) {
+    FastArgs A{P, Wk.marg_eval, nullptr, Wk.zpart_eval, Wk.st, Wk.fx_scale, Wk.fallbacks};
+    e = launch_seg_fast(A, Wk.plan, false, s);
+  } else {
+    e = launch_segments_w<kEvalSum, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, Wk.st, cfg, s);
+  }
   if (e != cudaSuccess) return e;
   k_eval_finish<<<1, 1024, 0, s>>>(P, Wk, cfg);
   return cudaGetLastError();
@@ -393,7 +423,7 @@ cudaError_t launch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, 
 cudaError_t launch_evaluate_at(const Problem& P, const Work& Wk, bool want_seg, cudaStream_t s) {
   RunConfig cfg{};
   k_margins<<<(P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1, kVecThreads,
-              0, s>>>(P, Wk.y_eval, nullptr, 0, Wk.marg_eval, nullptr, nullptr);
+              0, s>>>(P, Wk.y_eval, nullptr, 0, Wk.marg_eval, nullptr, nullptr, nullptr);
   cudaError_t e = want_seg ? launch_segments_w<kEvalSeg, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, nullptr, cfg, s)
                            : launch_segments_w<kEvalSum, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, nullptr, cfg, s);
   if (e != cudaSuccess) return e;
@@ -401,7 +431,9 @@ cudaError_t launch_evaluate_at(const Problem& P, const Work& Wk, bool want_seg, 
   return cudaGetLastError();
 }
 
-int kernel_launches_per_iteration() { return 3; }
+int kernel_launches_per_iteration(const Work& Wk, const RunConfig& cfg) {
+  return (Wk.fast && cfg.batch_frac >= 1.0) ? 4 : 3;
+}
 int kernel_launches_per_eval() { return 3; }
 
 }  // namespace spfom

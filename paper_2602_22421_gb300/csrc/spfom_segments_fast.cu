@@ -1,0 +1,299 @@
+// Segment kernel for GB300's binary64 budget (binary64 results, binary32 decisions
+// with a certificate).
+//
+// GB300 executes binary64 arithmetic and every binary64 <-> binary32/int
+// conversion at about 1/60 of the binary32 rate, so a segment solve that
+// sorts and scans in binary64 is bound by that pipe, far from HBM speed. This
+// kernel keeps binary64 for the values that feed the dual step and takes the
+// discrete decision -- which products the optimal assortment holds -- in
+// binary32, with a certificate that the binary32 decision is the exact one.
+//
+// Decision (Section 4.1 inner problem, GAM form; build letters). With
+// a_j = m_j v_j, b_j = vt_j for the products with m_j > 0, the optimal
+// assortment is S* = {j : a_j > R* b_j} where R* = N(S*)/D(S*),
+// N(S) = sum_S a_j, D(S) = vt_0 + sum_S b_j (the greedy order of Lemma 1:
+// item j enters exactly when its key a_j / b_j exceeds the optimal rate).
+// Dinkelbach's iteration R <- N(S(R))/D(S(R)), S(R) = {a_j > R b_j}, started at
+// R = 0, shrinks S monotonically to such a fixed point, and every fixed point
+// is optimal: for any T, N(T) - R D(T) <= N(S) - R D(S) = 0. It runs in
+// binary32 on binary32 images of the inputs. The decision is certified when
+// every candidate clears the threshold by a relative margin
+// |a_j - R b_j| > 2^-16 (a_j + R b_j); the binary32 rounding of a_j, b_j, N, D
+// and R is below 5e-6 relative for consideration sets of up to 32 products,
+// so a certified set is the exact-arithmetic optimum S*. Segments that are not
+// certified (a near-tie, or an input outside binary32's normal range) repeat
+// the iteration in binary64.
+//
+// Values, in binary64: D* = vt_0 + sum_{S*} vt_j, N* = sum_{S*} m_j v_j,
+// q = lambda / D*, z = q N*, and the sales x_j = q v_j of the chosen products.
+//
+// Layout: W lanes per segment, P = 4 products per lane (lane r holds products
+// r, r + W, r + 2W, r + 3W of the segment's CSR slice, so each group reads its
+// slice with contiguous loads), and the group's binary64 reductions cost
+// log2(W) shuffle steps shared by 32/W segments per warp instruction.
+//
+// Sales aggregate: each block sums x_j per product in shared memory as
+// unsigned 64-bit fixed point (x * 2^F rounded; F fixed per instance so that
+// the arrival mass fits in 62 bits), which makes the sum exact and
+// independent of order, and writes its n partial sums out; k_reduce_products
+// folds them into the product sales. No contended global atomics.
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "spfom_internal.h"
+
+namespace spfom {
+
+namespace {
+
+constexpr float kCertDelta = 1.52587890625e-05f;  // 2^-16
+
+// binary32 image of a non-negative binary64, by dropping the low 29 mantissa
+// bits and rebiasing the exponent (no conversion instruction; relative error
+// below 2^-23). Zero maps to zero; ok is cleared for values outside binary32's
+// normal range and for negative values.
+__device__ __forceinline__ float f32_trunc(double d, bool& ok) {
+  const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+  if ((hi | lo) == 0u) return 0.f;
+  ok &= ((hi >> 20) - 897u) < 254u;
+  return __uint_as_float(__funnelshift_l(lo, hi, 3) - 0xC0000000u);
+}
+
+__device__ double block_sum_d(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double tot = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)((blockDim.x + 31) >> 5); ++k) tot += sh[k];
+  return tot;
+}
+
+template <int W, int P, bool SCATTER>
+__global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
+  extern __shared__ unsigned long long acc[];  // [n] product sales (fixed point) when SCATTER
+  __shared__ double sh[32];
+  if (A.st && A.st->converged) return;
+  const Problem& Pr = A.P;
+  if (SCATTER) {
+    for (int j = threadIdx.x; j < Pr.n; j += blockDim.x) acc[j] = 0ull;
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & (W - 1);
+  const int gbase = (threadIdx.x & 31) & ~(W - 1);
+  const unsigned gmask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << gbase);
+  const long long gpb = blockDim.x / W;
+  const long long ngroups = (long long)gridDim.x * gpb;
+  double zacc = 0.0;
+  int fallbacks = 0;
+  for (long long l = blockIdx.x * gpb + threadIdx.x / W; l < Pr.L; l += ngroups) {
+    const long long b = Pr.seg_ptr[l];
+    const int K = (int)(Pr.seg_ptr[l + 1] - b);
+    int jv[P];
+    double mv[P], vv[P], tv[P];
+    float af[P], bf[P];
+    unsigned cand = 0;
+    bool ok = true;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int k = lane + p * W;
+      jv[p] = 0;
+      mv[p] = vv[p] = tv[p] = 0.0;
+      af[p] = bf[p] = 0.f;
+      if (k < K) {
+        jv[p] = Pr.seg_prod[b + k];
+        vv[p] = Pr.v[b + k];
+        tv[p] = Pr.vt[b + k];
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      if (lane + p * W < K) {
+        mv[p] = A.marg[jv[p]];
+        if (__double_as_longlong(mv[p]) > 0) {  // m_j > 0
+          cand |= 1u << p;
+          af[p] = f32_trunc(mv[p], ok) * f32_trunc(vv[p], ok);
+          bf[p] = f32_trunc(tv[p], ok);
+        }
+      }
+    }
+    const double lam = Pr.lam[l], vt0 = Pr.vt0[l];
+    const float vt0f = f32_trunc(vt0, ok);
+    // Dinkelbach in binary32 from R = 0.
+    float R = 0.f;
+    unsigned sel = 0xffffffffu;  // no previous set
+    bool conv = false;
+    for (int it = 0; it < P * W + 2; ++it) {
+      unsigned s = 0;
+      float N = 0.f, D = 0.f;
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        if (((cand >> p) & 1u) && af[p] > R * bf[p]) {
+          s |= 1u << p;
+          N += af[p];
+          D += bf[p];
+        }
+      if (__all_sync(gmask, s == sel)) {
+        conv = true;
+        break;
+      }
+#pragma unroll
+      for (int o = W >> 1; o > 0; o >>= 1) {
+        N += __shfl_xor_sync(gmask, N, o, W);
+        D += __shfl_xor_sync(gmask, D, o, W);
+      }
+      R = N / (vt0f + D);
+      sel = s;
+    }
+    bool good = ok && conv;
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      if ((cand >> p) & 1u) {
+        const float a = af[p], c = R * bf[p];
+        if (!(fabsf(a - c) > kCertDelta * (a + c))) good = false;
+      }
+    unsigned S = sel;
+    if (!__all_sync(gmask, good)) {
+      // Not certified: the same iteration in binary64.
+      if (lane == 0) ++fallbacks;
+      double Rd = 0.0;
+      unsigned prev = 0xffffffffu;
+      for (int it = 0; it < P * W + 2; ++it) {
+        unsigned s = 0;
+        double N = 0.0, D = 0.0;
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+          if ((cand >> p) & 1u) {
+            const double a = mv[p] * vv[p];
+            if (a > Rd * tv[p]) {
+              s |= 1u << p;
+              N += a;
+              D += tv[p];
+            }
+          }
+        if (__all_sync(gmask, s == prev)) break;
+#pragma unroll
+        for (int o = W >> 1; o > 0; o >>= 1) {
+          N += __shfl_xor_sync(gmask, N, o, W);
+          D += __shfl_xor_sync(gmask, D, o, W);
+        }
+        Rd = N / (vt0 + D);
+        prev = s;
+      }
+      S = prev;
+    }
+    // binary64 values of the chosen assortment.
+    double Nl = 0.0, Dl = 0.0;
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      if ((S >> p) & 1u) {
+        Dl += tv[p];
+        Nl = fma(mv[p], vv[p], Nl);
+      }
+#pragma unroll
+    for (int o = W >> 1; o > 0; o >>= 1) {
+      Nl += __shfl_xor_sync(gmask, Nl, o, W);
+      Dl += __shfl_xor_sync(gmask, Dl, o, W);
+    }
+    const double q = lam / (vt0 + Dl);
+    if (lane == 0) zacc += q * Nl;
+    if (SCATTER) {
+      const double qs = q * A.fx_scale;
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        if ((S >> p) & 1u) atomicAdd(acc + jv[p], __double2ull_rn(qs * vv[p]));
+    }
+  }
+  const double tot = block_sum_d(zacc, sh);
+  if (threadIdx.x == 0) A.zpart[blockIdx.x] = tot;
+  if (fallbacks && A.fallbacks) atomicAdd(A.fallbacks, (unsigned long long)fallbacks);
+  if (SCATTER) {
+    __syncthreads();
+    unsigned long long* dst = A.part + (size_t)blockIdx.x * Pr.n;
+    for (int j = threadIdx.x; j < Pr.n; j += blockDim.x) dst[j] = acc[j];
+  }
+}
+
+// s_fx[j] += sum of one chunk of the per-block partial sums (grid.y chunks).
+__global__ void k_reduce_products(int n, int nparts, const unsigned long long* __restrict__ part,
+                                  unsigned long long* __restrict__ s_fx, const DevState* st) {
+  if (st->converged) return;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const int per = (nparts + gridDim.y - 1) / gridDim.y;
+  const int b0 = blockIdx.y * per, b1 = min(nparts, b0 + per);
+  unsigned long long acc = 0ull;
+#pragma unroll 4
+  for (int b = b0; b < b1; ++b) acc += __ldcg(part + (size_t)b * n + j);
+  if (acc) atomicAdd(s_fx + j, acc);
+}
+
+template <int W, bool SCATTER>
+void set_smem(int bytes) {
+  cudaFuncSetAttribute(k_seg_fast<W, 4, SCATTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <bool SCATTER>
+cudaError_t launch_w(const FastArgs& A, int W, int grid, int smem, cudaStream_t s) {
+  switch (W) {
+    case 1: k_seg_fast<1, 4, SCATTER><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 2: k_seg_fast<2, 4, SCATTER><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 4: k_seg_fast<4, 4, SCATTER><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 8: k_seg_fast<8, 4, SCATTER><<<grid, kFastThreads, smem, s>>>(A); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <bool SCATTER>
+int occupancy(int W, int smem) {
+  int nb = 0;
+  switch (W) {
+    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_fast<1, 4, SCATTER>, kFastThreads, smem); break;
+    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_fast<2, 4, SCATTER>, kFastThreads, smem); break;
+    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_fast<4, 4, SCATTER>, kFastThreads, smem); break;
+    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_fast<8, 4, SCATTER>, kFastThreads, smem); break;
+    default: break;
+  }
+  return nb;
+}
+
+}  // namespace
+
+bool fast_plan(int n, int kmax, int sms, FastPlan* plan) {
+  if (kmax > 32) return false;
+  const int smem = n * (int)sizeof(unsigned long long);
+  if (smem > kFastMaxSmem) return false;
+  int W = 1;
+  while (W * 4 < kmax) W <<= 1;
+  set_smem<1, true>(smem);
+  set_smem<2, true>(smem);
+  set_smem<4, true>(smem);
+  set_smem<8, true>(smem);
+  const int nb = occupancy<true>(W, smem);
+  const int nbe = occupancy<false>(W, 0);
+  if (nb <= 0 || nbe <= 0) return false;
+  plan->W = W;
+  plan->smem = smem;
+  plan->grid = nb * sms;
+  plan->grid_eval = nbe * sms;
+  plan->reduce_chunks = 16;
+  return true;
+}
+
+cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s) {
+  return scatter ? launch_w<true>(A, plan.W, plan.grid, plan.smem, s)
+                 : launch_w<false>(A, plan.W, plan.grid_eval, 0, s);
+}
+
+cudaError_t launch_reduce_products(const Problem& P, const FastPlan& plan, const unsigned long long* part,
+                                   unsigned long long* s_fx, const DevState* st, cudaStream_t s) {
+  if (P.n <= 0) return cudaSuccess;
+  dim3 grid((P.n + 255) / 256, plan.reduce_chunks);
+  k_reduce_products<<<grid, 256, 0, s>>>(P.n, plan.grid, part, s_fx, st);
+  return cudaGetLastError();
+}
+
+}  // namespace spfom

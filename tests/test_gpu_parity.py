@@ -62,13 +62,15 @@ def mid_small():
 CASES = {"tiny_mnl": lambda: tiny_mnl(0), "small_gam": small_gam, "edge": edge_instance, "mid_small": mid_small}
 
 
+@pytest.mark.parametrize("path", [0, 1], ids=["certified", "general"])
 @pytest.mark.parametrize("name", list(CASES))
-def test_iterates_track_oracle_200(name):
+def test_iterates_track_oracle_200(name, path):
     inst = CASES[name]()
     o = Oracle(inst)
     run = o.run(OracleParams())
     done = 0
-    with Solver(inst) as s:
+    with Solver(inst, path=path) as s:
+        assert s.stats()["fast_path"] == (1 if path == 0 else 0)
         for t in (1, 2, 5, 63, 64, 65, 128, 129, 200):
             while done < t:
                 marg_prev = o.margins(run.y)  # margins the coming iteration uses
@@ -94,6 +96,31 @@ def test_iterates_track_oracle_200(name):
                     assert st[k] == pytest.approx(ost[k], rel=1e-5, abs=1e-12), k
                 assert st["dual_avg"] == pytest.approx(ost["dual_avg"], rel=ITER_RTOL)
                 assert st["primal_avg"] == pytest.approx(ost["primal_avg"], rel=ITER_RTOL)
+        # binary64 redos stay rare (each iteration solves L segments, each evaluation L more)
+        assert st["fallback_segments"] <= max(5, 1e-3 * inst.L * (200 + 3))
+
+
+def tie_instance():
+    """Three MNL segments over products {0, 1} with v = (1/2, 1/4), v0 = 1 and
+    prices (3, 1): at y = 0 adding product 1 leaves N/D = 1 unchanged, an exact
+    tie that no binary32 certificate can settle."""
+    from instances import Instance
+    return Instance(n=2, m=1, L=3, r=np.array([3.0, 1.0]), c=np.array([1e30]),
+                    a_ptr=np.array([0, 1, 2], np.int32), a_idx=np.array([0, 0], np.int32), a_val=None,
+                    seg_ptr=np.array([0, 2, 4, 6], np.int64), seg_prod=np.array([0, 1] * 3, np.int32),
+                    v=np.array([0.5, 0.25] * 3), w=None, lam=np.ones(3), v0=np.ones(3), name="tie")
+
+
+def test_exact_tie_falls_back_to_binary64_and_keeps_smallest_set():
+    inst = tie_instance()
+    run = Oracle(inst).run(OracleParams(eval_every=0))
+    run.step(1)
+    np.testing.assert_array_equal(run.s, [1.0, 0.0])
+    with Solver(inst, eval_every=0) as s:
+        st = s.step(1)
+        assert st["fast_path"] == 1 and st["fallback_segments"] == 3
+        np.testing.assert_allclose(s.vector(5), run.s, rtol=1e-15, atol=1e-15)
+        assert st["z_sum"] == pytest.approx(3.0, rel=1e-15)
 
 
 def st_iters(s):
