@@ -82,14 +82,20 @@ class Instance:
 def _distinct_sorted(rng: np.random.Generator, n: int, K: np.ndarray) -> np.ndarray:
     """For each row l draw K[l] distinct uniform ids in [0, n), ascending.
 
-    Rows with a repeated id are redrawn whole, which leaves every K-subset
-    equally likely. Returns the rows concatenated."""
+    Sparse rows (4 * max K <= n) draw K ids and redraw a row whole when it
+    repeats an id; dense rows rank n uniform keys and keep the first K. Both
+    make every K-subset equally likely. Returns the rows concatenated."""
     L = K.size
     kmax = int(K.max()) if L else 0
     if kmax > n:
         raise ValueError("consideration set larger than the product count")
-    out = np.empty((L, kmax), dtype=np.int64)
     col = np.arange(kmax)
+    if 4 * kmax > n:
+        out = np.argsort(rng.random((L, n)), axis=1)[:, :kmax]
+        out = np.where(col[None, :] < K[:, None], out, n)
+        out.sort(axis=1)
+        return out[col[None, :] < K[:, None]].astype(np.int32)
+    out = np.empty((L, kmax), dtype=np.int64)
     todo = np.arange(L)
     while todo.size:
         cand = rng.integers(0, n, size=(todo.size, kmax))
