@@ -31,7 +31,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "time-to-1e-4 KKT (s) & SPFOM iters/s: GPU plain vs FP32/batched/learned"
-KERNEL_SRC = os.path.join(ROOT, "paper_2602_22421_gb300", "csrc", "spfom_kernels.cu")
+CSRC = os.path.join(ROOT, "paper_2602_22421_gb300", "csrc")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 BYTES_PER_NNZ = 20      # seg_prod int32 + v f64 + (v - w) f64
 BYTES_PER_SEGMENT = 24  # seg_ptr int64 + lambda f64 + (v0 + sum w) f64
@@ -132,14 +132,16 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_traffic(nnz):
-    """DRAM bytes per segment-kernel launch from the committed ncu summary, if
-    it was taken on the current kernel source; scaled by nonzeros."""
+def kernel_traffic(kernel, src, nnz):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel source; scaled by nonzeros."""
     if not os.path.exists(TRAFFIC):
         return None, None
     with open(TRAFFIC) as f:
-        d = json.load(f)
-    sha = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+        d = json.load(f).get(kernel)
+    if not d:
+        return None, None
+    sha = hashlib.sha256(open(os.path.join(CSRC, src), "rb").read()).hexdigest()
     if d.get("kernel_source_sha256") != sha:
         return None, "kernel changed since the ncu capture"
     return d["dram_bytes_per_launch"] * nnz / d["nnz"], d.get("capture")
@@ -246,11 +248,17 @@ def run_gpu(args):
         alg = BYTES_PER_NNZ * inst.nnz + BYTES_PER_SEGMENT * inst.L
         peak, src = measured_peaks()
         achieved = alg / per_launch / 1e9
-        traffic, cap = kernel_traffic(inst.nnz)
-        roof = {"bound": "hbm", "kernel": "k_segments (iterate)", "achieved": achieved, "peak": peak,
+        if pst["fast_path"]:
+            kname, ksrc = "k_seg_fast", "spfom_segments_fast.cu"
+        else:
+            kname, ksrc = "k_segments", "spfom_kernels.cu"
+        traffic, cap = kernel_traffic(kname, ksrc, inst.nnz)
+        solves = (2 + min(args.steps, 10)) * ips * inst.L
+        roof = {"bound": "hbm", "kernel": kname + " (iterate)", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                 "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch * 1e3,
-                "peak_source": f"{src} hbm_gbs", "traffic_note": cap}
+                "peak_source": f"{src} hbm_gbs", "traffic_note": cap,
+                "binary64_redo_fraction": pst["fallback_segments"] / solves}
     # --- time to KKT <= 1e-4 -------------------------------------------------
     ttk = None
     if not args.no_solve:

@@ -383,6 +383,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       W.fast = true;
       W.plan = plan;
       W.fx_scale = std::ldexp(1.0, F);
+      W.fx_bits = F;
       W.inv_fx_scale = std::ldexp(1.0, -F);
       W.zparts_iter = plan.grid;
       W.zparts_eval = plan.grid_eval;

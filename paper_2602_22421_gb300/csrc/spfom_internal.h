@@ -82,6 +82,7 @@ struct Work {
   unsigned long long* s_fx;       // [n] fixed-point product sales
   unsigned long long* fallbacks;  // running count of segments decided in binary64
   double fx_scale, inv_fx_scale;  // 2^F and 2^-F
+  int fx_bits;                    // F
 };
 
 struct FastArgs {
@@ -92,6 +93,7 @@ struct FastArgs {
   const DevState* st;
   double fx_scale;
   unsigned long long* fallbacks;
+  int fx_bits;  // F of the fixed-point scale 2^F
 };
 
 struct RunConfig {

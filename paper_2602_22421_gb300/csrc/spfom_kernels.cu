@@ -253,15 +253,19 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
     last = (prev == gridDim.x - 1);
   }
   __syncthreads();
-  if (!last || threadIdx.x != 0) return;
-  // Last block: fold the partial sums in block order.
+  if (!last) return;
+  // Last block: fold the partial sums (strided over the block, then a tree).
   __threadfence();
   double zs = 0.0, cys = 0.0, Ps = 0.0;
-  for (int b = 0; b < Wk.zparts_iter; ++b) zs += __ldcg(Wk.zpart + b);
-  for (int b = 0; b < (int)gridDim.x; ++b) {
+  for (int b = threadIdx.x; b < Wk.zparts_iter; b += blockDim.x) zs += __ldcg(Wk.zpart + b);
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
     cys += __ldcg(Wk.cypart + b);
     Ps += __ldcg(Wk.Ppart + b);
   }
+  zs = block_sum(zs, sh);
+  cys = block_sum(cys, sh);
+  Ps = block_sum(Ps, sh);
+  if (threadIdx.x != 0) return;
   st->z_sum = full ? zs : CUDART_NAN;
   st->dual_iter = full ? cys + zs : CUDART_NAN;
   st->P = Ps;
@@ -289,8 +293,8 @@ __global__ void __launch_bounds__(1024) k_eval_finish(Problem P, Work Wk, RunCon
     c2 += __dmul_rn(c, c);
   }
   double zs = 0.0;
-  if (threadIdx.x == 0)
-    for (int b = 0; b < Wk.zparts_eval; ++b) zs += Wk.zpart_eval[b];
+  for (int b = threadIdx.x; b < Wk.zparts_eval; b += blockDim.x) zs += Wk.zpart_eval[b];
+  zs = block_sum(zs, sh);
   const double tcy = block_sum(cy, sh);
   const double tover = block_sum(over2, sh);
   const double tc2 = block_sum(c2, sh);
@@ -334,11 +338,10 @@ __global__ void __launch_bounds__(1024) k_evaluate_finish(Problem P, Work Wk) {
   for (int i = threadIdx.x; i < P.m; i += blockDim.x)
     if (Wk.y_eval[i] != 0.0) cy += __dmul_rn(P.c[i], Wk.y_eval[i]);
   const double tcy = block_sum(cy, sh);
-  if (threadIdx.x == 0) {
-    double zs = 0.0;
-    for (int b = 0; b < Wk.seg_blocks; ++b) zs += Wk.zpart_eval[b];
-    Wk.st->eval_out = tcy + zs;
-  }
+  double zs = 0.0;
+  for (int b = threadIdx.x; b < Wk.seg_blocks; b += blockDim.x) zs += Wk.zpart_eval[b];
+  zs = block_sum(zs, sh);
+  if (threadIdx.x == 0) Wk.st->eval_out = tcy + zs;
 }
 
 template <int MODE, bool SAMPLED>
@@ -389,7 +392,7 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
   if (seg_begin) cudaEventRecord(seg_begin, s);
   cudaError_t e;
   if (fast) {
-    FastArgs A{P, Wk.marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks};
+    FastArgs A{P, Wk.marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits};
     e = launch_seg_fast(A, Wk.plan, true, s);
   } else {
     e = sampled ? launch_segments_w<kIterate, true>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s)
@@ -410,7 +413,7 @@ cudaError_t launch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, 
   k_margins<<<gn, kVecThreads, 0, s>>>(P, nullptr, Wk.sum_y, 1, Wk.marg_eval, nullptr, nullptr, Wk.st);
   cudaError_t e;
   if (Wk.fast) {
-    FastArgs A{P, Wk.marg_eval, nullptr, Wk.zpart_eval, Wk.st, Wk.fx_scale, Wk.fallbacks};
+    FastArgs A{P, Wk.marg_eval, nullptr, Wk.zpart_eval, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits};
     e = launch_seg_fast(A, Wk.plan, false, s);
   } else {
     e = launch_segments_w<kEvalSum, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, Wk.st, cfg, s);

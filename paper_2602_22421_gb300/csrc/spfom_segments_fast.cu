@@ -59,6 +59,44 @@ __device__ __forceinline__ float f32_trunc(double d, bool& ok) {
   return __uint_as_float(__funnelshift_l(lo, hi, 3) - 0xC0000000u);
 }
 
+// round(a * b * 2^F) for positive normal binary64 a, b with a * b * 2^F < 2^62,
+// from the 53-bit significands on the integer unit (one rounding, of the exact
+// product). a = ma 2^(ea - 1075), b = mb 2^(eb - 1075) with biased exponents ea, eb.
+__device__ __forceinline__ unsigned long long fixed_product(double a, double b, int F) {
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
+  const unsigned long long ma = (ua & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const unsigned long long mb = (ub & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const int sh = 2150 - F - (int)(ua >> 52) - (int)(ub >> 52);  // a b 2^F = ma mb / 2^sh
+  if (sh < 43 || sh > 126) return 0ull;  // sh < 43 cannot occur below 2^62; sh > 126 rounds to 0
+  unsigned long long lo = ma * mb, hi = __umul64hi(ma, mb);
+  if (sh <= 64) {
+    const unsigned long long half = 1ull << (sh - 1);
+    lo += half;
+    hi += (lo < half) ? 1ull : 0ull;
+  } else {
+    hi += 1ull << (sh - 65);
+  }
+  return sh < 64 ? (hi << (64 - sh)) | (lo >> sh) : (hi >> (sh - 64));
+}
+
+// lam / d for positive normal d: binary32 reciprocal seed (24 bits, from the
+// integer image of d), two binary64 Newton steps r <- r + r (1 - d r), then one
+// product (a few ulps from the correctly rounded quotient).
+__device__ __forceinline__ double quotient(double lam, double d) {
+  bool ok = true;
+  const float r32 = __frcp_rn(f32_trunc(d, ok));
+  const unsigned rb = __float_as_uint(r32);
+  // widen the binary32 seed to binary64: rebias the exponent, shift the significand
+  double r = __hiloint2double((int)(((rb >> 23) + 896u) << 20 | ((rb & 0x7FFFFFu) >> 3)), (int)(rb << 29));
+  if (!ok) r = 1.0 / d;
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  return lam * r;
+}
+
 __device__ double block_sum_d(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -197,13 +235,12 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
       Nl += __shfl_xor_sync(gmask, Nl, o, W);
       Dl += __shfl_xor_sync(gmask, Dl, o, W);
     }
-    const double q = lam / (vt0 + Dl);
+    const double q = quotient(lam, vt0 + Dl);
     if (lane == 0) zacc += q * Nl;
     if (SCATTER) {
-      const double qs = q * A.fx_scale;
 #pragma unroll
       for (int p = 0; p < P; ++p)
-        if ((S >> p) & 1u) atomicAdd(acc + jv[p], __double2ull_rn(qs * vv[p]));
+        if ((S >> p) & 1u) atomicAdd(acc + jv[p], fixed_product(q, vv[p], A.fx_bits));
     }
   }
   const double tot = block_sum_d(zacc, sh);
