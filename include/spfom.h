@@ -195,6 +195,53 @@ const char* spfom_last_error(const spfom_ctx* ctx);
 /* Name of a status code (never NULL). */
 const char* spfom_status_string(spfom_status s);
 
+/* ---- Allocation-free product sales --------------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that
+ * cannot call cudaMalloc: code running inside a memory pool it does not own,
+ * embedders whose device allocator is reserved for their own tensors, or
+ * services that must not allocate device memory once they are up. Everything
+ * else in this library allocates through its ctx.
+ *
+ * spfom_sales_noalloc computes what the segment pass of one iteration
+ * computes -- every segment's exact best response at the given margins, the
+ * sales summed per product and the sum of the segment values z_l -- from
+ * device arrays the caller owns, into device buffers the caller owns. It
+ * allocates nothing: its scratch is a set of fixed arrays inside the library
+ * (SPFOM_NOALLOC_MAX_PRODUCTS doubles of sales plus 8 KiB), which every GPU
+ * that loads the library keeps until the process exits.
+ *  - The first call on a device (with that device current) looks up the
+ *    scratch arrays' device addresses; make that first call before capturing
+ *    any CUDA stream on that device.
+ *  - Work is enqueued on `stream` (NULL: the legacy default stream) and the
+ *    call returns without waiting for it.
+ *  - All calls share the scratch arrays, and each leaves its results there;
+ *    every call clears what it accumulates before using it. Calls whose work
+ *    overlaps on the GPU (other streams, other host threads) race on the
+ *    arrays and give wrong results: serialise them.
+ *  - Limits: n <= SPFOM_NOALLOC_MAX_PRODUCTS and max_set_size <= 32, else
+ *    EINVAL (nothing launched). A segment larger than max_set_size is left
+ *    out and *z_sum is set to NaN.
+ *  - No input validation beyond sizes: ids must lie in [0, n), v > 0,
+ *    0 <= w <= v, v0 > 0, lam >= 0, as for spfom_load_instance.
+ * Outputs: sales [n] (device), z_sum [1] (device). ECUDA if the scratch
+ * cannot be located or a launch fails. */
+#define SPFOM_NOALLOC_MAX_PRODUCTS 131072
+
+typedef struct {
+  int32_t n;                 /* products */
+  int32_t max_set_size;      /* upper bound on every consideration-set size */
+  int64_t L;                 /* segments */
+  const int64_t* seg_ptr;    /* device [L+1] */
+  const int32_t* seg_prod;   /* device [seg_ptr[L]] */
+  const double* v;           /* device [seg_ptr[L]] nominal attractions */
+  const double* w;           /* device [seg_ptr[L]] shadow attractions, or NULL (MNL) */
+  const double* lam;         /* device [L] */
+  const double* v0;          /* device [L] */
+} spfom_device_segments;
+
+spfom_status spfom_sales_noalloc(const spfom_device_segments* seg, const double* margins, double* sales,
+                                 double* z_sum, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

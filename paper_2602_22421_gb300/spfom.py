@@ -22,7 +22,7 @@ VEC_Y, VEC_YBAR, VEC_SUM_Y, VEC_SUM_G, VEC_G, VEC_S, VEC_MARGINS = range(7)
 # Every function include/spfom.h declares.
 EXPORTS = ("spfom_default_params", "spfom_create", "spfom_load_instance", "spfom_reset", "spfom_step",
            "spfom_solve", "spfom_vector", "spfom_duals", "spfom_evaluate", "spfom_get_stats", "spfom_destroy",
-           "spfom_last_error", "spfom_status_string")
+           "spfom_last_error", "spfom_status_string", "spfom_sales_noalloc")
 
 _f64p = C.POINTER(C.c_double)
 _i32p = C.POINTER(C.c_int32)
@@ -41,6 +41,15 @@ class InstanceC(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("L", C.c_int64), ("r", _f64p), ("c", _f64p),
                 ("a_ptr", _i32p), ("a_idx", _i32p), ("a_val", _f64p), ("seg_ptr", _i64p), ("seg_prod", _i32p),
                 ("v", _f64p), ("w", _f64p), ("lam", _f64p), ("v0", _f64p)]
+
+
+class DeviceSegments(C.Structure):
+    _fields_ = [("n", C.c_int32), ("max_set_size", C.c_int32), ("L", C.c_int64), ("seg_ptr", C.c_void_p),
+                ("seg_prod", C.c_void_p), ("v", C.c_void_p), ("w", C.c_void_p), ("lam", C.c_void_p),
+                ("v0", C.c_void_p)]
+
+
+NOALLOC_MAX_PRODUCTS = 131072
 
 
 class Stats(C.Structure):
@@ -91,6 +100,8 @@ def lib():
         h.spfom_last_error.restype = C.c_char_p
         h.spfom_status_string.argtypes = [C.c_int]
         h.spfom_status_string.restype = C.c_char_p
+        h.spfom_sales_noalloc.argtypes = [P(DeviceSegments), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        h.spfom_sales_noalloc.restype = C.c_int
         for f in ("spfom_create", "spfom_load_instance", "spfom_reset", "spfom_step", "spfom_solve", "spfom_vector",
                   "spfom_duals", "spfom_evaluate", "spfom_get_stats"):
             getattr(h, f).restype = C.c_int
@@ -110,6 +121,13 @@ def default_params(**kw) -> Params:
             raise KeyError(k)
         setattr(p, k, v)
     return p
+
+
+def sales_noalloc(n, L, max_set_size, seg_ptr, seg_prod, v, w, lam, v0, margins, sales, z_sum, stream=None) -> int:
+    """spfom_sales_noalloc on device pointers (ints, e.g. torch ``data_ptr()``);
+    returns the status code. Allocates nothing."""
+    d = DeviceSegments(n, max_set_size, L, seg_ptr, seg_prod, v, w or None, lam, v0)
+    return lib().spfom_sales_noalloc(C.byref(d), margins, sales, z_sum, stream)
 
 
 def _current_stream():

@@ -85,3 +85,5 @@ def test_struct_layouts_match_header():
     assert fields("spfom_params") == [f for f, _ in b.Params._fields_]
     assert fields("spfom_instance") == [f for f, _ in b.InstanceC._fields_]
     assert fields("spfom_stats") == [f for f, _ in b.Stats._fields_]
+    assert fields("spfom_device_segments") == [f for f, _ in b.DeviceSegments._fields_]
+    assert re.search(r"#define SPFOM_NOALLOC_MAX_PRODUCTS (\d+)", text).group(1) == str(b.NOALLOC_MAX_PRODUCTS)
