@@ -35,6 +35,8 @@ CSRC = os.path.join(ROOT, "paper_2602_22421_gb300", "csrc")
 TRAFFIC = os.path.join(ROOT, "profiles", "traffic.json")
 BYTES_PER_NNZ = 20      # seg_prod int32 + v f64 + (v - w) f64
 BYTES_PER_SEGMENT = 24  # seg_ptr int64 + lambda f64 + (v0 + sum w) f64
+BYTES_PER_NNZ_F32 = 12      # seg_prod int32 + v f32 + (v - w) f32
+BYTES_PER_SEGMENT_F32 = 16  # seg_ptr int64 + lambda f32 + (v0 + sum w) f32
 
 
 def parse():
@@ -220,57 +222,72 @@ def run_gpu(args):
     inst = workload(args, seed=1 + rank)
     ips = args.iters_per_step
     stream = torch.cuda.Stream()  # a real stream handle: the ctx runs on it, the events bracket it
-    # --- timed throughput: iterations never stop early (kkt_tol = 0) -------
-    s = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0)
-    s.step(args.warmup * ips)
-    barrier()
-    clk = Clocks(local) if rank == 0 else None
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    e0.record(stream)
-    st = s.step(args.steps * ips)
-    e1.record(stream)
-    barrier()
-    clocks = clk.stop() if clk else None
-    ms = allmax(e0.elapsed_time(e1))
-    total_iters = ws * args.steps * ips
-    value = total_iters / (ms * 1e-3)
-    launches = st["kernel_launches"]
-    s.close()
-    # --- roofline of the segment kernel (event pair around every launch) ----
-    roof = None
-    if rank == 0:
-        sp = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, profile=1)
-        sp.step(2 * ips)
-        pst = sp.step(min(args.steps, 10) * ips)
-        sp.close()
-        per_launch = pst["seg_kernel_seconds"] / max(1, pst["seg_kernel_launches"])
-        alg = BYTES_PER_NNZ * inst.nnz + BYTES_PER_SEGMENT * inst.L
-        peak, src = measured_peaks()
-        achieved = alg / per_launch / 1e9
-        if pst["fast_path"]:
-            kname, ksrc = "k_seg_fast", "spfom_segments_fast.cu"
-        else:
-            kname, ksrc = "k_segments", "spfom_kernels.cu"
-        traffic, cap = kernel_traffic(kname, ksrc, inst.nnz)
-        solves = (2 + min(args.steps, 10)) * ips * inst.L
-        roof = {"bound": "hbm", "kernel": kname + " (iterate)", "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-                "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch * 1e3,
-                "peak_source": f"{src} hbm_gbs", "traffic_note": cap,
-                "binary64_redo_fraction": pst["fallback_segments"] / solves}
-    # --- time to KKT <= 1e-4 -------------------------------------------------
-    ttk = None
-    if not args.no_solve:
-        sv = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=1e-4, max_iters=20000)
+
+    def measure(precision, with_clocks):
+        """Timed iterations (kkt_tol = 0: nothing is skipped), then a profiled
+        pass for the segment kernel's roofline, then a solve to KKT <= 1e-4."""
+        s = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, precision=precision)
+        s.step(args.warmup * ips)
         barrier()
-        w0 = time.perf_counter()
-        sst = sv.solve()
-        wall = time.perf_counter() - w0
-        ttk = {"seconds_device": sst["seconds"], "seconds_wall": wall, "iterations": sst["iters"],
-               "converged": bool(sst["converged"]), "kkt": sst["kkt"], "dual_obj": sst["dual_avg"],
-               "primal_obj": sst["primal_avg"], "restarts": sst["restarts"]}
-        sv.close()
+        clk = Clocks(local) if (rank == 0 and with_clocks) else None
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        st = s.step(args.steps * ips)
+        e1.record(stream)
+        barrier()
+        clocks = clk.stop() if clk else None
+        ms = allmax(e0.elapsed_time(e1))
+        s.close()
+        out = {"value": ws * args.steps * ips / (ms * 1e-3), "ms": ms, "launches": st["kernel_launches"],
+               "clocks": clocks, "iter_precision": st["iter_precision"]}
+        if rank == 0:
+            sp = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, profile=1, precision=precision)
+            sp.step(2 * ips)
+            pst = sp.step(min(args.steps, 10) * ips)
+            sp.close()
+            per_launch = pst["seg_kernel_seconds"] / max(1, pst["seg_kernel_launches"])
+            if precision == 32:
+                alg = BYTES_PER_NNZ_F32 * inst.nnz + BYTES_PER_SEGMENT_F32 * inst.L
+                kname, ksrc = "k_seg_f32", "spfom_segments_fast.cu"
+            else:
+                alg = BYTES_PER_NNZ * inst.nnz + BYTES_PER_SEGMENT * inst.L
+                kname, ksrc = ("k_seg_fast", "spfom_segments_fast.cu") if pst["fast_path"] else \
+                    ("k_segments", "spfom_kernels.cu")
+            peak, src = measured_peaks()
+            achieved = alg / per_launch / 1e9
+            traffic, cap = kernel_traffic(kname, ksrc, inst.nnz)
+            solves = (2 + min(args.steps, 10)) * ips * inst.L
+            out["roofline"] = {"bound": "hbm", "kernel": kname + " (iterate)", "achieved": achieved, "peak": peak,
+                               "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                               "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch * 1e3,
+                               "peak_source": f"{src} hbm_gbs", "traffic_note": cap,
+                               "binary64_redo_fraction": pst["fallback_segments"] / solves}
+        if not args.no_solve:
+            sv = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=1e-4, max_iters=20000,
+                        precision=precision)
+            barrier()
+            w0 = time.perf_counter()
+            sst = sv.solve()
+            wall = time.perf_counter() - w0
+            out["ttk"] = {"seconds_device": sst["seconds"], "seconds_wall": wall, "iterations": sst["iters"],
+                          "converged": bool(sst["converged"]), "kkt": sst["kkt"], "dual_obj": sst["dual_avg"],
+                          "primal_obj": sst["primal_avg"], "restarts": sst["restarts"],
+                          "final_iter_precision": sst["iter_precision"]}
+            sv.close()
+        return out
+
+    m64 = measure(64, True)
+    m32 = measure(32, False)
+    value, ms, launches, clocks = m64["value"], m64["ms"], m64["launches"], m64["clocks"]
+    roof = m64.get("roofline")
+    ttk = m64.get("ttk")
+    fp32 = {"value": m32["value"], "unit": "iters/s", "ms_per_step": m32["ms"] / args.steps,
+            "roofline": m32.get("roofline"), "time_to_kkt_1e-4": m32.get("ttk"), "gpu_launches": m32["launches"],
+            "dtype": "f32 segment solves, f64 dual step / residuals / evaluations"}
+    if ttk and m32.get("ttk"):
+        fp32["objective_rel_diff_vs_f64"] = abs(m32["ttk"]["dual_obj"] / ttk["dual_obj"] - 1)
+        fp32["speedup_time_to_kkt_vs_f64"] = ttk["seconds_device"] / m32["ttk"]["seconds_device"]
     # --- end to end through host buffers -------------------------------------
     e2e = None
     if not args.no_e2e:
@@ -300,7 +317,7 @@ def run_gpu(args):
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
                "config": config_of(inst, args), "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-               "roofline": roof, "cpu_baseline": cpu, "time_to_kkt_1e-4": ttk}
+               "roofline": roof, "cpu_baseline": cpu, "time_to_kkt_1e-4": ttk, "fp32_bulk": fp32}
         print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()

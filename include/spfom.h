@@ -51,7 +51,13 @@ typedef struct spfom_ctx spfom_ctx;
 
 /* Iteration parameters. spfom_default_params() fills the defaults noted. */
 typedef struct {
-  int32_t precision;         /* 64 (default): the iteration in binary64 */
+  int32_t precision;         /* 64 (default): the iteration in binary64 (binary32 only for
+                                certified discrete decisions). 32: binary32 bulk iteration -- the
+                                segment solves and sales in binary32 from binary32 copies of the
+                                attractions (12 B per nonzero), while margins, the dual step,
+                                averages, KKT residuals, restart test and evaluations stay in
+                                binary64; needs consideration sets of <= 32 products and
+                                attractions, rates and v0 + sum w within binary32's normal range */
   double tau;                /* dual step size; <= 0 (default): tau0 * mean(r) / mean(c) */
   double tau0;               /* 0.1: the step of the Section 4.5 experiments, rescaled */
   double mu;                 /* 0: step of Algorithm 2; > 0: eq. stronglycvxupdate */
@@ -69,8 +75,11 @@ typedef struct {
   int32_t profile;           /* 0; nonzero: time every segment-kernel launch of spfom_step with
                                 a CUDA event pair (spfom_stats.seg_kernel_seconds) */
   int32_t path;              /* 0 (default): the certified-decision segment kernel whenever the
-                                instance allows it (sets of <= 32 products, n <= 25600, full
-                                batch), else the general kernel; 1: always the general kernel */
+                                instance allows it (sets of <= 32 products, full batch), else the
+                                general kernel; 1: always the general kernel */
+  int32_t polish;            /* precision 32 only, 1 (default): once a binary64 evaluation finds
+                                KKT <= kkt_tol, spfom_solve continues with binary64 iterations
+                                until the next evaluation confirms it; 0: stop at the first */
   void* stream;              /* cudaStream_t to run on; NULL (default): the ctx creates one */
 } spfom_params;
 
@@ -124,7 +133,7 @@ typedef struct {
   int64_t fallback_segments;   /* segment solves since the last reset whose binary32 decision
                                   was not certified and was redone in binary64 */
   int32_t fast_path;           /* 1 when the certified-decision kernel runs the iterations */
-  int32_t pad2_;
+  int32_t iter_precision;      /* 32 or 64: precision of the last iteration's segment pass */
 } spfom_stats;
 
 /* Which vector spfom_vector() returns. */

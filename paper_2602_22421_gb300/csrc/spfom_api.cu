@@ -39,6 +39,7 @@ struct spfom_ctx {
   std::vector<cudaEvent_t> prof_ev;  // event pairs of profiled segment launches
   int sms = 0;
   unsigned long long fallback_host = 0;
+  bool polishing = false;  // precision 32: binary64 iterations after the first converged evaluation
 };
 
 namespace {
@@ -176,6 +177,8 @@ spfom_status init_state(spfom_ctx* ctx, const double* y0) {
   SPFOM_CUDA(ctx, cudaMemcpyAsync(W.st, &st, sizeof st, cudaMemcpyHostToDevice, ctx->stream));
   SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->host_t = 0;
+  ctx->polishing = false;
+  ctx->cfg.f32 = ctx->p.precision == 32 ? 1 : 0;
   return SPFOM_OK;
 }
 
@@ -184,6 +187,7 @@ void fill_stats(const spfom_ctx* ctx, const DevState& st, double secs, spfom_sta
   spfom_stats s{};
   s.fallback_segments = (long long)ctx->fallback_host;
   s.fast_path = (ctx->W.fast && ctx->cfg.batch_frac >= 1.0) ? 1 : 0;
+  s.iter_precision = (s.fast_path && ctx->cfg.f32) ? 32 : 64;
   s.iters = st.t;
   s.restarts = st.restarts;
   s.evals = st.evals;
@@ -233,6 +237,7 @@ void spfom_default_params(spfom_params* p) {
   p->kkt_tol = 1e-4;
   p->max_iters = 100000;
   p->device = 0;
+  p->polish = 1;
   p->stream = nullptr;
 }
 
@@ -257,7 +262,7 @@ spfom_status spfom_create(const spfom_params* p, spfom_ctx** out) {
   *out = nullptr;
   spfom_params prm;
   if (p) prm = *p; else spfom_default_params(&prm);
-  if (prm.precision != 64) return SPFOM_ENOTSUP;
+  if (prm.precision != 64 && prm.precision != 32) return SPFOM_ENOTSUP;
   if (!(prm.batch_frac > 0.0) || !(prm.restart_beta >= 0.0) || !(prm.kkt_tol >= 0.0) || prm.tau0 < 0 ||
       prm.mu < 0 || !(prm.restart_tau_decay > 0.0))
     return SPFOM_EINVAL;
@@ -302,6 +307,18 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   spfom_status s = validate(ctx, I, &kmax);
   if (s != SPFOM_OK) return s;
   if (kmax > 32) return fail(ctx, SPFOM_ENOTSUP, "consideration set of %d products (at most 32 supported)", kmax);
+  if (ctx->p.precision == 32) {
+    // binary32 copies must stay normal numbers (zero allowed for v - w and lambda)
+    auto in32 = [](double x, bool zero_ok) { return (zero_ok && x == 0.0) || (x >= 1.1754943508222875e-38 && x <= 3.4028234663852886e+38); };
+    for (long long p = 0; p < I->seg_ptr[I->L]; ++p) {
+      const double vt = I->w ? I->v[p] - I->w[p] : I->v[p];
+      if (!in32(I->v[p], false) || !in32(vt, true))
+        return fail(ctx, SPFOM_ENOTSUP, "precision 32: attraction at %lld outside binary32's normal range", p);
+    }
+    for (long long l = 0; l < I->L; ++l)
+      if (!in32(I->lam[l], true) || !in32(I->v0[l], false))
+        return fail(ctx, SPFOM_ENOTSUP, "precision 32: lambda or v0 of segment %lld outside binary32's range", l);
+  }
   SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
   free_instance(ctx);
   const int n = I->n, m = I->m;
@@ -385,10 +402,22 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       W.fx_scale = std::ldexp(1.0, F);
       W.fx_bits = F;
       W.inv_fx_scale = std::ldexp(1.0, -F);
-      W.zparts_iter = plan.grid;
+      W.zparts_iter = std::max(plan.grid, plan.grid32);
       W.zparts_eval = plan.grid_eval;
-      SPFOM_TRY(dalloc(ctx, &W.part, (size_t)plan.grid * (size_t)(n > 0 ? n : 1)));
+      if (plan.scatter == 1)
+        SPFOM_TRY(dalloc(ctx, &W.part, (size_t)std::max(plan.grid, plan.grid32) * (size_t)(n > 0 ? n : 1)));
       SPFOM_TRY(dalloc(ctx, &W.s_fx, (size_t)n));
+    }
+    if (ctx->p.precision == 32) {
+      if (!W.fast) {
+        free_instance(ctx);
+        return fail(ctx, SPFOM_ENOTSUP, "precision 32 needs the certified-decision kernel (path 0)");
+      }
+      SPFOM_TRY(dalloc(ctx, &W.v32, (size_t)nnz));
+      SPFOM_TRY(dalloc(ctx, &W.vt32, (size_t)nnz));
+      SPFOM_TRY(dalloc(ctx, &W.lam32, (size_t)L));
+      SPFOM_TRY(dalloc(ctx, &W.vt0_32, (size_t)L));
+      SPFOM_TRY(dalloc(ctx, &W.marg32, (size_t)n));
     }
     SPFOM_TRY(dalloc(ctx, &W.fallbacks, 1));
   }
@@ -400,6 +429,10 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   if (ctx->p.batch_frac < 1.0) SPFOM_TRY(dalloc(ctx, &W.x_cur, (size_t)nnz));
 #undef SPFOM_TRY
   ctx->P = P;
+  if (W.v32) {
+    e = spfom::launch_prep_f32(P, W, ctx->stream);
+    if (e != cudaSuccess) { free_instance(ctx); return cuda_fail(ctx, e, "binary32 copies"); }
+  }
   // step size: tau, or tau0 * mean(r) / mean(c) (sums in index order)
   double sr = 0.0, sc = 0.0;
   for (int j = 0; j < n; ++j) sr += I->r[j];
@@ -414,6 +447,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   cfg.restart_artificial = ctx->p.restart_artificial;
   cfg.restart_tau_decay = ctx->p.restart_tau_decay;
   cfg.kkt_tol = ctx->p.kkt_tol;
+  cfg.f32 = ctx->p.precision == 32 ? 1 : 0;
   ctx->loaded = true;
   s = init_state(ctx, nullptr);
   if (s != SPFOM_OK) {
@@ -498,6 +532,15 @@ spfom_status spfom_solve(spfom_ctx* ctx, const double* y0, spfom_stats* out) {
     seg += st.seg_kernel_seconds;
     segl += st.seg_kernel_launches;
     launches += st.kernel_launches;
+    if (st.converged && ctx->cfg.f32 && ctx->p.polish) {
+      // binary64 polish: clear the flag and iterate in binary64 until the next evaluation
+      ctx->cfg.f32 = 0;
+      ctx->polishing = true;
+      const int zero = 0;
+      SPFOM_CUDA(ctx, cudaMemcpyAsync(&ctx->W.st->converged, &zero, sizeof zero, cudaMemcpyHostToDevice,
+                                      ctx->stream));
+      continue;
+    }
     if (st.converged) break;
   }
   st.seconds = secs;

@@ -48,8 +48,10 @@ constexpr int kFastMaxSmem = 200 * 1024;
 // Launch plan of the certified-decision segment kernel.
 struct FastPlan {
   int W;              // lanes per segment (4 products per lane)
-  int smem;           // bytes of the per-block product accumulator
-  int grid;           // blocks of the iterate launch (= number of partial sums)
+  int scatter;        // 1: shared-memory sums + per-block partials; 2: global atomics
+  int smem;           // bytes of the per-block product accumulator (scatter 1)
+  int grid;           // blocks of the binary64 iterate launch (= number of partial sums)
+  int grid32;         // blocks of the binary32 iterate launch
   int grid_eval;      // blocks of the evaluation launch
   int reduce_chunks;  // grid.y of k_reduce_products
 };
@@ -83,6 +85,12 @@ struct Work {
   unsigned long long* fallbacks;  // running count of segments decided in binary64
   double fx_scale, inv_fx_scale;  // 2^F and 2^-F
   int fx_bits;                    // F
+  // binary32 copies for the precision-32 mode (null otherwise)
+  float* v32;
+  float* vt32;
+  float* lam32;
+  float* vt0_32;
+  float* marg32;
 };
 
 struct FastArgs {
@@ -94,6 +102,24 @@ struct FastArgs {
   double fx_scale;
   unsigned long long* fallbacks;
   int fx_bits;  // F of the fixed-point scale 2^F
+  unsigned long long* s_fx;  // product sums when the plan scatters with global atomics
+};
+
+struct F32Args {
+  const long long* seg_ptr;
+  const int* seg_prod;
+  const float* v32;
+  const float* vt32;
+  const float* lam32;
+  const float* vt0_32;
+  long long L;
+  int n;
+  int fx_bits;
+  const float* marg32;
+  unsigned long long* part;
+  unsigned long long* s_fx;
+  double* zpart;
+  const DevState* st;
 };
 
 struct RunConfig {
@@ -101,6 +127,7 @@ struct RunConfig {
   unsigned long long seed;
   unsigned long long sample_thr;  // segment l is solved at t iff hash < sample_thr
   double restart_beta, restart_artificial, restart_tau_decay, kkt_tol;
+  int f32;  // run the iterations' segment pass in binary32
 };
 
 // Launchers (spfom_kernels.cu). Each returns the launch status.
@@ -117,7 +144,11 @@ int kernel_launches_per_eval();
 // spfom_segments_fast.cu
 bool fast_plan(int n, int kmax, int sms, FastPlan* plan);
 cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s);
-cudaError_t launch_reduce_products(const Problem& P, const FastPlan& plan, const unsigned long long* part,
-                                   unsigned long long* s_fx, const DevState* st, cudaStream_t s);
+cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s);
+cudaError_t launch_reduce_products(const Problem& P, const FastPlan& plan, int nparts,
+                                   const unsigned long long* part, unsigned long long* s_fx, const DevState* st,
+                                   cudaStream_t s);
+// binary32 copies of v, vt, lambda, vt0 for the precision-32 mode
+cudaError_t launch_prep_f32(const Problem& P, Work& Wk, cudaStream_t s);
 
 }  // namespace spfom

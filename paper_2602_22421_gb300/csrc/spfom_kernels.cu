@@ -86,7 +86,8 @@ __global__ void k_prep_segments(long long L, const long long* __restrict__ seg_p
 // given (full-batch iterations rebuild the sales from zero).
 __global__ void k_margins(Problem P, const double* __restrict__ y, const double* __restrict__ sum_y, int avg,
                           double* __restrict__ marg, double* __restrict__ s_clear,
-                          unsigned long long* __restrict__ sfx_clear, const DevState* st) {
+                          unsigned long long* __restrict__ sfx_clear, const DevState* st,
+                          float* __restrict__ marg32 = nullptr) {
   if (st && st->converged) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= P.n) return;
@@ -99,6 +100,7 @@ __global__ void k_margins(Problem P, const double* __restrict__ y, const double*
     acc = __dadd_rn(acc, __dmul_rn(a, yi));
   }
   marg[j] = __dsub_rn(P.r[j], acc);
+  if (marg32) marg32[j] = __double2float_rn(marg[j]);
   if (s_clear) s_clear[j] = 0.0;
   if (sfx_clear) sfx_clear[j] = 0ull;
 }
@@ -210,7 +212,8 @@ __global__ void __launch_bounds__(kSegThreads) k_segments(Problem P, const doubl
 }
 
 // -------------------------------------------------------------- a3 .. a5 --
-__global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, RunConfig cfg, int full) {
+__global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, RunConfig cfg, int full,
+                                                              int zparts) {
   DevState* st = Wk.st;
   if (st->converged) return;
   __shared__ double sh[32];
@@ -257,7 +260,7 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
   // Last block: fold the partial sums (strided over the block, then a tree).
   __threadfence();
   double zs = 0.0, cys = 0.0, Ps = 0.0;
-  for (int b = threadIdx.x; b < Wk.zparts_iter; b += blockDim.x) zs += __ldcg(Wk.zpart + b);
+  for (int b = threadIdx.x; b < zparts; b += blockDim.x) zs += __ldcg(Wk.zpart + b);
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
     cys += __ldcg(Wk.cypart + b);
     Ps += __ldcg(Wk.Ppart + b);
@@ -385,15 +388,23 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
                              cudaEvent_t seg_begin, cudaEvent_t seg_end) {
   const bool sampled = cfg.batch_frac < 1.0;
   const bool fast = Wk.fast && !sampled;
+  const bool f32 = fast && cfg.f32 && Wk.v32;
   const int gv = vec_grid(P);
   const int gn = (P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1;
   k_margins<<<gn, kVecThreads, 0, s>>>(P, Wk.y, nullptr, 0, Wk.marg, (sampled || fast) ? nullptr : Wk.s,
-                                       fast ? Wk.s_fx : nullptr, Wk.st);
+                                       fast ? Wk.s_fx : nullptr, Wk.st, f32 ? Wk.marg32 : nullptr);
   if (seg_begin) cudaEventRecord(seg_begin, s);
   cudaError_t e;
-  if (fast) {
-    FastArgs A{P, Wk.marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits};
+  int zparts = Wk.seg_blocks;
+  if (f32) {
+    F32Args A{P.seg_ptr, P.seg_prod, Wk.v32, Wk.vt32, Wk.lam32, Wk.vt0_32, P.L, P.n, Wk.fx_bits, Wk.marg32,
+              Wk.part, Wk.s_fx, Wk.zpart, Wk.st};
+    e = launch_seg_f32(A, Wk.plan, s);
+    zparts = Wk.plan.grid32;
+  } else if (fast) {
+    FastArgs A{P, Wk.marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, Wk.s_fx};
     e = launch_seg_fast(A, Wk.plan, true, s);
+    zparts = Wk.plan.grid;
   } else {
     e = sampled ? launch_segments_w<kIterate, true>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s)
                 : launch_segments_w<kIterate, false>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s);
@@ -401,10 +412,10 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
   if (seg_end) cudaEventRecord(seg_end, s);
   if (e != cudaSuccess) return e;
   if (fast) {
-    e = launch_reduce_products(P, Wk.plan, Wk.part, Wk.s_fx, Wk.st, s);
+    e = launch_reduce_products(P, Wk.plan, zparts, Wk.part, Wk.s_fx, Wk.st, s);
     if (e != cudaSuccess) return e;
   }
-  k_dual_step<<<gv, kVecThreads, 0, s>>>(P, Wk, cfg, sampled ? 0 : 1);
+  k_dual_step<<<gv, kVecThreads, 0, s>>>(P, Wk, cfg, sampled ? 0 : 1, zparts);
   return cudaGetLastError();
 }
 
@@ -413,7 +424,7 @@ cudaError_t launch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, 
   k_margins<<<gn, kVecThreads, 0, s>>>(P, nullptr, Wk.sum_y, 1, Wk.marg_eval, nullptr, nullptr, Wk.st);
   cudaError_t e;
   if (Wk.fast) {
-    FastArgs A{P, Wk.marg_eval, nullptr, Wk.zpart_eval, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits};
+    FastArgs A{P, Wk.marg_eval, nullptr, Wk.zpart_eval, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, nullptr};
     e = launch_seg_fast(A, Wk.plan, false, s);
   } else {
     e = launch_segments_w<kEvalSum, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, Wk.st, cfg, s);
@@ -435,7 +446,33 @@ cudaError_t launch_evaluate_at(const Problem& P, const Work& Wk, bool want_seg, 
 }
 
 int kernel_launches_per_iteration(const Work& Wk, const RunConfig& cfg) {
-  return (Wk.fast && cfg.batch_frac >= 1.0) ? 4 : 3;
+  if (!(Wk.fast && cfg.batch_frac >= 1.0)) return 3;
+  return Wk.plan.scatter == 1 ? 4 : 3;
+}
+
+namespace {
+__global__ void k_prep_f32_items(long long nnz, const double* __restrict__ v, const double* __restrict__ vt,
+                                 float* __restrict__ v32, float* __restrict__ vt32) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p < nnz) {
+    v32[p] = __double2float_rn(v[p]);
+    vt32[p] = __double2float_rn(vt[p]);
+  }
+}
+__global__ void k_prep_f32_segments(long long L, const double* __restrict__ lam, const double* __restrict__ vt0,
+                                    float* __restrict__ lam32, float* __restrict__ vt0_32) {
+  const long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (l < L) {
+    lam32[l] = __double2float_rn(lam[l]);
+    vt0_32[l] = __double2float_rn(vt0[l]);
+  }
+}
+}  // namespace
+
+cudaError_t launch_prep_f32(const Problem& P, Work& Wk, cudaStream_t s) {
+  if (P.nnz > 0) k_prep_f32_items<<<(unsigned)((P.nnz + 255) / 256), 256, 0, s>>>(P.nnz, P.v, P.vt, Wk.v32, Wk.vt32);
+  if (P.L > 0) k_prep_f32_segments<<<(unsigned)((P.L + 255) / 256), 256, 0, s>>>(P.L, P.lam, P.vt0, Wk.lam32, Wk.vt0_32);
+  return cudaGetLastError();
 }
 int kernel_launches_per_eval() { return 3; }
 

@@ -109,13 +109,13 @@ __device__ double block_sum_d(double v, double* sh) {
   return tot;
 }
 
-template <int W, int P, bool SCATTER>
+template <int W, int P, int SC>
 __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
-  extern __shared__ unsigned long long acc[];  // [n] product sales (fixed point) when SCATTER
+  extern __shared__ unsigned long long acc[];  // [n] product sales (fixed point) when SC == 1
   __shared__ double sh[32];
   if (A.st && A.st->converged) return;
   const Problem& Pr = A.P;
-  if (SCATTER) {
+  if (SC == 1) {
     for (int j = threadIdx.x; j < Pr.n; j += blockDim.x) acc[j] = 0ull;
     __syncthreads();
   }
@@ -237,19 +237,120 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
     }
     const double q = quotient(lam, vt0 + Dl);
     if (lane == 0) zacc += q * Nl;
-    if (SCATTER) {
+    if (SC != 0) {
 #pragma unroll
       for (int p = 0; p < P; ++p)
-        if ((S >> p) & 1u) atomicAdd(acc + jv[p], fixed_product(q, vv[p], A.fx_bits));
+        if ((S >> p) & 1u) atomicAdd((SC == 1 ? acc : A.s_fx) + jv[p], fixed_product(q, vv[p], A.fx_bits));
     }
   }
   const double tot = block_sum_d(zacc, sh);
   if (threadIdx.x == 0) A.zpart[blockIdx.x] = tot;
   if (fallbacks && A.fallbacks) atomicAdd(A.fallbacks, (unsigned long long)fallbacks);
-  if (SCATTER) {
+  if (SC == 1) {
     __syncthreads();
     unsigned long long* dst = A.part + (size_t)blockIdx.x * Pr.n;
     for (int j = threadIdx.x; j < Pr.n; j += blockDim.x) dst[j] = acc[j];
+  }
+}
+
+// round(a * b * 2^F) for non-negative binary32 a, b with a * b * 2^F < 2^62: the
+// 48-bit product of the significands is exact in 64 bits, so the only
+// rounding is the final one. a = ma 2^(ea - 150), b = mb 2^(eb - 150).
+__device__ __forceinline__ unsigned long long fixed_product32(float a, float b, int F) {
+  const unsigned ua = __float_as_uint(a), ub = __float_as_uint(b);
+  const int ea = (int)(ua >> 23), eb = (int)(ub >> 23);
+  if (ea == 0 || eb == 0) return 0ull;  // zero or subnormal: far below the fixed-point unit
+  const unsigned long long prod =
+      (unsigned long long)((ua & 0x7FFFFFu) | 0x800000u) * (unsigned long long)((ub & 0x7FFFFFu) | 0x800000u);
+  const int sh = 300 - F - ea - eb;  // a b 2^F = prod / 2^sh
+  if (sh <= 0) return prod << (-sh);
+  if (sh > 63) return 0ull;
+  return (prod + (1ull << (sh - 1))) >> sh;
+}
+
+// Binary32 bulk iteration (the precision-32 mode): the same decision as
+// k_seg_fast without certificate, and binary32 values: the final Dinkelbach
+// set's N and D give q = lambda / (vt0 + D) and z = q N; the sales are the exact
+// products q v rounded once to fixed point. Reads 12 B per nonzero.
+template <int W, int P, int SC>
+__global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
+  extern __shared__ unsigned long long acc[];
+  __shared__ double sh[32];
+  if (A.st->converged) return;
+  if (SC == 1) {
+    for (int j = threadIdx.x; j < A.n; j += blockDim.x) acc[j] = 0ull;
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & (W - 1);
+  const int gbase = (threadIdx.x & 31) & ~(W - 1);
+  const unsigned gmask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << gbase);
+  const long long gpb = blockDim.x / W;
+  const long long ngroups = (long long)gridDim.x * gpb;
+  float zacc = 0.f;
+  for (long long l = blockIdx.x * gpb + threadIdx.x / W; l < A.L; l += ngroups) {
+    const long long b = A.seg_ptr[l];
+    const int K = (int)(A.seg_ptr[l + 1] - b);
+    int jv[P];
+    float vv[P], tv[P], af[P];
+    unsigned cand = 0;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      const int k = lane + p * W;
+      jv[p] = 0;
+      vv[p] = tv[p] = af[p] = 0.f;
+      if (k < K) {
+        jv[p] = A.seg_prod[b + k];
+        vv[p] = A.v32[b + k];
+        tv[p] = A.vt32[b + k];
+      }
+    }
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      if (lane + p * W < K) {
+        const float m = A.marg32[jv[p]];
+        if (m > 0.f) {
+          cand |= 1u << p;
+          af[p] = m * vv[p];
+        }
+      }
+    const float lam = A.lam32[l], vt0 = A.vt0_32[l];
+    float R = 0.f, Nsel = 0.f, Dsel = 0.f;
+    unsigned sel = 0xffffffffu;
+    for (int it = 0; it < P * W + 2; ++it) {
+      unsigned s = 0;
+      float N = 0.f, D = 0.f;
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        if (((cand >> p) & 1u) && af[p] > R * tv[p]) {
+          s |= 1u << p;
+          N += af[p];
+          D += tv[p];
+        }
+      if (__all_sync(gmask, s == sel)) break;
+#pragma unroll
+      for (int o = W >> 1; o > 0; o >>= 1) {
+        N += __shfl_xor_sync(gmask, N, o, W);
+        D += __shfl_xor_sync(gmask, D, o, W);
+      }
+      R = N / (vt0 + D);
+      sel = s;
+      Nsel = N;
+      Dsel = D;
+    }
+    const float q = lam / (vt0 + Dsel);
+    if (lane == 0) zacc += q * Nsel;
+    if (SC != 0) {
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        if ((sel >> p) & 1u) atomicAdd((SC == 1 ? acc : A.s_fx) + jv[p], fixed_product32(q, vv[p], A.fx_bits));
+    }
+  }
+  const double tot = block_sum_d((double)zacc, sh);
+  if (threadIdx.x == 0) A.zpart[blockIdx.x] = tot;
+  if (SC == 1) {
+    __syncthreads();
+    unsigned long long* dst = A.part + (size_t)blockIdx.x * A.n;
+    for (int j = threadIdx.x; j < A.n; j += blockDim.x) dst[j] = acc[j];
   }
 }
 
@@ -267,69 +368,94 @@ __global__ void k_reduce_products(int n, int nparts, const unsigned long long* _
   if (acc) atomicAdd(s_fx + j, acc);
 }
 
-template <int W, bool SCATTER>
-void set_smem(int bytes) {
-  cudaFuncSetAttribute(k_seg_fast<W, 4, SCATTER>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
-template <bool SCATTER>
-cudaError_t launch_w(const FastArgs& A, int W, int grid, int smem, cudaStream_t s) {
+template <int SC>
+cudaError_t launch_fast_w(const FastArgs& A, int W, int grid, int smem, cudaStream_t s) {
   switch (W) {
-    case 1: k_seg_fast<1, 4, SCATTER><<<grid, kFastThreads, smem, s>>>(A); break;
-    case 2: k_seg_fast<2, 4, SCATTER><<<grid, kFastThreads, smem, s>>>(A); break;
-    case 4: k_seg_fast<4, 4, SCATTER><<<grid, kFastThreads, smem, s>>>(A); break;
-    case 8: k_seg_fast<8, 4, SCATTER><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 1: k_seg_fast<1, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 2: k_seg_fast<2, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 4: k_seg_fast<4, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 8: k_seg_fast<8, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
-template <bool SCATTER>
-int occupancy(int W, int smem) {
-  int nb = 0;
+template <int SC>
+cudaError_t launch_f32_w(const F32Args& A, int W, int grid, int smem, cudaStream_t s) {
   switch (W) {
-    case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_fast<1, 4, SCATTER>, kFastThreads, smem); break;
-    case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_fast<2, 4, SCATTER>, kFastThreads, smem); break;
-    case 4: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_fast<4, 4, SCATTER>, kFastThreads, smem); break;
-    case 8: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_fast<8, 4, SCATTER>, kFastThreads, smem); break;
-    default: break;
+    case 1: k_seg_f32<1, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 2: k_seg_f32<2, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 4: k_seg_f32<4, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 8: k_seg_f32<8, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+template <class K>
+int blocks_per_sm(K kernel, int smem) {
+  int nb = 0;
+  if (smem > 0) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kFastThreads, smem);
   return nb;
+}
+
+int occupancy(int W, int sc, int smem, bool f32) {
+#define SPFOM_OCC(WW)                                                                          \
+  if (W == WW) {                                                                               \
+    if (f32) return sc == 1 ? blocks_per_sm(k_seg_f32<WW, 4, 1>, smem)                        \
+                            : blocks_per_sm(k_seg_f32<WW, 4, 2>, 0);                           \
+    return sc == 0 ? blocks_per_sm(k_seg_fast<WW, 4, 0>, 0)                                   \
+                   : (sc == 1 ? blocks_per_sm(k_seg_fast<WW, 4, 1>, smem)                     \
+                              : blocks_per_sm(k_seg_fast<WW, 4, 2>, 0));                      \
+  }
+  SPFOM_OCC(1)
+  SPFOM_OCC(2)
+  SPFOM_OCC(4)
+  SPFOM_OCC(8)
+#undef SPFOM_OCC
+  return 0;
 }
 
 }  // namespace
 
 bool fast_plan(int n, int kmax, int sms, FastPlan* plan) {
   if (kmax > 32) return false;
-  const int smem = n * (int)sizeof(unsigned long long);
-  if (smem > kFastMaxSmem) return false;
   int W = 1;
   while (W * 4 < kmax) W <<= 1;
-  set_smem<1, true>(smem);
-  set_smem<2, true>(smem);
-  set_smem<4, true>(smem);
-  set_smem<8, true>(smem);
-  const int nb = occupancy<true>(W, smem);
-  const int nbe = occupancy<false>(W, 0);
-  if (nb <= 0 || nbe <= 0) return false;
+  const int smem = n * (int)sizeof(unsigned long long);
+  const int sc = smem <= kFastMaxSmem ? 1 : 2;
+  const int nb = occupancy(W, sc, smem, false);
+  const int nb32 = occupancy(W, sc, smem, true);
+  const int nbe = occupancy(W, 0, 0, false);
+  if (nb <= 0 || nbe <= 0 || nb32 <= 0) return false;
   plan->W = W;
-  plan->smem = smem;
+  plan->scatter = sc;
+  plan->smem = sc == 1 ? smem : 0;
   plan->grid = nb * sms;
+  plan->grid32 = nb32 * sms;
   plan->grid_eval = nbe * sms;
   plan->reduce_chunks = 16;
   return true;
 }
 
 cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s) {
-  return scatter ? launch_w<true>(A, plan.W, plan.grid, plan.smem, s)
-                 : launch_w<false>(A, plan.W, plan.grid_eval, 0, s);
+  if (!scatter) return launch_fast_w<0>(A, plan.W, plan.grid_eval, 0, s);
+  return plan.scatter == 1 ? launch_fast_w<1>(A, plan.W, plan.grid, plan.smem, s)
+                           : launch_fast_w<2>(A, plan.W, plan.grid, 0, s);
 }
 
-cudaError_t launch_reduce_products(const Problem& P, const FastPlan& plan, const unsigned long long* part,
-                                   unsigned long long* s_fx, const DevState* st, cudaStream_t s) {
-  if (P.n <= 0) return cudaSuccess;
+cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s) {
+  return plan.scatter == 1 ? launch_f32_w<1>(A, plan.W, plan.grid32, plan.smem, s)
+                           : launch_f32_w<2>(A, plan.W, plan.grid32, 0, s);
+}
+
+cudaError_t launch_reduce_products(const Problem& P, const FastPlan& plan, int nparts,
+                                   const unsigned long long* part, unsigned long long* s_fx, const DevState* st,
+                                   cudaStream_t s) {
+  if (P.n <= 0 || plan.scatter != 1) return cudaSuccess;
   dim3 grid((P.n + 255) / 256, plan.reduce_chunks);
-  k_reduce_products<<<grid, 256, 0, s>>>(P.n, plan.grid, part, s_fx, st);
+  k_reduce_products<<<grid, 256, 0, s>>>(P.n, nparts, part, s_fx, st);
   return cudaGetLastError();
 }
 

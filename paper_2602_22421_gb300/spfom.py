@@ -34,7 +34,8 @@ class Params(C.Structure):
                 ("batch_frac", C.c_double), ("seed", C.c_uint64), ("eval_every", C.c_int64),
                 ("restart_beta", C.c_double), ("restart_artificial", C.c_double),
                 ("restart_tau_decay", C.c_double), ("kkt_tol", C.c_double), ("max_iters", C.c_int64),
-                ("device", C.c_int32), ("profile", C.c_int32), ("path", C.c_int32), ("stream", C.c_void_p)]
+                ("device", C.c_int32), ("profile", C.c_int32), ("path", C.c_int32), ("polish", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class InstanceC(C.Structure):
@@ -60,7 +61,7 @@ class Stats(C.Structure):
                 ("sum_revenue", C.c_double), ("tau", C.c_double), ("mu", C.c_double), ("seconds", C.c_double),
                 ("seg_kernel_seconds", C.c_double), ("seg_kernel_launches", C.c_int64),
                 ("kernel_launches", C.c_int64), ("fallback_segments", C.c_int64), ("fast_path", C.c_int32),
-                ("pad2_", C.c_int32)]
+                ("iter_precision", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}

@@ -59,7 +59,13 @@ def mid_small():
     return mid_gam(1, L=40_001, n=2000, m=400)
 
 
-CASES = {"tiny_mnl": lambda: tiny_mnl(0), "small_gam": small_gam, "edge": edge_instance, "mid_small": mid_small}
+def wide():
+    """More products than a block's shared memory holds as sums (global atomics)."""
+    return mid_gam(1, L=20_001, n=30_000, m=500)
+
+
+CASES = {"tiny_mnl": lambda: tiny_mnl(0), "small_gam": small_gam, "edge": edge_instance, "mid_small": mid_small,
+         "wide": wide}
 
 
 @pytest.mark.parametrize("path", [0, 1], ids=["certified", "general"])
@@ -248,3 +254,54 @@ def test_large_consideration_set_is_unsupported():
     with pytest.raises(SpfomError) as ei:
         Solver(inst)
     assert ei.value.status == 7
+
+
+# -- binary32 bulk mode (precision 32) --------------------------------------
+FP32_ERRORS = {}
+
+
+@pytest.mark.parametrize("name", ["mid_small", "wide"])
+def test_fp32_bulk_error_against_fp64_oracle(name):
+    """Binary32 segment solves with binary64 residuals: the error against the
+    FP64 oracle is reported per result (FP32_ERRORS) and bounded: one iteration
+    from y = 0 is within binary32 rounding; after 200 iterations the iterates
+    stay close although binary32 decisions near ties may differ."""
+    inst = CASES[name]()
+    run = Oracle(inst).run(OracleParams())
+    with Solver(inst, precision=32) as s:
+        st = s.step(1)
+        run.step(1)
+        assert st["iter_precision"] == 32 and st["fast_path"] == 1
+        e = {"y@1": nrel(s.duals(), run.y), "s@1": nrel(s.vector(5), run.s), "g@1": nrel(s.vector(4), run.g),
+             "z_sum@1": abs(st["z_sum"] / run.stats()["z_sum"] - 1)}
+        assert max(e.values()) <= 1e-5, e
+        st = s.step(199)
+        run.step(199)
+        ost = run.stats()
+        e.update({"y@200": nrel(s.duals(), run.y), "g@200": nrel(s.vector(4), run.g),
+                  "dual_avg@200": abs(st["dual_avg"] / ost["dual_avg"] - 1),
+                  "kkt@200": abs(st["kkt"] - ost["kkt"])})
+        FP32_ERRORS[name] = e
+        print(f"binary32 vs FP64 oracle errors ({name}): {e}")
+        assert e["y@200"] <= 1e-2 and e["dual_avg@200"] <= 1e-5 and e["kkt@200"] <= 1e-4, e
+
+
+def test_fp32_bulk_solve_matches_fp64_objective():
+    """Time-to-KKT form: binary32 iterations, binary64 KKT checks and a binary64
+    polish reach KKT <= 1e-4 with the dual objective within 1e-4 of the FP64
+    oracle's at its own KKT <= 1e-4."""
+    inst = mid_gam(1, L=20_000, n=1000, m=200)
+    run = Oracle(inst).run(OracleParams())
+    for _ in range(200):
+        ost = run.step(64)
+        if ost["converged"]:
+            break
+    with Solver(inst, precision=32) as s:
+        st = s.solve()
+        assert st["converged"] == 1 and st["kkt"] <= 1e-4 and st["iter_precision"] == 64
+        assert st["dual_avg"] == pytest.approx(ost["dual_avg"], rel=1e-4)
+        assert st["primal_avg"] == pytest.approx(ost["primal_avg"], rel=1e-4)
+    with Solver(inst, precision=32, polish=0) as s:
+        st = s.solve()
+        assert st["converged"] == 1 and st["iter_precision"] == 32
+        assert st["dual_avg"] == pytest.approx(ost["dual_avg"], rel=1e-4)
