@@ -224,11 +224,21 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
   const bool fx = Wk.fast && full;
   if (gid < P.m) {
     double g = 0.0;
-    for (int q = P.at_ptr[gid]; q < P.at_ptr[gid + 1]; ++q) {
-      const double a = P.at_val ? P.at_val[q] : 1.0;
-      const int j = P.at_idx[q];
-      const double sj = fx ? __dmul_rn(__ull2double_rn(Wk.s_fx[j]), Wk.inv_fx_scale) : Wk.s[j];
-      g = __dadd_rn(g, __dmul_rn(a, sj));
+    const int q0 = P.at_ptr[gid], q1 = P.at_ptr[gid + 1];
+    // Eight products at a time: the index loads, then the sales loads, are
+    // issued together; the sum still runs in ascending product order.
+    for (int qb = q0; qb < q1; qb += 8) {
+      int jj[8];
+      double sv[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) jj[k] = qb + k < q1 ? P.at_idx[qb + k] : -1;
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        sv[k] = jj[k] < 0 ? 0.0
+                          : (fx ? __dmul_rn(__ull2double_rn(Wk.s_fx[jj[k]]), Wk.inv_fx_scale) : Wk.s[jj[k]]);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (jj[k] >= 0) g = __dadd_rn(g, __dmul_rn(P.at_val ? P.at_val[qb + k] : 1.0, sv[k]));
     }
     const double yo = Wk.y[gid], c = P.c[gid];
     const double yn = __dsub_rn(__dmul_rn(shrink, yo), __dmul_rn(tau, __dsub_rn(c, g)));
