@@ -88,13 +88,18 @@ spfom_status dalloc(spfom_ctx* ctx, T** out, size_t count) {
   return SPFOM_OK;
 }
 
+// Copy count elements; `slack` more elements are allocated after them and
+// zeroed (bulk copies widened to 16-byte boundaries may read them).
 template <class T>
-spfom_status upload(spfom_ctx* ctx, T** out, const T* src, size_t count) {
-  spfom_status s = dalloc(ctx, out, count);
+spfom_status upload(spfom_ctx* ctx, T** out, const T* src, size_t count, size_t slack = 0) {
+  spfom_status s = dalloc(ctx, out, count + slack);
   if (s != SPFOM_OK) return s;
   if (count) SPFOM_CUDA(ctx, cudaMemcpyAsync(*out, src, count * sizeof(T), cudaMemcpyHostToDevice, ctx->stream));
+  if (slack) SPFOM_CUDA(ctx, cudaMemsetAsync(*out + count, 0, slack * sizeof(T), ctx->stream));
   return SPFOM_OK;
 }
+
+constexpr size_t kSlack = 4;  // elements of zeroed slack after arrays that bulk copies read
 
 bool is_finite(double x) { return std::isfinite(x); }
 
@@ -354,8 +359,8 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   SPFOM_TRY(upload(ctx, &d_atidx, at_idx.data(), (size_t)nnzA));
   if (I->a_val) SPFOM_TRY(upload(ctx, &d_atval, at_val.data(), (size_t)nnzA));
   static_assert(sizeof(long long) == sizeof(int64_t), "int64");
-  SPFOM_TRY(upload(ctx, &d_segptr, reinterpret_cast<const long long*>(I->seg_ptr), (size_t)L + 1));
-  SPFOM_TRY(upload(ctx, &d_prod, I->seg_prod, (size_t)nnz));
+  SPFOM_TRY(upload(ctx, &d_segptr, reinterpret_cast<const long long*>(I->seg_ptr), (size_t)L + 1, kSlack));
+  SPFOM_TRY(upload(ctx, &d_prod, I->seg_prod, (size_t)nnz, kSlack));
   SPFOM_TRY(upload(ctx, &d_v, I->v, (size_t)nnz));
   if (I->w) SPFOM_TRY(upload(ctx, &d_w, I->w, (size_t)nnz));
   SPFOM_TRY(upload(ctx, &d_lam, I->lam, (size_t)L));
@@ -398,6 +403,14 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
     spfom::FastPlan plan{};
     if (ctx->p.path == 0 && F >= 30 && spfom::fast_plan(n, kmax, ctx->sms, &plan)) {
       W.fast = true;
+      if (ctx->p.precision == 32 && spfom::tma_plan(n, ctx->sms, &plan)) {
+        // tiles of consecutive segments for the bulk-copy staging of the binary32 pass
+        const long long nt = spfom::make_tiles(reinterpret_cast<const long long*>(I->seg_ptr), L, nullptr);
+        std::vector<long long> tiles((size_t)nt + 1);
+        spfom::make_tiles(reinterpret_cast<const long long*>(I->seg_ptr), L, tiles.data());
+        SPFOM_TRY(upload(ctx, &W.tile_ptr, tiles.data(), tiles.size()));
+        W.ntiles = nt;
+      }
       W.plan = plan;
       W.fx_scale = std::ldexp(1.0, F);
       W.fx_bits = F;
@@ -413,10 +426,14 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
         free_instance(ctx);
         return fail(ctx, SPFOM_ENOTSUP, "precision 32 needs the certified-decision kernel (path 0)");
       }
-      SPFOM_TRY(dalloc(ctx, &W.v32, (size_t)nnz));
-      SPFOM_TRY(dalloc(ctx, &W.vt32, (size_t)nnz));
-      SPFOM_TRY(dalloc(ctx, &W.lam32, (size_t)L));
-      SPFOM_TRY(dalloc(ctx, &W.vt0_32, (size_t)L));
+      SPFOM_TRY(dalloc(ctx, &W.v32, (size_t)nnz + kSlack));
+      SPFOM_TRY(dalloc(ctx, &W.vt32, (size_t)nnz + kSlack));
+      SPFOM_TRY(dalloc(ctx, &W.lam32, (size_t)L + kSlack));
+      SPFOM_TRY(dalloc(ctx, &W.vt0_32, (size_t)L + kSlack));
+      SPFOM_CUDA(ctx, cudaMemsetAsync(W.v32 + nnz, 0, kSlack * sizeof(float), ctx->stream));
+      SPFOM_CUDA(ctx, cudaMemsetAsync(W.vt32 + nnz, 0, kSlack * sizeof(float), ctx->stream));
+      SPFOM_CUDA(ctx, cudaMemsetAsync(W.lam32 + L, 0, kSlack * sizeof(float), ctx->stream));
+      SPFOM_CUDA(ctx, cudaMemsetAsync(W.vt0_32 + L, 0, kSlack * sizeof(float), ctx->stream));
       SPFOM_TRY(dalloc(ctx, &W.marg32, (size_t)n));
     }
     SPFOM_TRY(dalloc(ctx, &W.fallbacks, 1));
@@ -508,6 +525,13 @@ spfom_status spfom_step(spfom_ctx* ctx, int64_t iters, spfom_stats* out) {
     }
   ctx->host_t = st.t;
   fill_stats(ctx, st, ms * 1e-3, out);
+  if (st.error) {
+    if (out) {
+      out->seg_kernel_seconds = seg;
+      out->kernel_launches = launches;
+    }
+    return fail(ctx, SPFOM_ETIMEOUT, "a bounded device wait (bulk-copy staging) gave up; results are invalid");
+  }
   if (out) {
     out->seg_kernel_seconds = seg;
     out->seg_kernel_launches = prof ? iters : 0;

@@ -44,6 +44,8 @@ struct Problem {
 
 constexpr int kFastThreads = 512;
 constexpr int kFastMaxSmem = 200 * 1024;
+constexpr int kTmaThreads = 1024;
+constexpr int kTmaMaxSmem = 226 * 1024;
 
 // Launch plan of the certified-decision segment kernel.
 struct FastPlan {
@@ -54,6 +56,9 @@ struct FastPlan {
   int grid32;         // blocks of the binary32 iterate launch
   int grid_eval;      // blocks of the evaluation launch
   int reduce_chunks;  // grid.y of k_reduce_products
+  int tma;            // 1: the binary32 pass runs k_seg_f32_tma (tile staging by bulk copies)
+  int tma_smem;       // its dynamic shared memory: product sums + two stages
+  int acc_bytes;      // bytes of the product sums at the start of that memory
 };
 
 // Work buffers of one ctx.
@@ -91,6 +96,8 @@ struct Work {
   float* lam32;
   float* vt0_32;
   float* marg32;
+  long long* tile_ptr;  // [ntiles+1] (binary32 tile staging)
+  long long ntiles;
 };
 
 struct FastArgs {
@@ -120,6 +127,11 @@ struct F32Args {
   unsigned long long* s_fx;
   double* zpart;
   const DevState* st;
+  // tile staging (k_seg_f32_tma)
+  const long long* tile_ptr;  // [ntiles+1] segment offsets of the tiles
+  long long ntiles;
+  int acc_bytes;
+  DevState* st_rw;            // for the timeout flag
 };
 
 struct RunConfig {
@@ -145,6 +157,8 @@ int kernel_launches_per_eval();
 bool fast_plan(int n, int kmax, int sms, FastPlan* plan);
 cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s);
 cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s);
+bool tma_plan(int n, int sms, FastPlan* plan);
+long long make_tiles(const long long* seg_ptr, long long L, long long* tiles_out);
 cudaError_t launch_reduce_products(const Problem& P, const FastPlan& plan, int nparts,
                                    const unsigned long long* part, unsigned long long* s_fx, const DevState* st,
                                    cudaStream_t s);

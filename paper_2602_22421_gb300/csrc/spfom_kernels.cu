@@ -408,7 +408,7 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
   int zparts = Wk.seg_blocks;
   if (f32) {
     F32Args A{P.seg_ptr, P.seg_prod, Wk.v32, Wk.vt32, Wk.lam32, Wk.vt0_32, P.L, P.n, Wk.fx_bits, Wk.marg32,
-              Wk.part, Wk.s_fx, Wk.zpart, Wk.st};
+              Wk.part, Wk.s_fx, Wk.zpart, Wk.st, Wk.tile_ptr, Wk.ntiles, Wk.plan.acc_bytes, Wk.st};
     e = launch_seg_f32(A, Wk.plan, s);
     zparts = Wk.plan.grid32;
   } else if (fast) {

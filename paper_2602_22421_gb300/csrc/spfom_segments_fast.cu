@@ -354,6 +354,220 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// TMA-staged binary32 kernel. The per-segment work is short and its loads are
+// dependent (offsets, then products, then margins), so with the 32 warps per SM
+// the registers allow, k_seg_f32 waits on memory. Here the block's next tile of
+// segments (<= kTileSegs segments, <= kTileItems products) is copied into shared
+// memory by the Tensor Memory Accelerator while the block works on the current
+// one: one elected thread issues six 1-D bulk copies (cp.async.bulk) per tile,
+// completion is tracked by a transaction-count mbarrier per stage, and two
+// stages alternate. Copies start and end on 16-byte boundaries (ranges are
+// widened outward; the device arrays carry 4 elements of slack at the end).
+// Every wait is bounded: on expiry the block records an error in the device
+// state (reported as SPFOM_ETIMEOUT), waits once more, boundedly, for its own
+// copies and returns.
+constexpr int kTileSegs = 512;
+constexpr int kTileItems = 4096;
+constexpr unsigned kWaitLimit = 1u << 22;
+
+struct StageLayout {  // byte offsets inside one stage
+  static constexpr int segp = 0;                                  // int64 [kTileSegs + 4]
+  static constexpr int lam = segp + (kTileSegs + 4) * 8;          // f32 [kTileSegs + 8]
+  static constexpr int vt0 = lam + (kTileSegs + 8) * 4;           // f32 [kTileSegs + 8]
+  static constexpr int prod = vt0 + (kTileSegs + 8) * 4;          // i32 [kTileItems + 8]
+  static constexpr int v = prod + (kTileItems + 8) * 4;           // f32 [kTileItems + 8]
+  static constexpr int vt = v + (kTileItems + 8) * 4;             // f32 [kTileItems + 8]
+  static constexpr int bytes = vt + (kTileItems + 8) * 4;
+};
+static_assert(StageLayout::bytes % 16 == 0, "stage size must keep 16-byte alignment");
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0u;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
+  for (unsigned it = 0; it < kWaitLimit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// Issue the copies of tile t into stage `stage` (called by one thread).
+__device__ void issue_tile(const F32Args& A, long long t, unsigned char* stage, unsigned bar) {
+  const long long l0 = A.tile_ptr[t], l1 = A.tile_ptr[t + 1];
+  const long long b = A.seg_ptr[l0], e = A.seg_ptr[l1];
+  const long long sa = l0 & ~1ll, se = (l1 + 2) & ~1ll;  // int64 offsets [l0, l1], widened to 16 B
+  const long long fa = l0 & ~3ll, fe = (l1 + 3) & ~3ll;  // f32 per-segment [l0, l1)
+  const long long ia = b & ~3ll, ie = (e + 3) & ~3ll;    // 4-byte per-product [b, e)
+  const unsigned segb = (unsigned)((se - sa) * 8), fb = (unsigned)((fe - fa) * 4), ib = (unsigned)((ie - ia) * 4);
+  // order the block's earlier generic reads of this stage before the async-proxy writes
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  mbar_expect_tx(bar, segb + 2 * fb + 3 * ib);
+  const unsigned base = smem_addr(stage);
+  bulk_g2s(base + StageLayout::segp, A.seg_ptr + sa, segb, bar);
+  bulk_g2s(base + StageLayout::lam, A.lam32 + fa, fb, bar);
+  bulk_g2s(base + StageLayout::vt0, A.vt0_32 + fa, fb, bar);
+  if (ib) {
+    bulk_g2s(base + StageLayout::prod, A.seg_prod + ia, ib, bar);
+    bulk_g2s(base + StageLayout::v, A.v32 + ia, ib, bar);
+    bulk_g2s(base + StageLayout::vt, A.vt32 + ia, ib, bar);
+  }
+}
+
+template <int W, int P, int SC>
+__global__ void __launch_bounds__(kTmaThreads, 1) k_seg_f32_tma(F32Args A) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ double sh[32];
+  if (A.st->converged) return;
+  unsigned long long* acc = reinterpret_cast<unsigned long long*>(smem);
+  unsigned char* stages = smem + A.acc_bytes;  // acc_bytes is a multiple of 128
+  const unsigned bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
+  const long long ntiles = A.ntiles;
+  if (threadIdx.x == 0) {
+    mbar_init(bar0, 1);
+    mbar_init(bar1, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (SC == 1)
+    for (int j = threadIdx.x; j < A.n; j += blockDim.x) acc[j] = 0ull;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < 2; ++k) {
+      const long long t = blockIdx.x + (long long)k * gridDim.x;
+      if (t < ntiles) issue_tile(A, t, stages + k * StageLayout::bytes, k ? bar1 : bar0);
+    }
+  }
+  const int lane = threadIdx.x & (W - 1);
+  const int gbase = (threadIdx.x & 31) & ~(W - 1);
+  const unsigned gmask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << gbase);
+  const int gpb = blockDim.x / W, group = threadIdx.x / W;
+  float zacc = 0.f;
+  bool failed = false;
+  int k = 0;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    const int stg = k & 1;
+    unsigned char* S = stages + stg * StageLayout::bytes;
+    const bool ok = mbar_wait_bounded(stg ? bar1 : bar0, (unsigned)((k >> 1) & 1));
+    if (__syncthreads_or(!ok)) {
+      failed = true;
+      break;
+    }
+    const long long l0 = A.tile_ptr[t], l1 = A.tile_ptr[t + 1];
+    const long long* segp = reinterpret_cast<const long long*>(S + StageLayout::segp) + (l0 & 1);
+    const float* lam_s = reinterpret_cast<const float*>(S + StageLayout::lam) + (l0 & 3);
+    const float* vt0_s = reinterpret_cast<const float*>(S + StageLayout::vt0) + (l0 & 3);
+    const long long ibase = segp[0] & ~3ll;
+    const int* prod_s = reinterpret_cast<const int*>(S + StageLayout::prod);
+    const float* v_s = reinterpret_cast<const float*>(S + StageLayout::v);
+    const float* vt_s = reinterpret_cast<const float*>(S + StageLayout::vt);
+    const int nseg = (int)(l1 - l0);
+    for (int ls = group; ls < nseg; ls += gpb) {
+      const int b = (int)(segp[ls] - ibase);
+      const int K = (int)(segp[ls + 1] - segp[ls]);
+      int jv[P];
+      float vv[P], tv[P], af[P];
+      unsigned cand = 0;
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const int kk = lane + p * W;
+        jv[p] = 0;
+        vv[p] = tv[p] = af[p] = 0.f;
+        if (kk < K) {
+          jv[p] = prod_s[b + kk];
+          vv[p] = v_s[b + kk];
+          tv[p] = vt_s[b + kk];
+        }
+      }
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        if (lane + p * W < K) {
+          const float m = A.marg32[jv[p]];
+          if (m > 0.f) {
+            cand |= 1u << p;
+            af[p] = m * vv[p];
+          }
+        }
+      const float lam = lam_s[ls], vt0 = vt0_s[ls];
+      float R = 0.f, Nsel = 0.f, Dsel = 0.f;
+      unsigned sel = 0xffffffffu;
+      for (int it = 0; it < P * W + 2; ++it) {
+        unsigned s = 0;
+        float N = 0.f, D = 0.f;
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+          if (((cand >> p) & 1u) && af[p] > R * tv[p]) {
+            s |= 1u << p;
+            N += af[p];
+            D += tv[p];
+          }
+        if (__all_sync(gmask, s == sel)) break;
+#pragma unroll
+        for (int o = W >> 1; o > 0; o >>= 1) {
+          N += __shfl_xor_sync(gmask, N, o, W);
+          D += __shfl_xor_sync(gmask, D, o, W);
+        }
+        R = __fdividef(N, vt0 + D);
+        sel = s;
+        Nsel = N;
+        Dsel = D;
+      }
+      const float q = __fdividef(lam, vt0 + Dsel);
+      if (lane == 0) zacc += q * Nsel;
+      if (SC != 0) {
+#pragma unroll
+        for (int p = 0; p < P; ++p)
+          if ((sel >> p) & 1u)
+            atomicAdd((SC == 1 ? acc : A.s_fx) + jv[p], fixed_product32(q, vv[p], A.fx_bits));
+      }
+    }
+    __syncthreads();  // every thread is done with this stage
+    if (threadIdx.x == 0) {
+      const long long tn = t + 2ll * gridDim.x;
+      if (tn < ntiles) issue_tile(A, tn, S, stg ? bar1 : bar0);
+    }
+  }
+  if (failed) {
+    // Record the timeout, give the copies still in flight -- stage k's (the wait
+    // that expired) and stage k+1's if that tile was issued -- one more bounded
+    // wait each, and leave.
+    if (threadIdx.x == 0) {
+      atomicExch(&A.st_rw->error, 1);
+      const long long t = blockIdx.x + (long long)k * gridDim.x;
+      mbar_wait_bounded((k & 1) ? bar1 : bar0, (unsigned)((k >> 1) & 1));
+      if (t + gridDim.x < ntiles) mbar_wait_bounded(((k + 1) & 1) ? bar1 : bar0, (unsigned)(((k + 1) >> 1) & 1));
+    }
+    return;
+  }
+  const double tot = block_sum_d((double)zacc, sh);
+  if (threadIdx.x == 0) A.zpart[blockIdx.x] = tot;
+  if (SC == 1) {
+    __syncthreads();
+    unsigned long long* dst = A.part + (size_t)blockIdx.x * A.n;
+    for (int j = threadIdx.x; j < A.n; j += blockDim.x) dst[j] = acc[j];
+  }
+}
+
 // s_fx[j] += sum of one chunk of the per-block partial sums (grid.y chunks).
 __global__ void k_reduce_products(int n, int nparts, const unsigned long long* __restrict__ part,
                                   unsigned long long* __restrict__ s_fx, const DevState* st) {
@@ -387,6 +601,18 @@ cudaError_t launch_f32_w(const F32Args& A, int W, int grid, int smem, cudaStream
     case 2: k_seg_f32<2, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     case 4: k_seg_f32<4, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     case 8: k_seg_f32<8, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int SC>
+cudaError_t launch_tma_w(const F32Args& A, int W, int grid, int smem, cudaStream_t s) {
+  switch (W) {
+    case 1: k_seg_f32_tma<1, 4, SC><<<grid, kTmaThreads, smem, s>>>(A); break;
+    case 2: k_seg_f32_tma<2, 4, SC><<<grid, kTmaThreads, smem, s>>>(A); break;
+    case 4: k_seg_f32_tma<4, 4, SC><<<grid, kTmaThreads, smem, s>>>(A); break;
+    case 8: k_seg_f32_tma<8, 4, SC><<<grid, kTmaThreads, smem, s>>>(A); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -446,8 +672,55 @@ cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatte
 }
 
 cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s) {
+  if (plan.tma)
+    return plan.scatter == 1 ? launch_tma_w<1>(A, plan.W, plan.grid32, plan.tma_smem, s)
+                             : launch_tma_w<2>(A, plan.W, plan.grid32, plan.tma_smem, s);
   return plan.scatter == 1 ? launch_f32_w<1>(A, plan.W, plan.grid32, plan.smem, s)
                            : launch_f32_w<2>(A, plan.W, plan.grid32, 0, s);
+}
+
+bool tma_plan(int n, int sms, FastPlan* plan) {
+  const int acc = plan->scatter == 1 ? ((n * 8 + 127) / 128) * 128 : 0;
+  const int smem = acc + 2 * StageLayout::bytes;
+  if (smem > kTmaMaxSmem) return false;
+  int nb = 0;
+#define SPFOM_TMA_OCC(WW)                                                                                   \
+  if (plan->W == WW) {                                                                                      \
+    if (plan->scatter == 1) {                                                                               \
+      cudaFuncSetAttribute(k_seg_f32_tma<WW, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_f32_tma<WW, 4, 1>, kTmaThreads, smem);       \
+    } else {                                                                                                \
+      cudaFuncSetAttribute(k_seg_f32_tma<WW, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_f32_tma<WW, 4, 2>, kTmaThreads, smem);       \
+    }                                                                                                       \
+  }
+  SPFOM_TMA_OCC(1)
+  SPFOM_TMA_OCC(2)
+  SPFOM_TMA_OCC(4)
+  SPFOM_TMA_OCC(8)
+#undef SPFOM_TMA_OCC
+  if (nb < 1) return false;
+  plan->tma = 1;
+  plan->tma_smem = smem;
+  plan->acc_bytes = acc;
+  plan->grid32 = nb * sms;
+  return true;
+}
+
+// Tiles of consecutive segments with at most kTileSegs segments and kTileItems
+// products each (host side; seg_ptr is the caller's host array).
+long long make_tiles(const long long* seg_ptr, long long L, long long* tiles_out) {
+  long long nt = 0, l = 0;
+  if (tiles_out) tiles_out[0] = 0;
+  while (l < L) {
+    long long e = l;
+    while (e < L && e - l < kTileSegs && seg_ptr[e + 1] - seg_ptr[l] <= kTileItems) ++e;
+    if (e == l) e = l + 1;  // a single segment never exceeds kTileItems (sets hold <= 32 products)
+    ++nt;
+    if (tiles_out) tiles_out[nt] = e;
+    l = e;
+  }
+  return nt;
 }
 
 cudaError_t launch_reduce_products(const Problem& P, const FastPlan& plan, int nparts,

@@ -260,7 +260,7 @@ def test_large_consideration_set_is_unsupported():
 FP32_ERRORS = {}
 
 
-@pytest.mark.parametrize("name", ["mid_small", "wide"])
+@pytest.mark.parametrize("name", ["mid_small", "wide", "edge"])
 def test_fp32_bulk_error_against_fp64_oracle(name):
     """Binary32 segment solves with binary64 residuals: the error against the
     FP64 oracle is reported per result (FP32_ERRORS) and bounded: one iteration
