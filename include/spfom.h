@@ -77,6 +77,9 @@ typedef struct {
   int32_t path;              /* 0 (default): the certified-decision segment kernel whenever the
                                 instance allows it (sets of <= 32 products, full batch), else the
                                 general kernel; 1: always the general kernel */
+  int32_t graphs;            /* 1 (default): spfom_step replays each whole evaluation period
+                                (eval_every iterations and the evaluation) from a CUDA graph
+                                captured on the ctx stream at first use; 0: direct launches */
   int32_t polish;            /* precision 32 only, 1 (default): once a binary64 evaluation finds
                                 KKT <= kkt_tol, spfom_solve continues with binary64 iterations
                                 until the next evaluation confirms it; 0: stop at the first */

@@ -40,6 +40,8 @@ struct spfom_ctx {
   int sms = 0;
   unsigned long long fallback_host = 0;
   bool polishing = false;  // precision 32: binary64 iterations after the first converged evaluation
+  cudaGraphExec_t period[2] = {nullptr, nullptr};  // one evaluation period, [binary64, binary32 pass]
+  bool period_failed = false;                      // capture unavailable on this stream
 };
 
 namespace {
@@ -64,7 +66,17 @@ spfom_status cuda_fail(spfom_ctx* ctx, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);     \
   } while (0)
 
+void drop_graphs(spfom_ctx* ctx) {
+  for (auto& g : ctx->period)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+  ctx->period_failed = false;
+}
+
 void free_instance(spfom_ctx* ctx) {
+  drop_graphs(ctx);
   for (void* b : ctx->bufs) cudaFreeAsync(b, ctx->stream);
   ctx->bufs.clear();
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
@@ -243,6 +255,7 @@ void spfom_default_params(spfom_params* p) {
   p->max_iters = 100000;
   p->device = 0;
   p->polish = 1;
+  p->graphs = 1;
   p->stream = nullptr;
 }
 
@@ -403,7 +416,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
     spfom::FastPlan plan{};
     if (ctx->p.path == 0 && F >= 30 && spfom::fast_plan(n, kmax, ctx->sms, &plan)) {
       W.fast = true;
-      if (ctx->p.precision == 32 && spfom::tma_plan(n, ctx->sms, &plan)) {
+      if (ctx->p.precision == 32 && spfom::tma_plan(n, kmax, ctx->sms, &plan)) {
         // tiles of consecutive segments for the bulk-copy staging of the binary32 pass
         const long long nt = spfom::make_tiles(reinterpret_cast<const long long*>(I->seg_ptr), L, nullptr);
         std::vector<long long> tiles((size_t)nt + 1);
@@ -481,6 +494,34 @@ spfom_status spfom_reset(spfom_ctx* ctx, const double* y0) {
   return init_state(ctx, y0);
 }
 
+namespace {
+
+// Capture one evaluation period (eval_every iterations, then the evaluation)
+// on the ctx stream into an executable graph. Returns null when the stream
+// cannot be captured (the caller then launches directly).
+cudaGraphExec_t capture_period(spfom_ctx* ctx) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  bool ok = true;
+  for (long long k = 0; k < ctx->p.eval_every && ok; ++k)
+    ok = spfom::launch_iteration(ctx->P, ctx->W, ctx->cfg, ctx->stream) == cudaSuccess;
+  if (ok) ok = spfom::launch_eval(ctx->P, ctx->W, ctx->cfg, ctx->stream) == cudaSuccess;
+  if (cudaStreamEndCapture(ctx->stream, &g) != cudaSuccess || !ok) ok = false;
+  if (ok && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+    ok = false;
+    ex = nullptr;
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  return ok ? ex : nullptr;
+}
+
+}  // namespace
+
 spfom_status spfom_step(spfom_ctx* ctx, int64_t iters, spfom_stats* out) {
   if (!ctx) return SPFOM_EINVAL;
   if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
@@ -495,15 +536,30 @@ spfom_status spfom_step(spfom_ctx* ctx, int64_t iters, spfom_stats* out) {
       ctx->prof_ev.push_back(e);
     }
   }
+  const bool graphs = ctx->p.graphs != 0 && !prof && E > 0;
+  const long long per_iter = spfom::kernel_launches_per_iteration(ctx->W, ctx->cfg);
   SPFOM_CUDA(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
   long long t = ctx->host_t, launches = 0;
-  for (int64_t k = 0; k < iters; ++k) {
+  for (int64_t k = 0; k < iters;) {
+    if (graphs && t % E == 0 && iters - k >= E && !ctx->period_failed) {
+      cudaGraphExec_t& ex = ctx->period[ctx->cfg.f32 ? 1 : 0];
+      if (!ex) ex = capture_period(ctx);
+      if (ex) {
+        SPFOM_CUDA(ctx, cudaGraphLaunch(ex, ctx->stream));
+        launches += E * per_iter + spfom::kernel_launches_per_eval();
+        k += E;
+        t += E;
+        continue;
+      }
+      ctx->period_failed = true;
+    }
     cudaError_t e = spfom::launch_iteration(ctx->P, ctx->W, ctx->cfg, ctx->stream,
                                             prof ? ctx->prof_ev[2 * k] : nullptr,
                                             prof ? ctx->prof_ev[2 * k + 1] : nullptr);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "iteration launch");
-    launches += spfom::kernel_launches_per_iteration(ctx->W, ctx->cfg);
+    launches += per_iter;
     ++t;
+    ++k;
     if (E > 0 && t % E == 0) {
       e = spfom::launch_eval(ctx->P, ctx->W, ctx->cfg, ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "evaluation launch");

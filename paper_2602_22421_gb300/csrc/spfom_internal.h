@@ -57,6 +57,7 @@ struct FastPlan {
   int grid_eval;      // blocks of the evaluation launch
   int reduce_chunks;  // grid.y of k_reduce_products
   int tma;            // 1: the binary32 pass runs k_seg_f32_tma (tile staging by bulk copies)
+  int tma_W;          // its lanes per segment (8 products per lane)
   int tma_smem;       // its dynamic shared memory: product sums + two stages
   int acc_bytes;      // bytes of the product sums at the start of that memory
 };
@@ -157,7 +158,7 @@ int kernel_launches_per_eval();
 bool fast_plan(int n, int kmax, int sms, FastPlan* plan);
 cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s);
 cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s);
-bool tma_plan(int n, int sms, FastPlan* plan);
+bool tma_plan(int n, int kmax, int sms, FastPlan* plan);
 long long make_tiles(const long long* seg_ptr, long long L, long long* tiles_out);
 cudaError_t launch_reduce_products(const Problem& P, const FastPlan& plan, int nparts,
                                    const unsigned long long* part, unsigned long long* s_fx, const DevState* st,

@@ -485,29 +485,23 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_seg_f32_tma(F32Args A) {
     for (int ls = group; ls < nseg; ls += gpb) {
       const int b = (int)(segp[ls] - ibase);
       const int K = (int)(segp[ls + 1] - segp[ls]);
-      int jv[P];
-      float vv[P], tv[P], af[P];
+      // per slot: a = m v (binary32) for candidates, b = v - w; ids and v are re-read
+      // from shared memory by the scatter, so they need no registers here
+      float tv[P], af[P];
       unsigned cand = 0;
 #pragma unroll
       for (int p = 0; p < P; ++p) {
         const int kk = lane + p * W;
-        jv[p] = 0;
-        vv[p] = tv[p] = af[p] = 0.f;
+        tv[p] = af[p] = 0.f;
         if (kk < K) {
-          jv[p] = prod_s[b + kk];
-          vv[p] = v_s[b + kk];
           tv[p] = vt_s[b + kk];
-        }
-      }
-#pragma unroll
-      for (int p = 0; p < P; ++p)
-        if (lane + p * W < K) {
-          const float m = A.marg32[jv[p]];
+          const float m = A.marg32[prod_s[b + kk]];
           if (m > 0.f) {
             cand |= 1u << p;
-            af[p] = m * vv[p];
+            af[p] = m * v_s[b + kk];
           }
         }
+      }
       const float lam = lam_s[ls], vt0 = vt0_s[ls];
       float R = 0.f, Nsel = 0.f, Dsel = 0.f;
       unsigned sel = 0xffffffffu;
@@ -537,8 +531,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_seg_f32_tma(F32Args A) {
       if (SC != 0) {
 #pragma unroll
         for (int p = 0; p < P; ++p)
-          if ((sel >> p) & 1u)
-            atomicAdd((SC == 1 ? acc : A.s_fx) + jv[p], fixed_product32(q, vv[p], A.fx_bits));
+          if ((sel >> p) & 1u) {
+            const int kk = b + lane + p * W;
+            atomicAdd((SC == 1 ? acc : A.s_fx) + prod_s[kk], fixed_product32(q, v_s[kk], A.fx_bits));
+          }
       }
     }
     __syncthreads();  // every thread is done with this stage
@@ -608,11 +604,10 @@ cudaError_t launch_f32_w(const F32Args& A, int W, int grid, int smem, cudaStream
 
 template <int SC>
 cudaError_t launch_tma_w(const F32Args& A, int W, int grid, int smem, cudaStream_t s) {
-  switch (W) {
-    case 1: k_seg_f32_tma<1, 4, SC><<<grid, kTmaThreads, smem, s>>>(A); break;
-    case 2: k_seg_f32_tma<2, 4, SC><<<grid, kTmaThreads, smem, s>>>(A); break;
-    case 4: k_seg_f32_tma<4, 4, SC><<<grid, kTmaThreads, smem, s>>>(A); break;
-    case 8: k_seg_f32_tma<8, 4, SC><<<grid, kTmaThreads, smem, s>>>(A); break;
+  switch (W) {  // 8 products per lane
+    case 1: k_seg_f32_tma<1, 8, SC><<<grid, kTmaThreads, smem, s>>>(A); break;
+    case 2: k_seg_f32_tma<2, 8, SC><<<grid, kTmaThreads, smem, s>>>(A); break;
+    case 4: k_seg_f32_tma<4, 8, SC><<<grid, kTmaThreads, smem, s>>>(A); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -673,34 +668,37 @@ cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatte
 
 cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s) {
   if (plan.tma)
-    return plan.scatter == 1 ? launch_tma_w<1>(A, plan.W, plan.grid32, plan.tma_smem, s)
-                             : launch_tma_w<2>(A, plan.W, plan.grid32, plan.tma_smem, s);
+    return plan.scatter == 1 ? launch_tma_w<1>(A, plan.tma_W, plan.grid32, plan.tma_smem, s)
+                             : launch_tma_w<2>(A, plan.tma_W, plan.grid32, plan.tma_smem, s);
   return plan.scatter == 1 ? launch_f32_w<1>(A, plan.W, plan.grid32, plan.smem, s)
                            : launch_f32_w<2>(A, plan.W, plan.grid32, 0, s);
 }
 
-bool tma_plan(int n, int sms, FastPlan* plan) {
+bool tma_plan(int n, int kmax, int sms, FastPlan* plan) {
+  int W8 = 1;  // lanes per segment with 8 products per lane
+  while (W8 * 8 < kmax) W8 <<= 1;
+  if (W8 > 4) return false;
   const int acc = plan->scatter == 1 ? ((n * 8 + 127) / 128) * 128 : 0;
   const int smem = acc + 2 * StageLayout::bytes;
   if (smem > kTmaMaxSmem) return false;
   int nb = 0;
 #define SPFOM_TMA_OCC(WW)                                                                                   \
-  if (plan->W == WW) {                                                                                      \
+  if (W8 == WW) {                                                                                           \
     if (plan->scatter == 1) {                                                                               \
-      cudaFuncSetAttribute(k_seg_f32_tma<WW, 4, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_f32_tma<WW, 4, 1>, kTmaThreads, smem);       \
+      cudaFuncSetAttribute(k_seg_f32_tma<WW, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_f32_tma<WW, 8, 1>, kTmaThreads, smem);       \
     } else {                                                                                                \
-      cudaFuncSetAttribute(k_seg_f32_tma<WW, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_f32_tma<WW, 4, 2>, kTmaThreads, smem);       \
+      cudaFuncSetAttribute(k_seg_f32_tma<WW, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_f32_tma<WW, 8, 2>, kTmaThreads, smem);       \
     }                                                                                                       \
   }
   SPFOM_TMA_OCC(1)
   SPFOM_TMA_OCC(2)
   SPFOM_TMA_OCC(4)
-  SPFOM_TMA_OCC(8)
 #undef SPFOM_TMA_OCC
   if (nb < 1) return false;
   plan->tma = 1;
+  plan->tma_W = W8;
   plan->tma_smem = smem;
   plan->acc_bytes = acc;
   plan->grid32 = nb * sms;

@@ -305,3 +305,20 @@ def test_fp32_bulk_solve_matches_fp64_objective():
         st = s.solve()
         assert st["converged"] == 1 and st["iter_precision"] == 32
         assert st["dual_avg"] == pytest.approx(ost["dual_avg"], rel=1e-4)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_graph_replay_equals_direct_launches(precision):
+    """Whole evaluation periods replayed from a CUDA graph give bit-identical
+    iterates to direct launches (the sums are fixed point, the partial sums
+    fold in block order)."""
+    inst = mid_small()
+    out = {}
+    for graphs in (0, 1):
+        with Solver(inst, precision=precision, graphs=graphs) as s:
+            s.step(5)      # leaves the period boundary: the next call starts with direct launches
+            st = s.step(195)
+            out[graphs] = (s.duals(), s.vector(3), st["kkt"], st["restarts"], st["kernel_launches"])
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2] and out[0][3] == out[1][3] and out[0][4] == out[1][4]
