@@ -49,7 +49,8 @@ constexpr int kTmaMaxSmem = 226 * 1024;
 
 // Launch plan of the certified-decision segment kernel.
 struct FastPlan {
-  int W;              // lanes per segment (4 products per lane)
+  int W;              // lanes per segment of k_seg_f32 (4 products per lane)
+  int W8;             // lanes per segment of k_seg_fast (8 products per lane)
   int scatter;        // 1: shared-memory sums + per-block partials; 2: global atomics
   int smem;           // bytes of the per-block product accumulator (scatter 1)
   int grid;           // blocks of the binary64 iterate launch (= number of partial sums)

@@ -129,8 +129,9 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
   for (long long l = blockIdx.x * gpb + threadIdx.x / W; l < Pr.L; l += ngroups) {
     const long long b = Pr.seg_ptr[l];
     const int K = (int)(Pr.seg_ptr[l + 1] - b);
+    // Registers hold the binary32 images a = m v, b = vt and the product ids;
+    // the binary64 values are read again (L1) for the products chosen.
     int jv[P];
-    double mv[P], vv[P], tv[P];
     float af[P], bf[P];
     unsigned cand = 0;
     bool ok = true;
@@ -138,22 +139,14 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
     for (int p = 0; p < P; ++p) {
       const int k = lane + p * W;
       jv[p] = 0;
-      mv[p] = vv[p] = tv[p] = 0.0;
       af[p] = bf[p] = 0.f;
       if (k < K) {
         jv[p] = Pr.seg_prod[b + k];
-        vv[p] = Pr.v[b + k];
-        tv[p] = Pr.vt[b + k];
-      }
-    }
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-      if (lane + p * W < K) {
-        mv[p] = A.marg[jv[p]];
-        if (__double_as_longlong(mv[p]) > 0) {  // m_j > 0
+        const double m = A.marg[jv[p]];
+        if (__double_as_longlong(m) > 0) {  // m_j > 0
           cand |= 1u << p;
-          af[p] = f32_trunc(mv[p], ok) * f32_trunc(vv[p], ok);
-          bf[p] = f32_trunc(tv[p], ok);
+          af[p] = f32_trunc(m, ok) * f32_trunc(Pr.v[b + k], ok);
+          bf[p] = f32_trunc(Pr.vt[b + k], ok);
         }
       }
     }
@@ -204,11 +197,12 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
 #pragma unroll
         for (int p = 0; p < P; ++p)
           if ((cand >> p) & 1u) {
-            const double a = mv[p] * vv[p];
-            if (a > Rd * tv[p]) {
+            const int k = lane + p * W;
+            const double a = A.marg[jv[p]] * Pr.v[b + k], t = Pr.vt[b + k];
+            if (a > Rd * t) {
               s |= 1u << p;
               N += a;
-              D += tv[p];
+              D += t;
             }
           }
         if (__all_sync(gmask, s == prev)) break;
@@ -227,8 +221,9 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
 #pragma unroll
     for (int p = 0; p < P; ++p)
       if ((S >> p) & 1u) {
-        Dl += tv[p];
-        Nl = fma(mv[p], vv[p], Nl);
+        const int k = lane + p * W;
+        Dl += Pr.vt[b + k];
+        Nl = fma(A.marg[jv[p]], Pr.v[b + k], Nl);
       }
 #pragma unroll
     for (int o = W >> 1; o > 0; o >>= 1) {
@@ -240,7 +235,8 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
     if (SC != 0) {
 #pragma unroll
       for (int p = 0; p < P; ++p)
-        if ((S >> p) & 1u) atomicAdd((SC == 1 ? acc : A.s_fx) + jv[p], fixed_product(q, vv[p], A.fx_bits));
+        if ((S >> p) & 1u)
+          atomicAdd((SC == 1 ? acc : A.s_fx) + jv[p], fixed_product(q, Pr.v[b + lane + p * W], A.fx_bits));
     }
   }
   const double tot = block_sum_d(zacc, sh);
@@ -580,11 +576,10 @@ __global__ void k_reduce_products(int n, int nparts, const unsigned long long* _
 
 template <int SC>
 cudaError_t launch_fast_w(const FastArgs& A, int W, int grid, int smem, cudaStream_t s) {
-  switch (W) {
-    case 1: k_seg_fast<1, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
-    case 2: k_seg_fast<2, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
-    case 4: k_seg_fast<4, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
-    case 8: k_seg_fast<8, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+  switch (W) {  // 8 products per lane
+    case 1: k_seg_fast<1, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 2: k_seg_fast<2, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 4: k_seg_fast<4, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -622,19 +617,23 @@ int blocks_per_sm(K kernel, int smem) {
 }
 
 int occupancy(int W, int sc, int smem, bool f32) {
-#define SPFOM_OCC(WW)                                                                          \
-  if (W == WW) {                                                                               \
-    if (f32) return sc == 1 ? blocks_per_sm(k_seg_f32<WW, 4, 1>, smem)                        \
-                            : blocks_per_sm(k_seg_f32<WW, 4, 2>, 0);                           \
-    return sc == 0 ? blocks_per_sm(k_seg_fast<WW, 4, 0>, 0)                                   \
-                   : (sc == 1 ? blocks_per_sm(k_seg_fast<WW, 4, 1>, smem)                     \
-                              : blocks_per_sm(k_seg_fast<WW, 4, 2>, 0));                      \
-  }
-  SPFOM_OCC(1)
-  SPFOM_OCC(2)
-  SPFOM_OCC(4)
-  SPFOM_OCC(8)
-#undef SPFOM_OCC
+#define SPFOM_OCC32(WW)                                                                        \
+  if (f32 && W == WW)                                                                          \
+    return sc == 1 ? blocks_per_sm(k_seg_f32<WW, 4, 1>, smem) : blocks_per_sm(k_seg_f32<WW, 4, 2>, 0);
+#define SPFOM_OCC64(WW)                                                                        \
+  if (!f32 && W == WW)                                                                         \
+    return sc == 0 ? blocks_per_sm(k_seg_fast<WW, 8, 0>, 0)                                   \
+                   : (sc == 1 ? blocks_per_sm(k_seg_fast<WW, 8, 1>, smem)                     \
+                              : blocks_per_sm(k_seg_fast<WW, 8, 2>, 0));
+  SPFOM_OCC32(1)
+  SPFOM_OCC32(2)
+  SPFOM_OCC32(4)
+  SPFOM_OCC32(8)
+  SPFOM_OCC64(1)
+  SPFOM_OCC64(2)
+  SPFOM_OCC64(4)
+#undef SPFOM_OCC32
+#undef SPFOM_OCC64
   return 0;
 }
 
@@ -642,15 +641,17 @@ int occupancy(int W, int sc, int smem, bool f32) {
 
 bool fast_plan(int n, int kmax, int sms, FastPlan* plan) {
   if (kmax > 32) return false;
-  int W = 1;
+  int W = 1, W8 = 1;
   while (W * 4 < kmax) W <<= 1;
+  while (W8 * 8 < kmax) W8 <<= 1;
   const int smem = n * (int)sizeof(unsigned long long);
   const int sc = smem <= kFastMaxSmem ? 1 : 2;
-  const int nb = occupancy(W, sc, smem, false);
+  const int nb = occupancy(W8, sc, smem, false);
   const int nb32 = occupancy(W, sc, smem, true);
-  const int nbe = occupancy(W, 0, 0, false);
+  const int nbe = occupancy(W8, 0, 0, false);
   if (nb <= 0 || nbe <= 0 || nb32 <= 0) return false;
   plan->W = W;
+  plan->W8 = W8;
   plan->scatter = sc;
   plan->smem = sc == 1 ? smem : 0;
   plan->grid = nb * sms;
@@ -661,9 +662,9 @@ bool fast_plan(int n, int kmax, int sms, FastPlan* plan) {
 }
 
 cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s) {
-  if (!scatter) return launch_fast_w<0>(A, plan.W, plan.grid_eval, 0, s);
-  return plan.scatter == 1 ? launch_fast_w<1>(A, plan.W, plan.grid, plan.smem, s)
-                           : launch_fast_w<2>(A, plan.W, plan.grid, 0, s);
+  if (!scatter) return launch_fast_w<0>(A, plan.W8, plan.grid_eval, 0, s);
+  return plan.scatter == 1 ? launch_fast_w<1>(A, plan.W8, plan.grid, plan.smem, s)
+                           : launch_fast_w<2>(A, plan.W8, plan.grid, 0, s);
 }
 
 cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s) {
