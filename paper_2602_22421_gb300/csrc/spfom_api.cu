@@ -256,6 +256,7 @@ void spfom_default_params(spfom_params* p) {
   p->device = 0;
   p->polish = 1;
   p->graphs = 1;
+  p->pipeline = 1;
   p->stream = nullptr;
 }
 
@@ -374,12 +375,14 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   static_assert(sizeof(long long) == sizeof(int64_t), "int64");
   SPFOM_TRY(upload(ctx, &d_segptr, reinterpret_cast<const long long*>(I->seg_ptr), (size_t)L + 1, kSlack));
   SPFOM_TRY(upload(ctx, &d_prod, I->seg_prod, (size_t)nnz, kSlack));
-  SPFOM_TRY(upload(ctx, &d_v, I->v, (size_t)nnz));
+  SPFOM_TRY(upload(ctx, &d_v, I->v, (size_t)nnz, kSlack));
   if (I->w) SPFOM_TRY(upload(ctx, &d_w, I->w, (size_t)nnz));
-  SPFOM_TRY(upload(ctx, &d_lam, I->lam, (size_t)L));
+  SPFOM_TRY(upload(ctx, &d_lam, I->lam, (size_t)L, kSlack));
   SPFOM_TRY(upload(ctx, &d_v0, I->v0, (size_t)L));
-  SPFOM_TRY(dalloc(ctx, &d_vt, (size_t)nnz));
-  SPFOM_TRY(dalloc(ctx, &d_vt0, (size_t)L));
+  SPFOM_TRY(dalloc(ctx, &d_vt, (size_t)nnz + kSlack));
+  SPFOM_TRY(dalloc(ctx, &d_vt0, (size_t)L + kSlack));
+  SPFOM_CUDA(ctx, cudaMemsetAsync(d_vt + nnz, 0, kSlack * sizeof(double), ctx->stream));
+  SPFOM_CUDA(ctx, cudaMemsetAsync(d_vt0 + L, 0, kSlack * sizeof(double), ctx->stream));
   P.r = d_r; P.c = d_c; P.a_ptr = d_aptr; P.a_idx = d_aidx; P.a_val = d_aval;
   P.at_ptr = d_atptr; P.at_idx = d_atidx; P.at_val = d_atval;
   P.seg_ptr = d_segptr; P.seg_prod = d_prod; P.v = d_v; P.vt = d_vt; P.lam = d_lam; P.vt0 = d_vt0;
@@ -416,6 +419,14 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
     spfom::FastPlan plan{};
     if (ctx->p.path == 0 && F >= 30 && spfom::fast_plan(n, kmax, ctx->sms, &plan)) {
       W.fast = true;
+      if (ctx->p.pipeline && spfom::pipe_plan(n, ctx->sms, &plan)) {
+        // tiles of consecutive segments for the binary64 pipeline
+        const long long nt = spfom::make_tiles64(reinterpret_cast<const long long*>(I->seg_ptr), L, nullptr);
+        std::vector<long long> tiles((size_t)nt + 1);
+        spfom::make_tiles64(reinterpret_cast<const long long*>(I->seg_ptr), L, tiles.data());
+        SPFOM_TRY(upload(ctx, &W.tile64_ptr, tiles.data(), tiles.size()));
+        W.ntiles64 = nt;
+      }
       if (ctx->p.precision == 32 && spfom::tma_plan(n, kmax, ctx->sms, &plan)) {
         // tiles of consecutive segments for the bulk-copy staging of the binary32 pass
         const long long nt = spfom::make_tiles(reinterpret_cast<const long long*>(I->seg_ptr), L, nullptr);
@@ -428,7 +439,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       W.fx_scale = std::ldexp(1.0, F);
       W.fx_bits = F;
       W.inv_fx_scale = std::ldexp(1.0, -F);
-      W.zparts_iter = std::max(plan.grid, plan.grid32);
+      W.zparts_iter = std::max(std::max(plan.grid, plan.grid32), plan.pipe ? plan.pipe_grid : 0);
       W.zparts_eval = plan.grid_eval;
       if (plan.scatter == 1)
         SPFOM_TRY(dalloc(ctx, &W.part, (size_t)std::max(plan.grid, plan.grid32) * (size_t)(n > 0 ? n : 1)));

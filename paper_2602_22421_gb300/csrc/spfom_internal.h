@@ -46,6 +46,9 @@ constexpr int kFastThreads = 512;
 constexpr int kFastMaxSmem = 200 * 1024;
 constexpr int kTmaThreads = 1024;
 constexpr int kTmaMaxSmem = 226 * 1024;
+constexpr int kPipeThreads = 512;    // binary64 pipeline: 1 producer warp + 15 consumer warps
+constexpr int kTile64Segs = 256;     // binary64 pipeline tile: segments
+constexpr int kTile64Items = 2048;   // binary64 pipeline tile: products
 
 // Launch plan of the certified-decision segment kernel.
 struct FastPlan {
@@ -61,6 +64,8 @@ struct FastPlan {
   int tma_W;          // its lanes per segment (8 products per lane)
   int tma_smem;       // its dynamic shared memory: product sums + two stages
   int acc_bytes;      // bytes of the product sums at the start of that memory
+  int pipe;           // 1: the binary64 pass runs k_seg_fast_pipe (warp-specialised TMA pipeline)
+  int pipe_smem, pipe_acc_bytes, pipe_grid;
 };
 
 // Work buffers of one ctx.
@@ -100,6 +105,8 @@ struct Work {
   float* marg32;
   long long* tile_ptr;  // [ntiles+1] (binary32 tile staging)
   long long ntiles;
+  long long* tile64_ptr;  // [ntiles64+1] (binary64 pipeline tiles)
+  long long ntiles64;
 };
 
 struct FastArgs {
@@ -112,6 +119,11 @@ struct FastArgs {
   unsigned long long* fallbacks;
   int fx_bits;  // F of the fixed-point scale 2^F
   unsigned long long* s_fx;  // product sums when the plan scatters with global atomics
+  // pipeline staging (k_seg_fast_pipe)
+  const long long* tile_ptr;
+  long long ntiles;
+  int acc_bytes;
+  DevState* st_rw;
 };
 
 struct F32Args {
@@ -160,6 +172,10 @@ bool fast_plan(int n, int kmax, int sms, FastPlan* plan);
 cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s);
 cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s);
 bool tma_plan(int n, int kmax, int sms, FastPlan* plan);
+// spfom_segments_tma.cu
+bool pipe_plan(int n, int sms, FastPlan* plan);
+cudaError_t launch_seg_fast_pipe(const FastArgs& A, const FastPlan& plan, cudaStream_t s);
+long long make_tiles64(const long long* seg_ptr, long long L, long long* tiles_out);
 long long make_tiles(const long long* seg_ptr, long long L, long long* tiles_out);
 cudaError_t launch_reduce_products(const Problem& P, const FastPlan& plan, int nparts,
                                    const unsigned long long* part, unsigned long long* s_fx, const DevState* st,

@@ -412,9 +412,15 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
     e = launch_seg_f32(A, Wk.plan, s);
     zparts = Wk.plan.grid32;
   } else if (fast) {
-    FastArgs A{P, Wk.marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, Wk.s_fx};
-    e = launch_seg_fast(A, Wk.plan, true, s);
-    zparts = Wk.plan.grid;
+    FastArgs A{P, Wk.marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, Wk.s_fx,
+               Wk.tile64_ptr, Wk.ntiles64, Wk.plan.pipe_acc_bytes, Wk.st};
+    if (Wk.plan.pipe) {
+      e = launch_seg_fast_pipe(A, Wk.plan, s);
+      zparts = Wk.plan.pipe_grid;
+    } else {
+      e = launch_seg_fast(A, Wk.plan, true, s);
+      zparts = Wk.plan.grid;
+    }
   } else {
     e = sampled ? launch_segments_w<kIterate, true>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s)
                 : launch_segments_w<kIterate, false>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s);
@@ -434,7 +440,8 @@ cudaError_t launch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, 
   k_margins<<<gn, kVecThreads, 0, s>>>(P, nullptr, Wk.sum_y, 1, Wk.marg_eval, nullptr, nullptr, Wk.st);
   cudaError_t e;
   if (Wk.fast) {
-    FastArgs A{P, Wk.marg_eval, nullptr, Wk.zpart_eval, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, nullptr};
+    FastArgs A{P, Wk.marg_eval, nullptr, Wk.zpart_eval, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, nullptr,
+               nullptr, 0, 0, Wk.st};
     e = launch_seg_fast(A, Wk.plan, false, s);
   } else {
     e = launch_segments_w<kEvalSum, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, Wk.st, cfg, s);

@@ -34,7 +34,8 @@ class Params(C.Structure):
                 ("batch_frac", C.c_double), ("seed", C.c_uint64), ("eval_every", C.c_int64),
                 ("restart_beta", C.c_double), ("restart_artificial", C.c_double),
                 ("restart_tau_decay", C.c_double), ("kkt_tol", C.c_double), ("max_iters", C.c_int64),
-                ("device", C.c_int32), ("profile", C.c_int32), ("path", C.c_int32), ("graphs", C.c_int32),
+                ("device", C.c_int32), ("profile", C.c_int32), ("path", C.c_int32), ("pipeline", C.c_int32),
+                ("graphs", C.c_int32),
                 ("polish", C.c_int32),
                 ("stream", C.c_void_p)]
 
