@@ -77,9 +77,11 @@ typedef struct {
   int32_t path;              /* 0 (default): the certified-decision segment kernel whenever the
                                 instance allows it (sets of <= 32 products, full batch), else the
                                 general kernel; 1: always the general kernel */
-  int32_t pipeline;          /* 1 (default): the binary64 certified pass streams tiles of segments
-                                into shared memory through a warp-specialised bulk-copy (TMA)
-                                pipeline when shared memory allows; 0: plain loads */
+  int32_t pipeline;          /* 0 (default): the binary64 certified pass reads with plain loads;
+                                1: it streams tiles of segments into shared memory through a
+                                warp-specialised bulk-copy (TMA) pipeline when shared memory allows
+                                (slower on the mid instance: the stages crowd the L1 cache that
+                                holds the margins) */
   int32_t graphs;            /* 1 (default): spfom_step replays each whole evaluation period
                                 (eval_every iterations and the evaluation) from a CUDA graph
                                 captured on the ctx stream at first use; 0: direct launches */

@@ -256,7 +256,7 @@ void spfom_default_params(spfom_params* p) {
   p->device = 0;
   p->polish = 1;
   p->graphs = 1;
-  p->pipeline = 1;
+  p->pipeline = 0;
   p->stream = nullptr;
 }
 
