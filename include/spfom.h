@@ -203,6 +203,37 @@ spfom_status spfom_evaluate(spfom_ctx* ctx, const double* y, double* z_out, doub
 /* Read the current state without running anything. */
 spfom_status spfom_get_stats(spfom_ctx* ctx, spfom_stats* out);
 
+/* ---- Batches and periods (Section 5.1) ------------------------------------
+ * Load `count` instances as one batch, replacing what the ctx held. The batch
+ * is the block-diagonal union of the instances (concatenated in order: their
+ * products, resources and segments keep their relative order), so one launch
+ * per kernel serves every instance, while each instance keeps its own step
+ * size, regulariser, epoch averages, KKT residual, restarts and convergence;
+ * a converged instance is frozen and its segments are skipped. spfom_step,
+ * spfom_solve, spfom_duals, spfom_vector and spfom_reset then act on the whole
+ * batch (vectors concatenated in instance order; spfom_solve returns when
+ * every instance has converged); spfom_stats reports the batch (iterations of
+ * the longest-running instance, summed objectives, largest residuals).
+ * Same validation as spfom_load_instance (the message names the instance);
+ * ENOTSUP unless every set holds <= 32 products. */
+spfom_status spfom_load_batch(spfom_ctx* ctx, const spfom_instance* insts, int32_t count);
+
+/* Per-instance state of a batch: out[count] (caller-owned). ESTATE without a batch. */
+spfom_status spfom_batch_stats(spfom_ctx* ctx, spfom_stats* out);
+
+/* Replace the capacities c (host [m], >= 0, or NULL) and/or the arrival rates
+ * lam (host [L], >= 0, or NULL) of the loaded instance or batch -- the
+ * multi-period re-solve of Section 5.1, with inventory depleted by the previous
+ * period's sales and demand rescaled -- without reloading its structure. The
+ * iteration state is kept; the next spfom_reset / spfom_solve restarts from the
+ * given duals (warm start) with step sizes recomputed from the new capacities. */
+spfom_status spfom_update(spfom_ctx* ctx, const double* c, const double* lam);
+
+/* Expected product sales (host [n] out) when every segment is offered its best
+ * assortment at duals y (host [m], >= 0): bid-price control of Section 5.1
+ * with bid prices y. Leaves the iteration state alone. */
+spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out);
+
 /* Free the ctx and all its device memory (NULL is a no-op). */
 void spfom_destroy(spfom_ctx* ctx);
 

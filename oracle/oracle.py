@@ -177,8 +177,8 @@ class Oracle:
     def default_tau(self, tau0: float) -> float:
         return self._lib.orc_default_tau(C.byref(self._c), tau0)
 
-    def run(self, params: Optional[Params] = None) -> "OracleRun":
-        return OracleRun(self, params or Params())
+    def run(self, params: Optional[Params] = None, y0=None) -> "OracleRun":
+        return OracleRun(self, params or Params(), y0)
 
 
 def sample_hash(seed: int, t: int, l: int) -> int:
@@ -199,6 +199,8 @@ class OracleRun:
         self._st = _State(_p(self.y, _f64p), _p(self.sum_y, _f64p), _p(self.sum_g, _f64p), _p(self.s, _f64p),
                           _p(self.g, _f64p), _p(self.x_cur, _f64p))
         orc._lib.orc_state_init(C.byref(orc._c), C.byref(self._pc), C.byref(self._st))
+        if y0 is not None:  # orc_state_init leaves y alone
+            self.y[:] = np.asarray(y0, np.float64)
 
     def step(self, iters: int) -> dict:
         rc = self.orc._lib.orc_run(C.byref(self.orc._c), C.byref(self._pc), C.byref(self._st), iters)

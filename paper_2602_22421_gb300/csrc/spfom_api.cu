@@ -42,6 +42,17 @@ struct spfom_ctx {
   bool polishing = false;  // precision 32: binary64 iterations after the first converged evaluation
   cudaGraphExec_t period[2] = {nullptr, nullptr};  // one evaluation period, [binary64, binary32 pass]
   bool period_failed = false;                      // capture unavailable on this stream
+  // batch (spfom_load_batch)
+  struct BatchSpec {
+    int count;
+    std::vector<int> res_ptr, prod_ptr;
+    std::vector<long long> seg_off;
+  };
+  const BatchSpec* loading_batch = nullptr;  // set while spfom_load_batch loads the union
+  BatchSpec batch;
+  std::vector<double> inst_tau;              // per-instance initial step sizes
+  std::vector<double> inst_mean_r;           // per-instance mean price (step size after spfom_update)
+  std::vector<spfom::InstState> h_inst;      // last state read back
 };
 
 namespace {
@@ -192,6 +203,23 @@ spfom_status init_state(spfom_ctx* ctx, const double* y0) {
   st.kkt = st.pinf = st.gap = st.dual_avg = st.primal_avg = NAN;
   st.kkt_anchor = INFINITY;
   SPFOM_CUDA(ctx, cudaMemcpyAsync(W.st, &st, sizeof st, cudaMemcpyHostToDevice, ctx->stream));
+  if (W.batch) {
+    const int cnt = W.bm.count;
+    ctx->h_inst.assign((size_t)cnt, spfom::InstState{});
+    for (int b = 0; b < cnt; ++b) {
+      spfom::InstState& I = ctx->h_inst[b];
+      I.tau = ctx->inst_tau[b];
+      I.mu = ctx->p.mu;
+      I.z_sum = I.P = I.dual_iter = NAN;
+      I.kkt = I.pinf = I.gap = I.dual_avg = I.primal_avg = NAN;
+      I.kkt_anchor = INFINITY;
+    }
+    SPFOM_CUDA(ctx, cudaMemcpyAsync(W.bm.inst, ctx->h_inst.data(), sizeof(spfom::InstState) * cnt,
+                                    cudaMemcpyHostToDevice, ctx->stream));
+    SPFOM_CUDA(ctx, cudaMemsetAsync(W.bm.conv, 0, sizeof(int) * cnt, ctx->stream));
+    SPFOM_CUDA(ctx, cudaMemsetAsync(W.bm.z_seg, 0, sizeof(double) * (P.L ? P.L : 1), ctx->stream));
+    SPFOM_CUDA(ctx, cudaMemsetAsync(W.bm.cy_res, 0, sizeof(double) * (P.m ? P.m : 1), ctx->stream));
+  }
   SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   ctx->host_t = 0;
   ctx->polishing = false;
@@ -222,11 +250,46 @@ void fill_stats(const spfom_ctx* ctx, const DevState& st, double secs, spfom_sta
   s.tau = st.tau;
   s.mu = st.mu;
   s.seconds = secs;
+  if (ctx->W.batch && !ctx->h_inst.empty()) {
+    // the batch: iterations and evaluations of the longest-running instance, sums of the
+    // objectives and counts, the largest residuals; converged when every instance is
+    long long it = 0, ev = 0, rs = 0, ep = 0;
+    double kkt = 0, pinf = 0, gap = 0, da = 0, pa = 0, di = 0, zs = 0, rv = 0, srv = 0;
+    int conv = 1;
+    for (const auto& I : ctx->h_inst) {
+      it = std::max(it, I.t);
+      ev = std::max(ev, I.evals);
+      ep = std::max(ep, I.count);
+      rs += I.restarts;
+      kkt = std::max(kkt, std::isnan(I.kkt) ? INFINITY : I.kkt);
+      pinf = std::max(pinf, std::isnan(I.pinf) ? INFINITY : I.pinf);
+      gap = std::max(gap, std::isnan(I.gap) ? INFINITY : I.gap);
+      da += I.dual_avg; pa += I.primal_avg; di += I.dual_iter; zs += I.z_sum; rv += I.P; srv += I.sum_P;
+      conv &= I.converged;
+    }
+    s.iters = it; s.evals = ev; s.restarts = rs; s.epoch_iters = ep; s.converged = conv;
+    s.kkt = kkt; s.pinf = pinf; s.gap = gap; s.dual_avg = da; s.primal_avg = pa; s.dual_iter = di;
+    s.z_sum = zs; s.revenue = rv; s.sum_revenue = srv;
+    s.tau = ctx->h_inst[0].tau; s.mu = ctx->h_inst[0].mu;
+  }
+  *out = s;
+}
+
+void inst_stats(const spfom_ctx* ctx, const spfom::InstState& I, spfom_stats* out) {
+  spfom_stats s{};
+  s.iters = I.t; s.restarts = I.restarts; s.evals = I.evals; s.epoch_iters = I.count; s.converged = I.converged;
+  s.kkt = I.kkt; s.pinf = I.pinf; s.gap = I.gap; s.dual_avg = I.dual_avg; s.primal_avg = I.primal_avg;
+  s.dual_iter = I.dual_iter; s.z_sum = I.z_sum; s.revenue = I.P; s.sum_revenue = I.sum_P; s.tau = I.tau; s.mu = I.mu;
+  s.fast_path = 1;
+  s.iter_precision = ctx->cfg.f32 ? 32 : 64;
   *out = s;
 }
 
 spfom_status read_state(spfom_ctx* ctx, DevState* st) {
   SPFOM_CUDA(ctx, cudaMemcpyAsync(st, ctx->W.st, sizeof *st, cudaMemcpyDeviceToHost, ctx->stream));
+  if (ctx->W.batch)
+    SPFOM_CUDA(ctx, cudaMemcpyAsync(ctx->h_inst.data(), ctx->W.bm.inst, sizeof(spfom::InstState) * ctx->W.bm.count,
+                                    cudaMemcpyDeviceToHost, ctx->stream));
   if (ctx->W.fallbacks)
     SPFOM_CUDA(ctx, cudaMemcpyAsync(&ctx->fallback_host, ctx->W.fallbacks, sizeof(unsigned long long),
                                     cudaMemcpyDeviceToHost, ctx->stream));
@@ -403,6 +466,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   SPFOM_TRY(dalloc(ctx, &W.sum_g, (size_t)m));
   SPFOM_TRY(dalloc(ctx, &W.g, (size_t)m));
   SPFOM_TRY(dalloc(ctx, &W.y_eval, (size_t)m));
+  SPFOM_TRY(dalloc(ctx, &W.s_eval, (size_t)n));
   SPFOM_TRY(dalloc(ctx, &W.s, (size_t)n));
   SPFOM_TRY(dalloc(ctx, &W.marg, (size_t)n));
   SPFOM_TRY(dalloc(ctx, &W.marg_eval, (size_t)n));
@@ -419,7 +483,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
     spfom::FastPlan plan{};
     if (ctx->p.path == 0 && F >= 30 && spfom::fast_plan(n, kmax, ctx->sms, &plan)) {
       W.fast = true;
-      if (ctx->p.pipeline && spfom::pipe_plan(n, ctx->sms, &plan)) {
+      if (ctx->p.pipeline && !ctx->loading_batch && spfom::pipe_plan(n, ctx->sms, &plan)) {
         // tiles of consecutive segments for the binary64 pipeline
         const long long nt = spfom::make_tiles64(reinterpret_cast<const long long*>(I->seg_ptr), L, nullptr);
         std::vector<long long> tiles((size_t)nt + 1);
@@ -490,6 +554,50 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   cfg.kkt_tol = ctx->p.kkt_tol;
   cfg.f32 = ctx->p.precision == 32 ? 1 : 0;
   ctx->loaded = true;
+  W.batch = false;
+  if (ctx->loading_batch) {
+    const auto& B = *ctx->loading_batch;
+    if (!W.fast) {
+      free_instance(ctx);
+      return fail(ctx, SPFOM_ENOTSUP, "a batch needs the certified-decision kernel (sets of <= 32 products, path 0)");
+    }
+    ctx->batch = B;
+    std::vector<int> res_inst((size_t)m), prod_inst((size_t)n), seg_inst((size_t)L);
+    ctx->inst_tau.assign((size_t)B.count, 0.0);
+    ctx->inst_mean_r.assign((size_t)B.count, 0.0);
+    for (int b = 0; b < B.count; ++b) {
+      for (int i = B.res_ptr[b]; i < B.res_ptr[b + 1]; ++i) res_inst[i] = b;
+      for (int j = B.prod_ptr[b]; j < B.prod_ptr[b + 1]; ++j) prod_inst[j] = b;
+      for (long long l = B.seg_off[b]; l < B.seg_off[b + 1]; ++l) seg_inst[l] = b;
+      double sr = 0.0, sc = 0.0;
+      const int nb = B.prod_ptr[b + 1] - B.prod_ptr[b], mb = B.res_ptr[b + 1] - B.res_ptr[b];
+      for (int j = B.prod_ptr[b]; j < B.prod_ptr[b + 1]; ++j) sr += I->r[j];
+      for (int i = B.res_ptr[b]; i < B.res_ptr[b + 1]; ++i) sc += I->c[i];
+      const double mr = nb > 0 ? sr / nb : 0.0, mc = mb > 0 ? sc / mb : 0.0;
+      ctx->inst_mean_r[b] = mr;
+      ctx->inst_tau[b] = ctx->p.tau > 0.0 ? ctx->p.tau : ((mc > 0.0 && mr > 0.0) ? ctx->p.tau0 * mr / mc : ctx->p.tau0);
+    }
+    spfom::BatchMaps& M = W.bm;
+    M.count = B.count;
+    int *d_ri, *d_pi, *d_si, *d_rp, *d_pp, *d_conv;
+    long long* d_so;
+    spfom::InstState* d_inst;
+#define SPFOM_TRYB(x) do { spfom_status s_ = (x); if (s_ != SPFOM_OK) { free_instance(ctx); return s_; } } while (0)
+    SPFOM_TRYB(upload(ctx, &d_ri, res_inst.data(), res_inst.size()));
+    SPFOM_TRYB(upload(ctx, &d_pi, prod_inst.data(), prod_inst.size()));
+    SPFOM_TRYB(upload(ctx, &d_si, seg_inst.data(), seg_inst.size()));
+    SPFOM_TRYB(upload(ctx, &d_rp, B.res_ptr.data(), B.res_ptr.size()));
+    SPFOM_TRYB(upload(ctx, &d_pp, B.prod_ptr.data(), B.prod_ptr.size()));
+    SPFOM_TRYB(upload(ctx, &d_so, B.seg_off.data(), B.seg_off.size()));
+    SPFOM_TRYB(dalloc(ctx, &d_inst, (size_t)B.count));
+    SPFOM_TRYB(dalloc(ctx, &d_conv, (size_t)B.count));
+    SPFOM_TRYB(dalloc(ctx, &M.z_seg, (size_t)L));
+    SPFOM_TRYB(dalloc(ctx, &M.cy_res, (size_t)m));
+#undef SPFOM_TRYB
+    M.res_inst = d_ri; M.prod_inst = d_pi; M.seg_inst = d_si; M.res_ptr = d_rp; M.prod_ptr = d_pp;
+    M.seg_off = d_so; M.inst = d_inst; M.conv = d_conv;
+    W.batch = true;
+  }
   s = init_state(ctx, nullptr);
   if (s != SPFOM_OK) {
     free_instance(ctx);
@@ -591,6 +699,10 @@ spfom_status spfom_step(spfom_ctx* ctx, int64_t iters, spfom_stats* out) {
       seg += sm * 1e-3;
     }
   ctx->host_t = st.t;
+  if (ctx->W.batch) {
+    // the host counts batch iterations itself (instances stop counting when they converge)
+    ctx->host_t = t;
+  }
   fill_stats(ctx, st, ms * 1e-3, out);
   if (st.error) {
     if (out) {
@@ -624,12 +736,19 @@ spfom_status spfom_solve(spfom_ctx* ctx, const double* y0, spfom_stats* out) {
     segl += st.seg_kernel_launches;
     launches += st.kernel_launches;
     if (st.converged && ctx->cfg.f32 && ctx->p.polish) {
-      // binary64 polish: clear the flag and iterate in binary64 until the next evaluation
+      // binary64 polish: clear the flag(s) and iterate in binary64 until the next evaluation
       ctx->cfg.f32 = 0;
       ctx->polishing = true;
       const int zero = 0;
       SPFOM_CUDA(ctx, cudaMemcpyAsync(&ctx->W.st->converged, &zero, sizeof zero, cudaMemcpyHostToDevice,
                                       ctx->stream));
+      if (ctx->W.batch) {
+        for (auto& I : ctx->h_inst) I.converged = 0;
+        SPFOM_CUDA(ctx, cudaMemcpyAsync(ctx->W.bm.inst, ctx->h_inst.data(),
+                                        sizeof(spfom::InstState) * ctx->W.bm.count, cudaMemcpyHostToDevice,
+                                        ctx->stream));
+        SPFOM_CUDA(ctx, cudaMemsetAsync(ctx->W.bm.conv, 0, sizeof(int) * ctx->W.bm.count, ctx->stream));
+      }
       continue;
     }
     if (st.converged) break;
@@ -708,6 +827,181 @@ spfom_status spfom_evaluate(spfom_ctx* ctx, const double* y, double* z_out, doub
   spfom_status s = read_state(ctx, &st);
   if (s != SPFOM_OK) return s;
   if (dual_out) *dual_out = st.eval_out;
+  return SPFOM_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+spfom_status spfom_load_batch(spfom_ctx* ctx, const spfom_instance* insts, int32_t count) {
+  if (!ctx) return SPFOM_EINVAL;
+  if (!insts || count <= 0) return fail(ctx, SPFOM_EINVAL, "a batch needs at least one instance");
+  // validate each instance, then concatenate them into the block-diagonal union
+  long long n = 0, m = 0, L = 0, nnz = 0, nnzA = 0;
+  bool any_w = false, any_aval = false;
+  for (int b = 0; b < count; ++b) {
+    int kmax = 0;
+    spfom_status s = validate(ctx, &insts[b], &kmax);
+    if (s != SPFOM_OK) {
+      ctx->err = "instance " + std::to_string(b) + ": " + ctx->err;
+      return s;
+    }
+    n += insts[b].n;
+    m += insts[b].m;
+    L += insts[b].L;
+    nnz += insts[b].seg_ptr[insts[b].L];
+    nnzA += insts[b].n > 0 ? insts[b].a_ptr[insts[b].n] : 0;
+    any_w |= insts[b].w != nullptr;
+    any_aval |= insts[b].a_val != nullptr;
+  }
+  if (n > INT32_MAX || m > INT32_MAX || nnzA > INT32_MAX) return fail(ctx, SPFOM_EINVAL, "batch too large");
+  std::vector<double> r((size_t)n), c((size_t)m), aval(any_aval ? (size_t)nnzA : 0), v((size_t)nnz),
+      w(any_w ? (size_t)nnz : 0), lam((size_t)L), v0((size_t)L);
+  std::vector<int32_t> a_ptr((size_t)n + 1, 0), a_idx((size_t)nnzA), prod((size_t)nnz);
+  std::vector<int64_t> seg_ptr((size_t)L + 1, 0);
+  spfom_ctx::BatchSpec B;
+  B.count = count;
+  B.res_ptr.assign((size_t)count + 1, 0);
+  B.prod_ptr.assign((size_t)count + 1, 0);
+  B.seg_off.assign((size_t)count + 1, 0);
+  long long jo = 0, io = 0, lo = 0, po = 0, qo = 0;
+  for (int b = 0; b < count; ++b) {
+    const spfom_instance& I = insts[b];
+    const long long Kb = I.seg_ptr[I.L], Ab = I.n > 0 ? I.a_ptr[I.n] : 0;
+    for (int j = 0; j < I.n; ++j) {
+      r[jo + j] = I.r[j];
+      a_ptr[jo + j + 1] = (int32_t)(qo + I.a_ptr[j + 1]);
+    }
+    for (long long q = 0; q < Ab; ++q) {
+      a_idx[qo + q] = (int32_t)(io + I.a_idx[q]);
+      if (any_aval) aval[qo + q] = I.a_val ? I.a_val[q] : 1.0;
+    }
+    for (int i = 0; i < I.m; ++i) c[io + i] = I.c[i];
+    for (long long l = 0; l < I.L; ++l) {
+      seg_ptr[lo + l + 1] = po + I.seg_ptr[l + 1];
+      lam[lo + l] = I.lam[l];
+      v0[lo + l] = I.v0[l];
+    }
+    for (long long p = 0; p < Kb; ++p) {
+      prod[po + p] = (int32_t)(jo + I.seg_prod[p]);
+      v[po + p] = I.v[p];
+      if (any_w) w[po + p] = I.w ? I.w[p] : 0.0;
+    }
+    jo += I.n;
+    io += I.m;
+    lo += I.L;
+    po += Kb;
+    qo += Ab;
+    B.res_ptr[b + 1] = (int)io;
+    B.prod_ptr[b + 1] = (int)jo;
+    B.seg_off[b + 1] = lo;
+  }
+  spfom_instance U{};
+  U.n = (int32_t)n;
+  U.m = (int32_t)m;
+  U.L = L;
+  U.r = r.data();
+  U.c = c.data();
+  U.a_ptr = a_ptr.data();
+  U.a_idx = a_idx.data();
+  U.a_val = any_aval ? aval.data() : nullptr;
+  U.seg_ptr = seg_ptr.data();
+  U.seg_prod = prod.data();
+  U.v = v.data();
+  U.w = any_w ? w.data() : nullptr;
+  U.lam = lam.data();
+  U.v0 = v0.data();
+  ctx->loading_batch = &B;
+  spfom_status s = spfom_load_instance(ctx, &U);
+  ctx->loading_batch = nullptr;
+  return s;
+}
+
+spfom_status spfom_batch_stats(spfom_ctx* ctx, spfom_stats* out) {
+  if (!ctx || !out) return SPFOM_EINVAL;
+  if (!ctx->loaded || !ctx->W.batch) return fail(ctx, SPFOM_ESTATE, "no batch loaded");
+  SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
+  DevState st;
+  spfom_status s = read_state(ctx, &st);
+  if (s != SPFOM_OK) return s;
+  for (int b = 0; b < ctx->W.bm.count; ++b) inst_stats(ctx, ctx->h_inst[b], &out[b]);
+  return SPFOM_OK;
+}
+
+spfom_status spfom_update(spfom_ctx* ctx, const double* c, const double* lam) {
+  if (!ctx) return SPFOM_EINVAL;
+  if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
+  const Problem& P = ctx->P;
+  if (c)
+    for (int i = 0; i < P.m; ++i)
+      if (!(c[i] >= 0.0) || !is_finite(c[i])) return fail(ctx, SPFOM_EINVAL, "c[%d] must be finite and >= 0", i);
+  double mass = 0.0;
+  if (lam) {
+    for (long long l = 0; l < P.L; ++l) {
+      if (!(lam[l] >= 0.0) || !is_finite(lam[l])) return fail(ctx, SPFOM_EINVAL, "lam[%lld] must be >= 0", l);
+      mass += lam[l];
+    }
+    int e2 = 0;
+    std::frexp(mass > 1.0 ? mass : 1.0, &e2);
+    const int F = 61 - e2;
+    if (ctx->W.fast && F < 30) return fail(ctx, SPFOM_ENOTSUP, "arrival mass too large for the fixed-point sales");
+    if (ctx->W.fast) {
+      ctx->W.fx_bits = F;
+      ctx->W.fx_scale = std::ldexp(1.0, F);
+      ctx->W.inv_fx_scale = std::ldexp(1.0, -F);
+    }
+  }
+  SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
+  drop_graphs(ctx);  // captured launches carry the fixed-point scale
+  if (c) SPFOM_CUDA(ctx, cudaMemcpyAsync(const_cast<double*>(P.c), c, sizeof(double) * P.m, cudaMemcpyHostToDevice,
+                                         ctx->stream));
+  if (lam) {
+    SPFOM_CUDA(ctx, cudaMemcpyAsync(const_cast<double*>(P.lam), lam, sizeof(double) * P.L, cudaMemcpyHostToDevice,
+                                    ctx->stream));
+    if (ctx->W.v32) {
+      cudaError_t e = spfom::launch_prep_f32(P, ctx->W, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "binary32 copies");
+    }
+  }
+  // step sizes follow the new capacities: tau0 * mean(r) / mean(c), per instance in a batch
+  if (c && !(ctx->p.tau > 0.0)) {
+    auto tau_of = [&](double mr, double mc) { return (mc > 0.0 && mr > 0.0) ? ctx->p.tau0 * mr / mc : ctx->p.tau0; };
+    if (ctx->W.batch) {
+      for (int b = 0; b < ctx->batch.count; ++b) {
+        double sc = 0.0;
+        const int i0 = ctx->batch.res_ptr[b], i1 = ctx->batch.res_ptr[b + 1];
+        for (int i = i0; i < i1; ++i) sc += c[i];
+        ctx->inst_tau[b] = tau_of(ctx->inst_mean_r[b], i1 > i0 ? sc / (i1 - i0) : 0.0);
+      }
+    } else {
+      std::vector<double> r((size_t)P.n);
+      SPFOM_CUDA(ctx, cudaMemcpyAsync(r.data(), P.r, sizeof(double) * P.n, cudaMemcpyDeviceToHost, ctx->stream));
+      SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+      double sr = 0.0, sc = 0.0;
+      for (int j = 0; j < P.n; ++j) sr += r[j];
+      for (int i = 0; i < P.m; ++i) sc += c[i];
+      ctx->tau_init = tau_of(P.n > 0 ? sr / P.n : 0.0, P.m > 0 ? sc / P.m : 0.0);
+    }
+  }
+  SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SPFOM_OK;
+}
+
+spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out) {
+  if (!ctx || !y || !s_out) return SPFOM_EINVAL;
+  if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
+  const Problem& P = ctx->P;
+  for (int i = 0; i < P.m; ++i)
+    if (!(y[i] >= 0.0) || !is_finite(y[i])) return fail(ctx, SPFOM_EINVAL, "y[%d] must be finite and >= 0", i);
+  SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
+  if (P.m) SPFOM_CUDA(ctx, cudaMemcpyAsync(ctx->W.y_eval, y, sizeof(double) * P.m, cudaMemcpyHostToDevice, ctx->stream));
+  Work w = ctx->W;
+  w.s = ctx->W.s_eval;  // scatter into the evaluation buffer: the iteration state stays as it is
+  cudaError_t e = spfom::launch_sales_at(P, w, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "sales launch");
+  if (P.n) SPFOM_CUDA(ctx, cudaMemcpyAsync(s_out, w.s, sizeof(double) * P.n, cudaMemcpyDeviceToHost, ctx->stream));
+  SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   return SPFOM_OK;
 }
 

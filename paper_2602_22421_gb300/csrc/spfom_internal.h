@@ -22,6 +22,33 @@ struct DevState {
   double eval_out;      // Dual(y) of spfom_evaluate
 };
 
+// Per-instance scalars of a batch (spfom_load_batch): the batch is the
+// block-diagonal union of its instances, and every instance keeps its own step
+// size, regulariser, epoch sums, KKT residual, restart and convergence state.
+struct InstState {
+  double tau, mu;
+  double sum_P;
+  double z_sum, P, dual_iter;
+  double kkt, pinf, gap, dual_avg, primal_avg, kkt_anchor;
+  long long t, count, restarts, evals;
+  int converged, pad;
+};
+
+// Batch maps in device memory.
+struct BatchMaps {
+  int count;                  // instances
+  const int* res_inst;        // [m] instance of each resource
+  const int* prod_inst;       // [n] instance of each product
+  const int* seg_inst;        // [L] instance of each segment
+  const int* res_ptr;         // [count+1] resource offsets
+  const int* prod_ptr;        // [count+1] product offsets
+  const long long* seg_off;   // [count+1] segment offsets
+  InstState* inst;            // [count]
+  int* conv;                  // [count] converged flags (read by the segment kernels)
+  double* z_seg;              // [L] segment values of the last pass
+  double* cy_res;             // [m] c_i y_i of the dual point of the last iteration
+};
+
 // Instance in device memory (all pointers device pointers).
 struct Problem {
   int n, m, nnzA;
@@ -77,7 +104,8 @@ struct Work {
   double* s;
   double* marg;
   double* marg_eval;
-  double* y_eval;      // dual point handed to spfom_evaluate
+  double* y_eval;      // dual point handed to spfom_evaluate / spfom_sales_at
+  double* s_eval;      // [n] product sales of spfom_sales_at
   double* z_seg;       // [L] per-segment values of spfom_evaluate
   double* zpart;       // per-block partial sums of z (iterate)
   double* zpart_eval;  // per-block partial sums of z (evaluation)
@@ -107,6 +135,8 @@ struct Work {
   long long ntiles;
   long long* tile64_ptr;  // [ntiles64+1] (binary64 pipeline tiles)
   long long ntiles64;
+  bool batch;             // instances of a batch (spfom_load_batch)
+  BatchMaps bm;
 };
 
 struct FastArgs {
@@ -124,6 +154,10 @@ struct FastArgs {
   long long ntiles;
   int acc_bytes;
   DevState* st_rw;
+  // batch mode: skip converged instances, write per-segment values
+  const int* seg_inst;
+  const int* inst_conv;
+  double* z_seg;
 };
 
 struct F32Args {
@@ -146,6 +180,10 @@ struct F32Args {
   long long ntiles;
   int acc_bytes;
   DevState* st_rw;            // for the timeout flag
+  // batch mode: skip converged instances, write per-segment values
+  const int* seg_inst;
+  const int* inst_conv;
+  double* z_seg;
 };
 
 struct RunConfig {
@@ -164,6 +202,7 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
                              cudaEvent_t seg_begin = nullptr, cudaEvent_t seg_end = nullptr);
 cudaError_t launch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s);
 cudaError_t launch_evaluate_at(const Problem& P, const Work& Wk, bool want_seg, cudaStream_t s);
+cudaError_t launch_sales_at(const Problem& P, const Work& Wk, cudaStream_t s);
 int kernel_launches_per_iteration(const Work& Wk, const RunConfig& cfg);
 int kernel_launches_per_eval();
 
@@ -172,6 +211,14 @@ bool fast_plan(int n, int kmax, int sms, FastPlan* plan);
 cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s);
 cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s);
 bool tma_plan(int n, int kmax, int sms, FastPlan* plan);
+// spfom_batch.cu
+cudaError_t launch_batch_iteration(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s);
+cudaError_t launch_batch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s);
+int batch_launches_per_iteration(const Work& Wk);
+int batch_launches_per_eval();
+// the segment pass of one iteration (shared with the single-instance path)
+cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfig& cfg, const double* marg,
+                                bool iterate, cudaStream_t s, int* zparts_out);
 // spfom_segments_tma.cu
 bool pipe_plan(int n, int sms, FastPlan* plan);
 cudaError_t launch_seg_fast_pipe(const FastArgs& A, const FastPlan& plan, cudaStream_t s);

@@ -394,8 +394,37 @@ cudaError_t launch_prep(const Problem& P, const double* w, const double* v0, dou
   return cudaGetLastError();
 }
 
+cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfig& cfg, const double* marg,
+                                bool iterate, cudaStream_t s, int* zparts_out) {
+  const int* seg_inst = Wk.batch ? Wk.bm.seg_inst : nullptr;
+  const int* conv = Wk.batch ? Wk.bm.conv : nullptr;
+  double* z_seg = Wk.batch ? Wk.bm.z_seg : nullptr;
+  if (!iterate) {
+    FastArgs A{P, marg, nullptr, Wk.zpart_eval, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, nullptr,
+               nullptr, 0, 0, Wk.st, seg_inst, conv, z_seg};
+    *zparts_out = Wk.plan.grid_eval;
+    return launch_seg_fast(A, Wk.plan, false, s);
+  }
+  if (cfg.f32 && Wk.v32) {
+    F32Args A{P.seg_ptr, P.seg_prod, Wk.v32, Wk.vt32, Wk.lam32, Wk.vt0_32, P.L, P.n, Wk.fx_bits, Wk.marg32,
+              Wk.part, Wk.s_fx, Wk.zpart, Wk.st, Wk.tile_ptr, Wk.ntiles, Wk.plan.acc_bytes, Wk.st,
+              seg_inst, conv, z_seg};
+    *zparts_out = Wk.plan.grid32;
+    return launch_seg_f32(A, Wk.plan, s);
+  }
+  FastArgs A{P, marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, Wk.s_fx,
+             Wk.tile64_ptr, Wk.ntiles64, Wk.plan.pipe_acc_bytes, Wk.st, seg_inst, conv, z_seg};
+  if (Wk.plan.pipe && !Wk.batch) {
+    *zparts_out = Wk.plan.pipe_grid;
+    return launch_seg_fast_pipe(A, Wk.plan, s);
+  }
+  *zparts_out = Wk.plan.grid;
+  return launch_seg_fast(A, Wk.plan, true, s);
+}
+
 cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s,
                              cudaEvent_t seg_begin, cudaEvent_t seg_end) {
+  if (Wk.batch) return launch_batch_iteration(P, Wk, cfg, s);
   const bool sampled = cfg.batch_frac < 1.0;
   const bool fast = Wk.fast && !sampled;
   const bool f32 = fast && cfg.f32 && Wk.v32;
@@ -406,21 +435,8 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
   if (seg_begin) cudaEventRecord(seg_begin, s);
   cudaError_t e;
   int zparts = Wk.seg_blocks;
-  if (f32) {
-    F32Args A{P.seg_ptr, P.seg_prod, Wk.v32, Wk.vt32, Wk.lam32, Wk.vt0_32, P.L, P.n, Wk.fx_bits, Wk.marg32,
-              Wk.part, Wk.s_fx, Wk.zpart, Wk.st, Wk.tile_ptr, Wk.ntiles, Wk.plan.acc_bytes, Wk.st};
-    e = launch_seg_f32(A, Wk.plan, s);
-    zparts = Wk.plan.grid32;
-  } else if (fast) {
-    FastArgs A{P, Wk.marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, Wk.s_fx,
-               Wk.tile64_ptr, Wk.ntiles64, Wk.plan.pipe_acc_bytes, Wk.st};
-    if (Wk.plan.pipe) {
-      e = launch_seg_fast_pipe(A, Wk.plan, s);
-      zparts = Wk.plan.pipe_grid;
-    } else {
-      e = launch_seg_fast(A, Wk.plan, true, s);
-      zparts = Wk.plan.grid;
-    }
+  if (fast) {
+    e = launch_segment_pass(P, Wk, cfg, Wk.marg, true, s, &zparts);
   } else {
     e = sampled ? launch_segments_w<kIterate, true>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s)
                 : launch_segments_w<kIterate, false>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s);
@@ -436,19 +452,28 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
 }
 
 cudaError_t launch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s) {
+  if (Wk.batch) return launch_batch_eval(P, Wk, cfg, s);
   const int gn = (P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1;
   k_margins<<<gn, kVecThreads, 0, s>>>(P, nullptr, Wk.sum_y, 1, Wk.marg_eval, nullptr, nullptr, Wk.st);
   cudaError_t e;
   if (Wk.fast) {
-    FastArgs A{P, Wk.marg_eval, nullptr, Wk.zpart_eval, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, nullptr,
-               nullptr, 0, 0, Wk.st};
-    e = launch_seg_fast(A, Wk.plan, false, s);
+    int zparts = 0;
+    e = launch_segment_pass(P, Wk, cfg, Wk.marg_eval, false, s, &zparts);
   } else {
     e = launch_segments_w<kEvalSum, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, Wk.st, cfg, s);
   }
   if (e != cudaSuccess) return e;
   k_eval_finish<<<1, 1024, 0, s>>>(P, Wk, cfg);
   return cudaGetLastError();
+}
+
+// Product sales of every segment's best response at the duals in Wk.y_eval
+// (the expected sales of bid-price control at those prices), into Wk.s.
+cudaError_t launch_sales_at(const Problem& P, const Work& Wk, cudaStream_t s) {
+  RunConfig cfg{};
+  const int gn = (P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1;
+  k_margins<<<gn, kVecThreads, 0, s>>>(P, Wk.y_eval, nullptr, 0, Wk.marg_eval, Wk.s, nullptr, nullptr);
+  return launch_segments_w<kIterate, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, nullptr, cfg, s);
 }
 
 cudaError_t launch_evaluate_at(const Problem& P, const Work& Wk, bool want_seg, cudaStream_t s) {
@@ -463,6 +488,7 @@ cudaError_t launch_evaluate_at(const Problem& P, const Work& Wk, bool want_seg, 
 }
 
 int kernel_launches_per_iteration(const Work& Wk, const RunConfig& cfg) {
+  if (Wk.batch) return batch_launches_per_iteration(Wk);
   if (!(Wk.fast && cfg.batch_frac >= 1.0)) return 3;
   return Wk.plan.scatter == 1 ? 4 : 3;
 }
@@ -491,6 +517,6 @@ cudaError_t launch_prep_f32(const Problem& P, Work& Wk, cudaStream_t s) {
   if (P.L > 0) k_prep_f32_segments<<<(unsigned)((P.L + 255) / 256), 256, 0, s>>>(P.L, P.lam, P.vt0, Wk.lam32, Wk.vt0_32);
   return cudaGetLastError();
 }
-int kernel_launches_per_eval() { return 3; }
+int kernel_launches_per_eval() { return 3; }  // single instance and batch alike
 
 }  // namespace spfom

@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
   double zacc = 0.0;
   int fallbacks = 0;
   for (long long l = blockIdx.x * gpb + threadIdx.x / W; l < Pr.L; l += ngroups) {
+    if (A.seg_inst && A.inst_conv[A.seg_inst[l]]) continue;  // batch: instance already converged
     const long long b = Pr.seg_ptr[l];
     const int K = (int)(Pr.seg_ptr[l + 1] - b);
     // Registers hold the binary32 images a = m v, b = vt and the product ids;
@@ -169,7 +170,10 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
       Dl += __shfl_xor_sync(gmask, Dl, o, W);
     }
     const double q = quotient(lam, vt0 + Dl);
-    if (lane == 0) zacc += q * Nl;
+    if (lane == 0) {
+      if (A.z_seg) A.z_seg[l] = q * Nl;
+      else zacc += q * Nl;
+    }
     if (SC != 0) {
 #pragma unroll
       for (int p = 0; p < P; ++p)
@@ -207,6 +211,7 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
   const long long ngroups = (long long)gridDim.x * gpb;
   float zacc = 0.f;
   for (long long l = blockIdx.x * gpb + threadIdx.x / W; l < A.L; l += ngroups) {
+    if (A.seg_inst && A.inst_conv[A.seg_inst[l]]) continue;  // batch: instance already converged
     const long long b = A.seg_ptr[l];
     const int K = (int)(A.seg_ptr[l + 1] - b);
     int jv[P];
@@ -257,7 +262,10 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
       Dsel = D;
     }
     const float q = lam / (vt0 + Dsel);
-    if (lane == 0) zacc += q * Nsel;
+    if (lane == 0) {
+      if (A.z_seg) A.z_seg[l] = (double)(q * Nsel);
+      else zacc += q * Nsel;
+    }
     if (SC != 0) {
 #pragma unroll
       for (int p = 0; p < P; ++p)
@@ -372,6 +380,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_seg_f32_tma(F32Args A) {
     const float* vt_s = reinterpret_cast<const float*>(S + StageLayout::vt);
     const int nseg = (int)(l1 - l0);
     for (int ls = group; ls < nseg; ls += gpb) {
+      if (A.seg_inst && A.inst_conv[A.seg_inst[l0 + ls]]) continue;  // batch: instance converged
       const int b = (int)(segp[ls] - ibase);
       const int K = (int)(segp[ls + 1] - segp[ls]);
       // per slot: a = m v (binary32) for candidates, b = v - w; ids and v are re-read
@@ -416,7 +425,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_seg_f32_tma(F32Args A) {
         Dsel = D;
       }
       const float q = __fdividef(lam, vt0 + Dsel);
-      if (lane == 0) zacc += q * Nsel;
+      if (lane == 0) {
+        if (A.z_seg) A.z_seg[l0 + ls] = (double)(q * Nsel);
+        else zacc += q * Nsel;
+      }
       if (SC != 0) {
 #pragma unroll
         for (int p = 0; p < P; ++p)

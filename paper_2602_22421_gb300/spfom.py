@@ -22,7 +22,8 @@ VEC_Y, VEC_YBAR, VEC_SUM_Y, VEC_SUM_G, VEC_G, VEC_S, VEC_MARGINS = range(7)
 # Every function include/spfom.h declares.
 EXPORTS = ("spfom_default_params", "spfom_create", "spfom_load_instance", "spfom_reset", "spfom_step",
            "spfom_solve", "spfom_vector", "spfom_duals", "spfom_evaluate", "spfom_get_stats", "spfom_destroy",
-           "spfom_last_error", "spfom_status_string", "spfom_sales_noalloc")
+           "spfom_last_error", "spfom_status_string", "spfom_sales_noalloc", "spfom_load_batch",
+           "spfom_batch_stats", "spfom_update", "spfom_sales_at")
 
 _f64p = C.POINTER(C.c_double)
 _i32p = C.POINTER(C.c_int32)
@@ -105,6 +106,12 @@ def lib():
         h.spfom_status_string.restype = C.c_char_p
         h.spfom_sales_noalloc.argtypes = [P(DeviceSegments), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         h.spfom_sales_noalloc.restype = C.c_int
+        h.spfom_load_batch.argtypes = [C.c_void_p, P(InstanceC), C.c_int32]
+        h.spfom_batch_stats.argtypes = [C.c_void_p, P(Stats)]
+        h.spfom_update.argtypes = [C.c_void_p, _f64p, _f64p]
+        h.spfom_sales_at.argtypes = [C.c_void_p, _f64p, _f64p]
+        for f in ("spfom_load_batch", "spfom_batch_stats", "spfom_update", "spfom_sales_at"):
+            getattr(h, f).restype = C.c_int
         for f in ("spfom_create", "spfom_load_instance", "spfom_reset", "spfom_step", "spfom_solve", "spfom_vector",
                   "spfom_duals", "spfom_evaluate", "spfom_get_stats"):
             getattr(h, f).restype = C.c_int
@@ -194,6 +201,34 @@ class Solver:
         self._check(self._lib.spfom_load_instance(self._h, C.byref(arrs.c)))
         self.n, self.m, self.L = arrs.c.n, arrs.c.m, arrs.c.L
         return self
+
+    def load_batch(self, insts):
+        """Load many instances as one batch (spfom_load_batch)."""
+        arrs = [i if isinstance(i, InstanceArrays) else InstanceArrays(i) for i in insts]
+        cs = (InstanceC * len(arrs))(*[a.c for a in arrs])
+        self._keep_batch = arrs
+        self._check(self._lib.spfom_load_batch(self._h, cs, len(arrs)))
+        self.n = sum(a.c.n for a in arrs)
+        self.m = sum(a.c.m for a in arrs)
+        self.L = sum(a.c.L for a in arrs)
+        self.batch_sizes = [(a.c.n, a.c.m, a.c.L) for a in arrs]
+        return self
+
+    def batch_stats(self) -> list:
+        out = (Stats * len(self.batch_sizes))()
+        self._check(self._lib.spfom_batch_stats(self._h, out))
+        return [o.as_dict() for o in out]
+
+    def update(self, c=None, lam=None):
+        c = None if c is None else np.ascontiguousarray(c, np.float64)
+        lam = None if lam is None else np.ascontiguousarray(lam, np.float64)
+        self._check(self._lib.spfom_update(self._h, _p(c, _f64p), _p(lam, _f64p)))
+
+    def sales_at(self, y) -> np.ndarray:
+        y = np.ascontiguousarray(y, np.float64)
+        out = np.empty(max(self.n, 1))
+        self._check(self._lib.spfom_sales_at(self._h, _p(y, _f64p), _p(out, _f64p)))
+        return out[: self.n]
 
     def reset(self, y0=None):
         y = None if y0 is None else np.ascontiguousarray(y0, np.float64)

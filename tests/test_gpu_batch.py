@@ -1,0 +1,134 @@
+"""Batched re-solves (spfom_load_batch) against per-instance oracle runs, and
+the multi-period update (needs a GPU).
+
+A batch is the block-diagonal union of its instances with per-instance step
+size, averages, KKT, restarts and convergence, so every instance of a batch
+must follow exactly the iterates of its own single-instance run.
+"""
+import numpy as np
+import pytest
+
+from instances import make_instance, mid_gam, seeded_duals, tiny_mnl
+from oracle import Oracle
+from oracle import Params as OracleParams
+
+pytestmark = pytest.mark.gpu
+ITER_RTOL = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def Solver(**kw):
+    from paper_2602_22421_gb300 import Solver as S
+    return S(None, device=0, **kw)
+
+
+def nrel(a, b):
+    scale = float(np.abs(b).max()) if np.size(b) else 0.0
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max()) / (scale if scale > 0 else 1.0) if np.size(b) else 0.0
+
+
+def members():
+    return [tiny_mnl(0), make_instance(n=30, m=8, L=600, kmin=3, kmax=8, gam=True, tightness=0.6, seed=5),
+            mid_gam(1, L=5000, n=300, m=60), mid_gam(7, L=2500, n=150, m=40, kmin=3, kmax=12)]
+
+
+def slices(insts):
+    out, i0 = [], 0
+    for inst in insts:
+        out.append(slice(i0, i0 + inst.m))
+        i0 += inst.m
+    return out
+
+
+def test_batch_members_track_their_own_oracle_runs():
+    insts = members()
+    runs = [Oracle(i).run(OracleParams()) for i in insts]
+    with Solver() as s:
+        s.load_batch(insts)
+        done = 0
+        for t in (1, 5, 64, 65, 128, 200):
+            s.step(t - done)
+            done = t
+            y = s.duals()
+            per = s.batch_stats()
+            for k, (inst, run, sl) in enumerate(zip(insts, runs, slices(insts))):
+                run.step(t - run.stats()["t"])
+                ost = run.stats()
+                assert per[k]["iters"] == ost["t"] == t
+                assert per[k]["restarts"] == ost["restarts"] and per[k]["evals"] == ost["evals"]
+                assert nrel(y[sl], run.y) <= ITER_RTOL, (k, t)
+                assert per[k]["dual_iter"] == pytest.approx(ost["dual_iter"], rel=ITER_RTOL)
+                if ost["evals"]:
+                    assert per[k]["kkt"] == pytest.approx(ost["kkt"], rel=1e-5)
+                    assert per[k]["dual_avg"] == pytest.approx(ost["dual_avg"], rel=ITER_RTOL)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batch_solve_converges_every_member(precision):
+    insts = members()[1:]  # the 40-segment instance needs a decaying step (see the oracle pins)
+    refs = []
+    for inst in insts:
+        run = Oracle(inst).run(OracleParams())
+        for _ in range(300):
+            ost = run.step(64)
+            if ost["converged"]:
+                break
+        assert ost["converged"]
+        refs.append(ost)
+    with Solver(precision=precision) as s:
+        s.load_batch(insts)
+        st = s.solve()
+        per = s.batch_stats()
+    assert st["converged"] == 1 and st["kkt"] <= 1e-4
+    for k, ref in enumerate(refs):
+        assert per[k]["converged"] == 1 and per[k]["kkt"] <= 1e-4
+        assert per[k]["dual_avg"] == pytest.approx(ref["dual_avg"], rel=1e-6 if precision == 64 else 1e-4)
+        if precision == 64:
+            assert per[k]["iters"] == ref["t"]
+
+
+def test_sales_at_matches_oracle_sweep():
+    inst = mid_gam(1, L=20_000, n=1000, m=200)
+    y = seeded_duals(inst.m, 3, float(np.mean(inst.r)) / 4)
+    from paper_2602_22421_gb300 import Solver as S
+    with S(inst, device=0) as s:
+        got = s.sales_at(y)
+        assert s.stats()["iters"] == 0
+    np.testing.assert_allclose(got, Oracle(inst).sweep(y)["s"], rtol=1e-12, atol=1e-12 * got.max())
+
+
+def test_multi_period_update_with_warm_start():
+    """Period 2 of a two-instance batch: capacities lowered by period 1's
+    expected sales under its bid prices, arrival rates rescaled, duals kept."""
+    insts = members()[2:]
+    with Solver() as s:
+        s.load_batch(insts)
+        s.step(256)
+        y1 = s.duals()
+        sales = s.sales_at(y1)
+        c_new, lam_new = [], []
+        rng = np.random.default_rng(11)
+        for inst, j0 in zip(insts, np.cumsum([0] + [i.n for i in insts])[:-1]):
+            A = np.zeros((inst.m, inst.n))
+            for j in range(inst.n):
+                A[inst.a_idx[inst.a_ptr[j]:inst.a_ptr[j + 1]], j] = 1.0
+            used = A @ sales[j0:j0 + inst.n]
+            c_new.append(np.maximum(0.0, 2.0 * inst.c - used))
+            lam_new.append(inst.lam * rng.uniform(0.5, 1.5))
+        s.update(np.concatenate(c_new), np.concatenate(lam_new))
+        s.reset(y1)
+        s.step(130)
+        y2 = s.duals()
+        per = s.batch_stats()
+    for k, (inst, sl) in enumerate(zip(insts, slices(insts))):
+        upd = inst.with_capacity(c_new[k])
+        upd.lam = lam_new[k]
+        run = Oracle(upd).run(OracleParams(), y0=y1[sl])
+        ost = run.step(130)
+        assert nrel(y2[sl], run.y) <= ITER_RTOL
+        assert per[k]["restarts"] == ost["restarts"] and per[k]["tau"] == ost["tau_used"]
