@@ -234,6 +234,15 @@ spfom_status spfom_update(spfom_ctx* ctx, const double* c, const double* lam);
  * with bid prices y. Leaves the iteration state alone. */
 spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out);
 
+/* Segment-to-warp tiling autotuner (no counterpart in the paper). Times each
+ * candidate segment kernel of the loaded instance or batch -- for the
+ * precision-32 pass: 1 = plain loads with 4 lanes x 4 products per segment,
+ * 2 = tiles staged by bulk copies with 8 products per lane -- for `iters`
+ * iterations each from the current duals, keeps the fastest, and restarts the
+ * iteration from those duals. *choice_out (or NULL) gets the choice; with a
+ * single candidate it just reports it. */
+spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* choice_out);
+
 /* Free the ctx and all its device memory (NULL is a no-op). */
 void spfom_destroy(spfom_ctx* ctx);
 

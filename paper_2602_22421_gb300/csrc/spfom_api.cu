@@ -503,10 +503,11 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       W.fx_scale = std::ldexp(1.0, F);
       W.fx_bits = F;
       W.inv_fx_scale = std::ldexp(1.0, -F);
-      W.zparts_iter = std::max(std::max(plan.grid, plan.grid32), plan.pipe ? plan.pipe_grid : 0);
+      W.zparts_iter = std::max(std::max(plan.grid, plan.grid32), std::max(plan.pipe ? plan.pipe_grid : 0,
+                                                                          plan.tma_ok ? plan.tma_grid : 0));
       W.zparts_eval = plan.grid_eval;
       if (plan.scatter == 1)
-        SPFOM_TRY(dalloc(ctx, &W.part, (size_t)std::max(plan.grid, plan.grid32) * (size_t)(n > 0 ? n : 1)));
+        SPFOM_TRY(dalloc(ctx, &W.part, (size_t)W.zparts_iter * (size_t)(n > 0 ? n : 1)));
       SPFOM_TRY(dalloc(ctx, &W.s_fx, (size_t)n));
     }
     if (ctx->p.precision == 32) {
@@ -1006,3 +1007,48 @@ spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out) {
 }
 
 }  // extern "C"
+
+extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* choice_out) {
+  if (!ctx) return SPFOM_EINVAL;
+  if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
+  if (iters <= 0) return fail(ctx, SPFOM_EINVAL, "iters must be > 0");
+  spfom::FastPlan& plan = ctx->W.plan;
+  const bool tunable = ctx->W.fast && ctx->W.v32 && ctx->cfg.f32 && plan.tma_ok;
+  if (!tunable) {
+    if (choice_out) *choice_out = plan.tma ? 2 : 1;
+    return SPFOM_OK;
+  }
+  SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
+  std::vector<double> y0((size_t)ctx->P.m);
+  if (ctx->P.m)
+    SPFOM_CUDA(ctx, cudaMemcpyAsync(y0.data(), ctx->W.y, sizeof(double) * ctx->P.m, cudaMemcpyDeviceToHost,
+                                    ctx->stream));
+  SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const double saved_tol = ctx->cfg.kkt_tol;
+  ctx->cfg.kkt_tol = -1.0;  // no instance may converge (and stop working) while being timed
+  double best = INFINITY;
+  int choice = 1;
+  for (int cand = 1; cand <= 2; ++cand) {
+    plan.tma = cand == 2 ? 1 : 0;
+    drop_graphs(ctx);
+    spfom_status s = init_state(ctx, y0.data());
+    spfom_stats st{};
+    if (s == SPFOM_OK) s = spfom_step(ctx, iters, &st);   // warm-up
+    if (s == SPFOM_OK) s = spfom_step(ctx, iters, &st);
+    if (s != SPFOM_OK) {
+      ctx->cfg.kkt_tol = saved_tol;
+      return s;
+    }
+    if (st.seconds < best) {
+      best = st.seconds;
+      choice = cand;
+    }
+  }
+  ctx->cfg.kkt_tol = saved_tol;
+  plan.tma = choice == 2 ? 1 : 0;
+  drop_graphs(ctx);
+  spfom_status s = init_state(ctx, y0.data());
+  if (s != SPFOM_OK) return s;
+  if (choice_out) *choice_out = choice;
+  return SPFOM_OK;
+}

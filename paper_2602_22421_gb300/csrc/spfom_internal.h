@@ -89,6 +89,8 @@ struct FastPlan {
   int reduce_chunks;  // grid.y of k_reduce_products
   int tma;            // 1: the binary32 pass runs k_seg_f32_tma (tile staging by bulk copies)
   int tma_W;          // its lanes per segment (8 products per lane)
+  int tma_grid;       // its blocks
+  int tma_ok;         // 1 when the staged kernel is available (spfom_autotune may switch tma)
   int tma_smem;       // its dynamic shared memory: product sums + two stages
   int acc_bytes;      // bytes of the product sums at the start of that memory
   int pipe;           // 1: the binary64 pass runs k_seg_fast_pipe (warp-specialised TMA pipeline)

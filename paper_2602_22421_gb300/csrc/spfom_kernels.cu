@@ -409,7 +409,7 @@ cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfi
     F32Args A{P.seg_ptr, P.seg_prod, Wk.v32, Wk.vt32, Wk.lam32, Wk.vt0_32, P.L, P.n, Wk.fx_bits, Wk.marg32,
               Wk.part, Wk.s_fx, Wk.zpart, Wk.st, Wk.tile_ptr, Wk.ntiles, Wk.plan.acc_bytes, Wk.st,
               seg_inst, conv, z_seg};
-    *zparts_out = Wk.plan.grid32;
+    *zparts_out = Wk.plan.tma ? Wk.plan.tma_grid : Wk.plan.grid32;
     return launch_seg_f32(A, Wk.plan, s);
   }
   FastArgs A{P, marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, Wk.s_fx,

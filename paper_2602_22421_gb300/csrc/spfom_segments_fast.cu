@@ -574,8 +574,8 @@ cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatte
 
 cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s) {
   if (plan.tma)
-    return plan.scatter == 1 ? launch_tma_w<1>(A, plan.tma_W, plan.grid32, plan.tma_smem, s)
-                             : launch_tma_w<2>(A, plan.tma_W, plan.grid32, plan.tma_smem, s);
+    return plan.scatter == 1 ? launch_tma_w<1>(A, plan.tma_W, plan.tma_grid, plan.tma_smem, s)
+                             : launch_tma_w<2>(A, plan.tma_W, plan.tma_grid, plan.tma_smem, s);
   return plan.scatter == 1 ? launch_f32_w<1>(A, plan.W, plan.grid32, plan.smem, s)
                            : launch_f32_w<2>(A, plan.W, plan.grid32, 0, s);
 }
@@ -604,10 +604,11 @@ bool tma_plan(int n, int kmax, int sms, FastPlan* plan) {
 #undef SPFOM_TMA_OCC
   if (nb < 1) return false;
   plan->tma = 1;
+  plan->tma_ok = 1;
   plan->tma_W = W8;
   plan->tma_smem = smem;
   plan->acc_bytes = acc;
-  plan->grid32 = nb * sms;
+  plan->tma_grid = nb * sms;
   return true;
 }
 

@@ -23,7 +23,7 @@ VEC_Y, VEC_YBAR, VEC_SUM_Y, VEC_SUM_G, VEC_G, VEC_S, VEC_MARGINS = range(7)
 EXPORTS = ("spfom_default_params", "spfom_create", "spfom_load_instance", "spfom_reset", "spfom_step",
            "spfom_solve", "spfom_vector", "spfom_duals", "spfom_evaluate", "spfom_get_stats", "spfom_destroy",
            "spfom_last_error", "spfom_status_string", "spfom_sales_noalloc", "spfom_load_batch",
-           "spfom_batch_stats", "spfom_update", "spfom_sales_at")
+           "spfom_batch_stats", "spfom_update", "spfom_sales_at", "spfom_autotune")
 
 _f64p = C.POINTER(C.c_double)
 _i32p = C.POINTER(C.c_int32)
@@ -110,7 +110,8 @@ def lib():
         h.spfom_batch_stats.argtypes = [C.c_void_p, P(Stats)]
         h.spfom_update.argtypes = [C.c_void_p, _f64p, _f64p]
         h.spfom_sales_at.argtypes = [C.c_void_p, _f64p, _f64p]
-        for f in ("spfom_load_batch", "spfom_batch_stats", "spfom_update", "spfom_sales_at"):
+        h.spfom_autotune.argtypes = [C.c_void_p, C.c_int32, P(C.c_int32)]
+        for f in ("spfom_load_batch", "spfom_batch_stats", "spfom_update", "spfom_sales_at", "spfom_autotune"):
             getattr(h, f).restype = C.c_int
         for f in ("spfom_create", "spfom_load_instance", "spfom_reset", "spfom_step", "spfom_solve", "spfom_vector",
                   "spfom_duals", "spfom_evaluate", "spfom_get_stats"):
@@ -229,6 +230,12 @@ class Solver:
         out = np.empty(max(self.n, 1))
         self._check(self._lib.spfom_sales_at(self._h, _p(y, _f64p), _p(out, _f64p)))
         return out[: self.n]
+
+    def autotune(self, iters: int = 64) -> int:
+        """Pick the fastest segment kernel for this instance (spfom_autotune)."""
+        ch = C.c_int32(0)
+        self._check(self._lib.spfom_autotune(self._h, int(iters), C.byref(ch)))
+        return ch.value
 
     def reset(self, y0=None):
         y = None if y0 is None else np.ascontiguousarray(y0, np.float64)

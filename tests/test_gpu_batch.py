@@ -132,3 +132,32 @@ def test_multi_period_update_with_warm_start():
         ost = run.step(130)
         assert nrel(y2[sl], run.y) <= ITER_RTOL
         assert per[k]["restarts"] == ost["restarts"] and per[k]["tau"] == ost["tau_used"]
+
+
+@pytest.mark.parametrize("batch", [False, True])
+def test_autotune_keeps_the_duals_and_the_solution(batch):
+    """spfom_autotune times the binary32 segment kernels, keeps the faster one
+    and restarts from the duals it was given; the solve that follows reaches the
+    same objective as the untuned one."""
+    insts = members()[2:] if batch else [mid_gam(3, L=30_000, n=800, m=160)]
+
+    def loaded(s):
+        s.load_batch(insts) if batch else s.load(insts[0])
+
+    with Solver(precision=32) as s:
+        loaded(s)
+        ref = s.solve()
+    with Solver(precision=32) as s:
+        loaded(s)
+        s.step(70)
+        y = s.duals()
+        choice = s.autotune(16)
+        assert choice in (1, 2)
+        assert s.stats()["iters"] == 0
+        np.testing.assert_array_equal(s.duals(), y)
+        st = s.solve()
+    assert st["converged"] == 1 and st["kkt"] <= 1e-4
+    assert st["dual_avg"] == pytest.approx(ref["dual_avg"], rel=1e-4)
+    with Solver(precision=64) as s:
+        loaded(s)
+        assert s.autotune(4) == 1
