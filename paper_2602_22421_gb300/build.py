@@ -16,7 +16,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspfom.so")
 SOURCES = ["spfom_kernels.cu", "spfom_segments_fast.cu", "spfom_segments_tma.cu", "spfom_batch.cu",
-           "spfom_api.cu", "spfom_noalloc.cu"]
+           "spfom_api.cu", "spfom_noalloc.cu", "spfom_mlp.cu", "spfom_warm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing"]
 
@@ -33,7 +33,7 @@ def _stale() -> bool:
         return True
     t = os.path.getmtime(LIB)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f != "gb300_probe.cu"] + \
-        [os.path.join(INCLUDE, "spfom.h"), __file__]
+        [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)] + [__file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -10,11 +10,13 @@
 #include <cstdio>
 #include <cstring>
 #include <algorithm>
+#include <chrono>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "../../include/spfom.h"
+#include "../../include/spfom_mlp.h"
 #include "spfom_internal.h"
 
 using spfom::DevState;
@@ -53,6 +55,9 @@ struct spfom_ctx {
   std::vector<double> inst_tau;              // per-instance initial step sizes
   std::vector<double> inst_mean_r;           // per-instance mean price (step size after spfom_update)
   std::vector<spfom::InstState> h_inst;      // last state read back
+  // learned warm start: device scratch (features, outputs, demand, duals)
+  void* warm_buf = nullptr;
+  size_t warm_bytes = 0;
 };
 
 namespace {
@@ -375,6 +380,7 @@ void spfom_destroy(spfom_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->p.device);
   free_instance(ctx);
+  if (ctx->warm_buf) cudaFree(ctx->warm_buf);
   if (ctx->d_state) cudaFree(ctx->d_state);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
   if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -1051,4 +1057,113 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   if (s != SPFOM_OK) return s;
   if (choice_out) *choice_out = choice;
   return SPFOM_OK;
+}
+
+// ---- learned warm start (include/spfom_mlp.h) ------------------------------------
+
+namespace {
+
+struct WarmScratch {
+  float* feat;     // [m][16]
+  float* out;      // [m]
+  double* d;       // [m]
+  double* y;       // [m]
+  double* rho;     // [n]
+  double* totals;  // [4]
+};
+
+spfom_status warm_scratch(spfom_ctx* ctx, WarmScratch* w) {
+  const size_t m = (size_t)std::max(ctx->P.m, 1), n = (size_t)std::max(ctx->P.n, 1);
+  auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+  const size_t need = up(m * 16 * 4) + up(m * 4) + up(m * 8) * 2 + up(n * 8) + up(4 * 8);
+  if (need > ctx->warm_bytes) {
+    if (ctx->warm_buf) cudaFree(ctx->warm_buf);
+    ctx->warm_buf = nullptr;
+    ctx->warm_bytes = 0;
+    SPFOM_CUDA(ctx, cudaMalloc(&ctx->warm_buf, need));
+    ctx->warm_bytes = need;
+  }
+  char* p = static_cast<char*>(ctx->warm_buf);
+  w->feat = reinterpret_cast<float*>(p);
+  p += up(m * 16 * 4);
+  w->out = reinterpret_cast<float*>(p);
+  p += up(m * 4);
+  w->d = reinterpret_cast<double*>(p);
+  p += up(m * 8);
+  w->y = reinterpret_cast<double*>(p);
+  p += up(m * 8);
+  w->rho = reinterpret_cast<double*>(p);
+  p += up(n * 8);
+  w->totals = reinterpret_cast<double*>(p);
+  return SPFOM_OK;
+}
+
+// Features into `feat` (device [m][16]) on the ctx stream, with w's scratch.
+spfom_status features_into(spfom_ctx* ctx, const WarmScratch& w, float* feat) {
+  const Problem& P = ctx->P;
+  if (P.m) SPFOM_CUDA(ctx, cudaMemsetAsync(ctx->W.y_eval, 0, sizeof(double) * P.m, ctx->stream));
+  Work wk = ctx->W;
+  wk.s = ctx->W.s_eval;
+  cudaError_t e = spfom::launch_sales_at(P, wk, ctx->stream);
+  if (e == cudaSuccess) e = spfom::launch_features(P, wk.s, w.d, w.rho, w.totals, feat, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "feature launch");
+  return SPFOM_OK;
+}
+
+}  // namespace
+
+extern "C" spfom_status spfom_features(spfom_ctx* ctx, float* features) {
+  if (!ctx || !features) return SPFOM_EINVAL;
+  if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
+  if (ctx->W.batch) return fail(ctx, SPFOM_ENOTSUP, "features are per instance; load a single instance");
+  SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
+  WarmScratch w{};
+  spfom_status s = warm_scratch(ctx, &w);
+  if (s == SPFOM_OK) s = features_into(ctx, w, features);
+  if (s != SPFOM_OK) return s;
+  SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SPFOM_OK;
+}
+
+extern "C" spfom_status spfom_solve_warm(spfom_ctx* ctx, spfom_mlp* net, int64_t warm_iters, spfom_stats* out,
+                                         int32_t* mode_out) {
+  if (!ctx || !net) return SPFOM_EINVAL;
+  if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
+  if (ctx->W.batch) return fail(ctx, SPFOM_ENOTSUP, "the warm start is per instance; load a single instance");
+  const auto t0 = std::chrono::steady_clock::now();
+  SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
+  const Problem& P = ctx->P;
+  WarmScratch w{};
+  spfom_status s = warm_scratch(ctx, &w);
+  if (s == SPFOM_OK) s = features_into(ctx, w, w.feat);
+  if (s != SPFOM_OK) return s;
+  s = spfom_mlp_forward(net, w.feat, P.m, w.out, ctx->stream);
+  if (s != SPFOM_OK) return fail(ctx, s, "warm-start forward pass: %s", spfom_status_string(s));
+  cudaError_t e = spfom::launch_warm_duals(P.m, P.n, w.out, w.totals, w.y, ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "warm-start duals");
+  std::vector<double> y0((size_t)P.m), zero((size_t)P.m, 0.0);
+  if (P.m) SPFOM_CUDA(ctx, cudaMemcpyAsync(y0.data(), w.y, sizeof(double) * P.m, cudaMemcpyDeviceToHost, ctx->stream));
+  SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  // judge the prediction by the dual objective (an upper bound on the optimum: lower is better)
+  double dual_warm = 0.0, dual_cold = 0.0;
+  s = spfom_evaluate(ctx, y0.data(), nullptr, &dual_warm);
+  if (s == SPFOM_OK) s = spfom_evaluate(ctx, zero.data(), nullptr, &dual_cold);
+  if (s != SPFOM_OK) return s;
+  int mode = 0;
+  if (dual_warm < dual_cold) {
+    const long long cap = ctx->p.max_iters;
+    if (warm_iters > 0 && warm_iters < cap) ctx->p.max_iters = warm_iters;
+    s = spfom_solve(ctx, y0.data(), out);
+    ctx->p.max_iters = cap;
+    mode = 1;
+    if (s == SPFOM_ENOTCONV) {
+      mode = 2;
+      s = spfom_solve(ctx, nullptr, out);
+    }
+  } else {
+    s = spfom_solve(ctx, nullptr, out);
+  }
+  if (mode_out) *mode_out = mode;
+  if (out) out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return s;
 }

@@ -205,6 +205,10 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
 cudaError_t launch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s);
 cudaError_t launch_evaluate_at(const Problem& P, const Work& Wk, bool want_seg, cudaStream_t s);
 cudaError_t launch_sales_at(const Problem& P, const Work& Wk, cudaStream_t s);
+// learned warm start (spfom_warm.cu)
+cudaError_t launch_features(const Problem& P, const double* s0, double* d, double* rho, double* totals, float* f,
+                            cudaStream_t s);
+cudaError_t launch_warm_duals(int m, int n, const float* o, const double* totals, double* y, cudaStream_t s);
 int kernel_launches_per_iteration(const Work& Wk, const RunConfig& cfg);
 int kernel_launches_per_eval();
 

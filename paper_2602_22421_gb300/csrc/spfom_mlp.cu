@@ -1,0 +1,829 @@
+// The warm-start perceptron (include/spfom_mlp.h): BF16 tensor-core matrix
+// products on tcgen05 with FP32 accumulators in tensor memory, operands staged
+// by TMA, and the elementwise parts of the forward pass, the backward pass and
+// Adam as plain kernels.
+//
+// Every product is C[M x N] = A[M x K] . B[N x K]^T with both operands stored
+// K-contiguous in BF16 ("TN"), so each operand tile is a TMA box of 64 K
+// values (128 bytes) by 128 (A) or BN (B) rows with the 128-byte swizzle,
+// which is also the layout the tcgen05 shared-memory descriptor reads. The
+// transposes the backward pass needs are written by the epilogue of the
+// product that makes the matrix (a transposed BF16 copy), so no separate
+// transpose runs.
+//
+// One CTA of 128 threads computes a 128 x BN tile (BN = 16 or 256); thread 0
+// issues the TMA loads of a 4-stage ring and the MMAs (K = 16 per instruction),
+// tcgen05.commit releases each stage back to the loads, and a final commit
+// signals the four warps, which read the accumulator rows of their 32 TMEM
+// lanes and apply the epilogue (bias, ReLU, ReLU-backward mask, FP32 and BF16
+// stores, transposed BF16 store). Products with a long K (the weight
+// gradients, K = rows) split K over grid.y and sum the partial tiles in a
+// fixed order. Every wait is bounded; a wait that gives up sets the network's
+// error flag, and the host reports SPFOM_ETIMEOUT.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "../../include/spfom_mlp.h"
+#include "spfom_device.cuh"
+
+namespace spfom {
+namespace mlp {
+
+namespace {
+
+constexpr int kF = SPFOM_MLP_FEATURES;
+constexpr int kH = SPFOM_MLP_HIDDEN;
+constexpr int kBM = 128, kBK = 64, kStages = 4, kThreads = 128;
+constexpr int kOutPad = 16;  // the output layer runs as a 16-column product (column 0 used)
+constexpr int kKPad = 64;    // products with K = 16 read operands padded to one 64-wide TMA box
+
+// Offsets in the packed parameter vector.
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kH * kF, kOffW2 = kOffB1 + kH, kOffB2 = kOffW2 + kH * kH,
+              kOffW3 = kOffB2 + kH, kOffB3 = kOffW3 + kH, kParams = kOffB3 + 1;
+static_assert(kParams == SPFOM_MLP_PARAMS, "parameter layout");
+
+// ---- tcgen05 / TMA primitives -------------------------------------------------
+
+// Shared-memory matrix descriptor for a K-major operand in the 128-byte swizzle
+// layout: rows of 128 bytes, 8-row groups 1024 bytes apart (stride byte
+// offset), descriptor version 1, layout type 2 (128-byte swizzle).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused by swizzled K-major layouts)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t cols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)), "r"(cols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(cols) : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// ---- the product kernel ----------------------------------------------------------
+
+struct Epi {
+  int M, N;                      // valid rows and columns of C
+  int ksplit;                    // K tiles per CTA along grid.y
+  const float* bias;             // [N] added to every row, or null
+  int relu;                      // max(0, .) after the bias
+  const __nv_bfloat16* mask;     // keep C[r][c] only where mask[r][c] > 0 (ReLU backward), or null
+  int ldmask;
+  float* out32;                  // FP32 row-major (split k: partial tile of grid.y at out32 + y * M * ld32)
+  int ld32;
+  __nv_bfloat16* out16;          // BF16 row-major, or null
+  int ld16;
+  __nv_bfloat16* out16t;         // BF16 transposed: out16t[c * ld16t + r], or null
+  int ld16t;
+  int zpad;                      // rows M..zpad-1 of out16t are written as zeros (K padding of later products)
+  int* error;                    // set to 1 when a wait gives up
+};
+
+template <int BN>
+struct GemmShape {
+  static constexpr int kA = kBM * kBK * 2;  // bytes of an A stage (16 KB)
+  static constexpr int kB = BN * kBK * 2;   // bytes of a B stage
+  static constexpr int kStage = kA + kB;
+  static constexpr int kSmem = kStages * kStage + 1024;  // + alignment slack
+  static constexpr uint32_t kCols = BN < 32 ? 32 : BN;   // TMEM columns (power of two >= 32)
+  static_assert(kStage % 1024 == 0, "stages must keep the 1024-byte swizzle alignment");
+};
+
+__device__ __forceinline__ bool bf16_positive(__nv_bfloat16 h) {
+  const unsigned short b = __bfloat16_as_ushort(h);
+  return b != 0 && (b & 0x8000u) == 0;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_tn(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int K, Epi E) {
+  using S = GemmShape<BN>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], done;
+  __shared__ uint32_t tmem_base;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM;
+  const int KT = (K + kBK - 1) / kBK;
+  const int kt0 = blockIdx.y * E.ksplit;
+  const int nkt = max(0, min(KT, kt0 + E.ksplit) - kt0);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(smem_addr(&full[s]), 1);
+      mbar_init(smem_addr(&empty[s]), 1);
+    }
+    mbar_init(smem_addr(&done), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(&tmem_base, S::kCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_base;
+
+  int ok = 1;
+  if (threadIdx.x == 0 && nkt > 0) {
+    const uint32_t idesc = idesc_bf16(kBM, BN);
+    auto load = [&](int i) {
+      const int s = i % kStages;
+      const uint32_t a = smem_addr(base + s * S::kStage), fb = smem_addr(&full[s]);
+      mbar_expect_tx(fb, S::kStage);
+      tma_load_2d(a, &ta, (kt0 + i) * kBK, m0, fb);
+      tma_load_2d(a + S::kA, &tb, (kt0 + i) * kBK, 0, fb);
+    };
+    const int pre = nkt < kStages ? nkt : kStages;
+    for (int i = 0; i < pre; ++i) load(i);
+    int issued = pre, consumed = 0;
+    for (int i = 0; i < nkt; ++i) {
+      const int s = i % kStages;
+      if (!mbar_wait_bounded(smem_addr(&full[s]), (unsigned)(i / kStages) & 1u)) {
+        ok = 0;
+        break;
+      }
+      consumed = i + 1;
+      tc_fence_after();
+      const int kleft = K - (kt0 + i) * kBK;
+      const int ksteps = ((kleft < kBK ? kleft : kBK) + 15) / 16;
+      const uint32_t a = smem_addr(base + s * S::kStage), b = a + S::kA;
+      for (int kk = 0; kk < ksteps; ++kk)
+        umma_bf16(tmem, sdesc_sw128(a + kk * 32), sdesc_sw128(b + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
+      umma_commit(smem_addr(&empty[s]));
+      // refill the stage of the previous tile once its MMAs have read it
+      if (i >= 1 && i - 1 + kStages < nkt) {
+        const int p = i - 1;
+        if (!mbar_wait_bounded(smem_addr(&empty[p % kStages]), (unsigned)(p / kStages) & 1u)) {
+          ok = 0;
+          break;
+        }
+        load(p + kStages);
+        ++issued;
+      }
+    }
+    umma_commit(smem_addr(&done));
+    if (!ok) {
+      // let the copies still in flight land before the CTA can exit
+      for (int i = consumed; i < issued; ++i) mbar_wait_bounded(smem_addr(&full[i % kStages]), (unsigned)(i / kStages) & 1u);
+      atomicExch(E.error, 1);
+    }
+  }
+  __syncwarp();
+  int have = nkt > 0;
+  if (have && !mbar_wait_bounded(smem_addr(&done), 0u)) ok = 0;
+  const int any_fail = __syncthreads_or(!ok);
+  if (any_fail) {
+    if (threadIdx.x == 0) atomicExch(E.error, 1);
+    have = 0;
+  }
+  tc_fence_after();
+
+  const int row = m0 + warp * 32 + lane;
+  const bool row_ok = row < E.M;
+  if (E.out16t && !row_ok && row < E.zpad)
+    for (int c = 0; c < E.N; ++c) E.out16t[(size_t)c * E.ld16t + row] = __float2bfloat16_rn(0.f);
+  float* out32 = E.out32 ? E.out32 + (size_t)blockIdx.y * (size_t)E.M * (size_t)E.ld32 : nullptr;
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 16) {
+    uint32_t r[16];
+    if (have) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+    float v[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = have ? __uint_as_float(r[i]) : 0.f;
+    if (!row_ok || c0 >= E.N) continue;
+    const int nc = E.N - c0 < 16 ? E.N - c0 : 16;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      if (i < nc) {
+        if (E.bias) v[i] += E.bias[c0 + i];
+        if (E.relu) v[i] = v[i] > 0.f ? v[i] : 0.f;
+        if (E.mask && !bf16_positive(E.mask[(size_t)row * E.ldmask + c0 + i])) v[i] = 0.f;
+      }
+    }
+    if (out32)
+      for (int i = 0; i < nc; ++i) out32[(size_t)row * E.ld32 + c0 + i] = v[i];
+    if (E.out16) {
+      if (nc == 16 && (E.ld16 & 7) == 0) {
+        __align__(16) __nv_bfloat16 h[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) h[i] = __float2bfloat16_rn(v[i]);
+        uint4* dst = reinterpret_cast<uint4*>(E.out16 + (size_t)row * E.ld16 + c0);
+        dst[0] = reinterpret_cast<const uint4*>(h)[0];
+        dst[1] = reinterpret_cast<const uint4*>(h)[1];
+      } else {
+        for (int i = 0; i < nc; ++i) E.out16[(size_t)row * E.ld16 + c0 + i] = __float2bfloat16_rn(v[i]);
+      }
+    }
+    if (E.out16t)
+      for (int i = 0; i < nc; ++i) E.out16t[(size_t)(c0 + i) * E.ld16t + row] = __float2bfloat16_rn(v[i]);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    tmem_dealloc(tmem, S::kCols);
+  }
+}
+
+// ---- elementwise kernels -------------------------------------------------------
+
+constexpr int kEw = 256;
+
+// x (FP32 [rows][16]) -> BF16 row-major copy [rows][64] (columns 16..63 zero,
+// the K padding of the first product) and BF16 transposed copy [16][ldt]
+// (columns rows..zpad-1 zero).
+__global__ void k_inputs(const float* __restrict__ x, long long rows, long long zpad, __nv_bfloat16* __restrict__ xb,
+                         __nv_bfloat16* __restrict__ xt, long long ldt) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= zpad * kKPad) return;
+  const long long r = i / kKPad;
+  const int c = (int)(i % kKPad);
+  const __nv_bfloat16 h = (r < rows && c < kF) ? __float2bfloat16_rn(x[r * kF + c]) : __float2bfloat16_rn(0.f);
+  if (r < rows) xb[i] = h;
+  if (xt && c < kF) xt[(size_t)c * ldt + r] = h;
+}
+
+// Master FP32 parameters -> BF16 operands: W1 [256][64] (columns 16..63 zero),
+// W2 [256][256], its transpose W2t [256][256], the output row padded to 16 rows
+// (W3p [16][256], row 0 = w3), W3pt [256][64] (column 0 = w3, the rest zero),
+// and the padded output bias b3p [16].
+__global__ void k_weights(const float* __restrict__ p, __nv_bfloat16* __restrict__ w1, __nv_bfloat16* __restrict__ w2,
+                          __nv_bfloat16* __restrict__ w2t, __nv_bfloat16* __restrict__ w3p,
+                          __nv_bfloat16* __restrict__ w3pt, float* __restrict__ b3p) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kH * kKPad) {
+    const int o = i / kKPad, c = i % kKPad;
+    w1[i] = c < kF ? __float2bfloat16_rn(p[kOffW1 + o * kF + c]) : __float2bfloat16_rn(0.f);
+    w3pt[i] = c == 0 ? __float2bfloat16_rn(p[kOffW3 + o]) : __float2bfloat16_rn(0.f);
+  }
+  if (i < kH * kH) {
+    const int o = i / kH, c = i % kH;
+    const __nv_bfloat16 h = __float2bfloat16_rn(p[kOffW2 + i]);
+    w2[i] = h;
+    w2t[(size_t)c * kH + o] = h;
+  }
+  if (i < kOutPad * kH) {
+    const int rr = i / kH, c = i % kH;
+    w3p[i] = rr == 0 ? __float2bfloat16_rn(p[kOffW3 + c]) : __float2bfloat16_rn(0.f);
+  }
+  if (i < kOutPad) b3p[i] = i == 0 ? p[kOffB3] : 0.f;
+}
+
+// Output column 0 of the padded output product -> out[rows].
+__global__ void k_take_output(const float* __restrict__ o16, long long rows, float* __restrict__ out) {
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < rows) out[r] = o16[(size_t)r * kOutPad];
+}
+
+// Loss terms and the output gradient dO_r = 2 (o_r - t_r) / R (BF16, padded to
+// 16 columns, row-major and transposed); per-block sums of (o - t)^2.
+__global__ void k_loss(const float* __restrict__ o16, const float* __restrict__ t, long long rows, long long zpad,
+                       __nv_bfloat16* __restrict__ d16, __nv_bfloat16* __restrict__ d16t, long long ldt,
+                       double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double e2 = 0.0;
+  const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+  if (r < rows) {
+    const float e = o16[(size_t)r * kOutPad] - t[r];
+    e2 = (double)e * (double)e;
+    const __nv_bfloat16 g = __float2bfloat16_rn(2.f * e / (float)rows);
+    for (int c = 0; c < kKPad; ++c) d16[(size_t)r * kKPad + c] = c == 0 ? g : z;
+    for (int c = 0; c < kOutPad; ++c) d16t[(size_t)c * ldt + r] = c == 0 ? g : z;
+  } else if (r < zpad) {
+    for (int c = 0; c < kOutPad; ++c) d16t[(size_t)c * ldt + r] = z;
+  }
+  const double tot = block_sum_d(e2, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+__global__ void k_loss_finish(const double* __restrict__ partial, int nb, long long rows, double* __restrict__ loss) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[b];
+  s = block_sum_d(s, sh);
+  if (threadIdx.x == 0) loss[0] = rows > 0 ? s / (double)rows : 0.0;
+}
+
+// Bias gradient: g[c] = sum_r d[c][r] over the transposed BF16 gradient [C][ldt]
+// (one block per column, fixed order).
+__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dt, long long ldt, long long rows, float* __restrict__ g) {
+  __shared__ double sh[32];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (long long r = threadIdx.x; r < rows; r += blockDim.x) s += (double)__bfloat162float(dt[(size_t)c * ldt + r]);
+  s = block_sum_d(s, sh);
+  if (threadIdx.x == 0) g[c] = (float)s;
+}
+
+// Split-K partial tiles [splits][M][N] -> g (optionally only column 0, strided).
+__global__ void k_splitk_sum(const float* __restrict__ part, int splits, int M, int N, float* __restrict__ g,
+                             int col0_only) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cols = col0_only ? 1 : N;
+  if (i >= M * cols) return;
+  const int r = i / cols, c = col0_only ? 0 : i % cols;
+  float s = 0.f;
+  for (int k = 0; k < splits; ++k) s += part[(size_t)k * M * N + (size_t)r * N + c];
+  g[i] = s;
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m1,
+                       float* __restrict__ m2, int n, float lr, float bc1, float bc2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float a = 0.9f * m1[i] + 0.1f * gi;
+  const float b = 0.999f * m2[i] + 0.001f * gi * gi;
+  m1[i] = a;
+  m2[i] = b;
+  p[i] -= lr * (a / bc1) / (sqrtf(b / bc2) + 1e-8f);
+}
+
+int blocks(long long n) { return (int)((n + kEw - 1) / kEw); }
+
+// ---- host side -------------------------------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor map of a BF16 row-major matrix [rows][cols] with leading dimension ld
+// (elements), boxes of 64 columns by box_rows rows, 128-byte swizzle.
+bool make_map(CUtensorMap* map, const __nv_bfloat16* ptr, long long rows, long long cols, long long ld, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn || ((uintptr_t)ptr & 15) || (ld * 2) % 16) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+long long round64(long long x) { return (x + 63) / 64 * 64; }
+
+}  // namespace
+
+// C[M][N] = A[M][K] . B[N][K]^T (BF16 operands, K-contiguous, leading
+// dimensions lda, ldb), epilogue E (E.M, E.N set here). The operands must hold
+// zeros in columns K..round64(K)-1 (so every TMA box lies inside them: lda,
+// ldb >= round64(K)) and A must have max(M, 128) readable rows and B exactly
+// 16 (N <= 16) or 256 rows. splits > 1 splits K; the partial tiles then go to
+// E.out32 as [splits][M][ld32] and *splits_used (or NULL) gets their count.
+cudaError_t gemm_tn(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B, long long ldb, int M, int N, int K,
+                    int splits, Epi E, cudaStream_t s, int* splits_used = nullptr) {
+  CUtensorMap ta, tb;
+  const int bn = N <= 16 ? 16 : 256;
+  const long long kcols = round64(K);
+  if (N > 256 || M <= 0 || K <= 0 || lda < kcols || ldb < kcols) return cudaErrorInvalidValue;
+  if (!make_map(&ta, A, M > kBM ? M : kBM, kcols, lda, kBM) || !make_map(&tb, B, bn, kcols, ldb, bn))
+    return cudaErrorInvalidValue;
+  const int KT = (K + kBK - 1) / kBK;
+  if (splits < 1) splits = 1;
+  if (splits > KT) splits = KT;
+  E.ksplit = (KT + splits - 1) / splits;
+  splits = (KT + E.ksplit - 1) / E.ksplit;
+  if (splits_used) *splits_used = splits;
+  E.M = M;
+  E.N = N;
+  dim3 grid((M + kBM - 1) / kBM, splits);
+  if (bn == 16) {
+    k_gemm_tn<16><<<grid, kThreads, GemmShape<16>::kSmem, s>>>(ta, tb, K, E);
+  } else {
+    k_gemm_tn<256><<<grid, kThreads, GemmShape<256>::kSmem, s>>>(ta, tb, K, E);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t gemm_setup() {
+  cudaError_t e = cudaFuncSetAttribute(k_gemm_tn<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, GemmShape<16>::kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gemm_tn<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, GemmShape<256>::kSmem);
+  return e;
+}
+
+}  // namespace mlp
+}  // namespace spfom
+
+// ---- the network object and its C ABI ---------------------------------------------
+
+using spfom::mlp::Epi;
+
+struct spfom_mlp {
+  int device = 0;
+  int* d_error = nullptr;
+  float* p = nullptr;   // master parameters
+  float* g = nullptr;   // gradients
+  float* m1 = nullptr;  // Adam moments
+  float* m2 = nullptr;
+  long long adam_t = 0;
+  // BF16 operands
+  __nv_bfloat16 *w1 = nullptr, *w2 = nullptr, *w2t = nullptr, *w3p = nullptr, *w3pt = nullptr;
+  float* b3p = nullptr;
+  bool weights_stale = true;
+  // workspaces for `cap` rows
+  long long cap = 0;
+  std::vector<void*> ws;
+  __nv_bfloat16 *xb = nullptr, *xt = nullptr, *h1 = nullptr, *h1t = nullptr, *h2 = nullptr, *h2t = nullptr,
+                *d16 = nullptr, *d16t = nullptr, *dh2 = nullptr, *dh2t = nullptr, *dh1t = nullptr;
+  float* o16 = nullptr;
+  float* part = nullptr;  // split-K partial tiles
+  double* lpart = nullptr;
+  double* d_loss = nullptr;
+};
+
+namespace {
+
+constexpr int kMaxSplits = 64;
+
+void free_ws(spfom_mlp* n) {
+  for (void* q : n->ws) cudaFree(q);
+  n->ws.clear();
+  n->cap = 0;
+}
+
+template <typename T>
+cudaError_t wsalloc(spfom_mlp* n, T** out, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 256);
+  if (e != cudaSuccess) return e;
+  n->ws.push_back(q);
+  *out = static_cast<T*>(q);
+  return cudaSuccess;
+}
+
+cudaError_t ensure_rows(spfom_mlp* n, long long rows) {
+  if (rows <= n->cap) return cudaSuccess;
+  free_ws(n);
+  // capacity: a multiple of 64 (the transposed copies are K operands, padded
+  // with zeros to whole 64-wide boxes) and at least one 128-row tile
+  const long long R = spfom::mlp::round64(rows < 1024 ? 1024 : rows + rows / 4);
+  const int H = SPFOM_MLP_HIDDEN, KP = spfom::mlp::kKPad;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](auto** p, size_t c) {
+    if (e == cudaSuccess) e = wsalloc(n, p, c);
+  };
+  A(&n->xb, (size_t)R * KP);
+  A(&n->xt, (size_t)R * 16);
+  A(&n->h1, (size_t)R * H);
+  A(&n->h1t, (size_t)R * H);
+  A(&n->h2, (size_t)R * H);
+  A(&n->h2t, (size_t)R * H);
+  A(&n->d16, (size_t)R * KP);
+  A(&n->d16t, (size_t)R * 16);
+  A(&n->dh2, (size_t)R * H);
+  A(&n->dh2t, (size_t)R * H);
+  A(&n->dh1t, (size_t)R * H);
+  A(&n->o16, (size_t)R * 16);
+  A(&n->part, (size_t)kMaxSplits * H * H);
+  A(&n->lpart, (size_t)(R / 256 + 2));
+  A(&n->d_loss, 1);
+  // rows beyond the ones a call writes are read by the 128-row tiles (and
+  // discarded); start them at zero
+  for (size_t k = 0; k < n->ws.size() && e == cudaSuccess; ++k) e = cudaMemset(n->ws[k], 0, 256);
+  if (e == cudaSuccess) e = cudaMemset(n->xb, 0, (size_t)R * KP * 2);
+  if (e == cudaSuccess) e = cudaMemset(n->d16, 0, (size_t)R * KP * 2);
+  if (e == cudaSuccess) e = cudaMemset(n->h1, 0, (size_t)R * H * 2);
+  if (e == cudaSuccess) e = cudaMemset(n->h2, 0, (size_t)R * H * 2);
+  if (e == cudaSuccess) e = cudaMemset(n->dh2, 0, (size_t)R * H * 2);
+  if (e != cudaSuccess) {
+    free_ws(n);
+    return e;
+  }
+  n->cap = R;
+  return cudaSuccess;
+}
+
+spfom_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return SPFOM_OK;
+  return e == cudaErrorMemoryAllocation ? SPFOM_ENOMEM : (e == cudaErrorInvalidValue ? SPFOM_EINVAL : SPFOM_ECUDA);
+}
+
+#define MLP_TRY(call)                            \
+  do {                                           \
+    cudaError_t e_ = (call);                     \
+    if (e_ != cudaSuccess) return from_cuda(e_); \
+  } while (0)
+
+Epi epi(spfom_mlp* n) {
+  Epi E{};
+  E.error = n->d_error;
+  return E;
+}
+
+cudaError_t refresh_weights(spfom_mlp* n, cudaStream_t s) {
+  if (!n->weights_stale) return cudaSuccess;
+  const int H = SPFOM_MLP_HIDDEN;
+  spfom::mlp::k_weights<<<(H * H + 255) / 256, 256, 0, s>>>(n->p, n->w1, n->w2, n->w2t, n->w3p, n->w3pt, n->b3p);
+  n->weights_stale = false;
+  return cudaGetLastError();
+}
+
+// Forward pass over `rows` rows already in n->xb; with keep the transposed
+// activations for the backward pass are written too.
+cudaError_t forward_rows(spfom_mlp* n, long long rows, bool keep, cudaStream_t s) {
+  using spfom::mlp::gemm_tn;
+  const int H = SPFOM_MLP_HIDDEN, KP = spfom::mlp::kKPad;
+  const long long ldt = n->cap;
+  Epi E = epi(n);
+  E.bias = n->p + spfom::mlp::kOffB1;
+  E.relu = 1;
+  E.out16 = n->h1;
+  E.ld16 = H;
+  E.out16t = keep ? n->h1t : nullptr;
+  E.ld16t = (int)ldt;
+  E.zpad = (int)spfom::mlp::round64(rows);
+  cudaError_t e = gemm_tn(n->xb, KP, n->w1, KP, (int)rows, H, SPFOM_MLP_FEATURES, 1, E, s);
+  if (e != cudaSuccess) return e;
+  E.bias = n->p + spfom::mlp::kOffB2;
+  E.out16 = n->h2;
+  E.out16t = keep ? n->h2t : nullptr;
+  e = gemm_tn(n->h1, H, n->w2, H, (int)rows, H, H, 1, E, s);
+  if (e != cudaSuccess) return e;
+  Epi O = epi(n);
+  O.bias = n->b3p;
+  O.out32 = n->o16;
+  O.ld32 = 16;
+  return gemm_tn(n->h2, H, n->w3p, H, (int)rows, 16, H, 1, O, s);
+}
+
+int splits_for(long long rows, int mtiles) {
+  const long long kt = (rows + 63) / 64;
+  long long sp = 304 / mtiles;
+  if (sp > kt / 4) sp = kt / 4;
+  if (sp < 1) sp = 1;
+  if (sp > kMaxSplits) sp = kMaxSplits;
+  return (int)sp;
+}
+
+spfom_status check_error(spfom_mlp* n, cudaStream_t s) {
+  int err = 0;
+  MLP_TRY(cudaMemcpyAsync(&err, n->d_error, sizeof(int), cudaMemcpyDeviceToHost, s));
+  MLP_TRY(cudaStreamSynchronize(s));
+  return err ? SPFOM_ETIMEOUT : SPFOM_OK;
+}
+
+// Weight gradient g = (d^T a) for d^T [256][ldt], a^T [N][ldt] over `rows`
+// rows (split K, fixed-order sum); col0 keeps only column 0 (N = 16 padded).
+cudaError_t weight_grad(spfom_mlp* n, const __nv_bfloat16* dt, const __nv_bfloat16* at, int N, long long rows,
+                        float* g, bool col0, cudaStream_t s) {
+  const int H = SPFOM_MLP_HIDDEN;
+  Epi E = epi(n);
+  E.out32 = n->part;
+  E.ld32 = N;
+  int used = 1;
+  cudaError_t e = spfom::mlp::gemm_tn(dt, n->cap, at, n->cap, H, N, (int)rows, splits_for(rows, 2), E, s, &used);
+  if (e != cudaSuccess) return e;
+  const int outs = col0 ? H : H * N;
+  spfom::mlp::k_splitk_sum<<<(outs + 255) / 256, 256, 0, s>>>(n->part, used, H, N, g, col0 ? 1 : 0);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+spfom_status spfom_mlp_create(int32_t device, uint64_t seed, spfom_mlp** out) {
+  if (!out) return SPFOM_EINVAL;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) return SPFOM_ECUDA;
+  if (!spfom::mlp::encode_fn()) return SPFOM_ENOTSUP;
+  if (spfom::mlp::gemm_setup() != cudaSuccess) return SPFOM_ECUDA;
+  spfom_mlp* n = new spfom_mlp();
+  n->device = device;
+  const int P = SPFOM_MLP_PARAMS, H = SPFOM_MLP_HIDDEN;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](auto** p, size_t c) {
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(p), c * sizeof(**p));
+  };
+  A(&n->d_error, 1);
+  A(&n->p, P);
+  A(&n->g, P);
+  A(&n->m1, P);
+  A(&n->m2, P);
+  A(&n->w1, (size_t)H * 64);
+  A(&n->w2, (size_t)H * H);
+  A(&n->w2t, (size_t)H * H);
+  A(&n->w3p, (size_t)16 * H);
+  A(&n->w3pt, (size_t)H * 64);
+  A(&n->b3p, 16);
+  if (e == cudaSuccess) e = cudaMemset(n->d_error, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(n->g, 0, sizeof(float) * P);
+  if (e != cudaSuccess) {
+    spfom_mlp_destroy(n);
+    return from_cuda(e);
+  }
+  // seeded Glorot-uniform initialisation (splitmix64 stream)
+  std::vector<float> h(P, 0.f);
+  uint64_t st = seed;
+  auto uni = [&]() {
+    uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+  };
+  const double a1 = std::sqrt(6.0 / (16 + H)), a2 = std::sqrt(6.0 / (H + H)), a3 = std::sqrt(6.0 / (H + 1));
+  for (int i = 0; i < H * 16; ++i) h[spfom::mlp::kOffW1 + i] = (float)(a1 * uni());
+  for (int i = 0; i < H * H; ++i) h[spfom::mlp::kOffW2 + i] = (float)(a2 * uni());
+  for (int i = 0; i < H; ++i) h[spfom::mlp::kOffW3 + i] = (float)(a3 * uni());
+  spfom_status s = spfom_mlp_set_params(n, h.data());
+  if (s != SPFOM_OK) {
+    spfom_mlp_destroy(n);
+    return s;
+  }
+  *out = n;
+  return SPFOM_OK;
+}
+
+void spfom_mlp_destroy(spfom_mlp* n) {
+  if (!n) return;
+  cudaSetDevice(n->device);
+  free_ws(n);
+  void* ptrs[] = {n->d_error, n->p, n->g, n->m1, n->m2, n->w1, n->w2, n->w2t, n->w3p, n->w3pt, n->b3p};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  delete n;
+}
+
+spfom_status spfom_mlp_set_params(spfom_mlp* n, const float* params) {
+  if (!n || !params) return SPFOM_EINVAL;
+  for (int i = 0; i < SPFOM_MLP_PARAMS; ++i)
+    if (!std::isfinite(params[i])) return SPFOM_EINVAL;
+  MLP_TRY(cudaSetDevice(n->device));
+  MLP_TRY(cudaMemcpy(n->p, params, sizeof(float) * SPFOM_MLP_PARAMS, cudaMemcpyHostToDevice));
+  MLP_TRY(cudaMemset(n->m1, 0, sizeof(float) * SPFOM_MLP_PARAMS));
+  MLP_TRY(cudaMemset(n->m2, 0, sizeof(float) * SPFOM_MLP_PARAMS));
+  n->adam_t = 0;
+  n->weights_stale = true;
+  return SPFOM_OK;
+}
+
+spfom_status spfom_mlp_get_params(spfom_mlp* n, float* params) {
+  if (!n || !params) return SPFOM_EINVAL;
+  MLP_TRY(cudaSetDevice(n->device));
+  MLP_TRY(cudaMemcpy(params, n->p, sizeof(float) * SPFOM_MLP_PARAMS, cudaMemcpyDeviceToHost));
+  return SPFOM_OK;
+}
+
+spfom_status spfom_mlp_get_grads(spfom_mlp* n, float* grads) {
+  if (!n || !grads) return SPFOM_EINVAL;
+  MLP_TRY(cudaSetDevice(n->device));
+  MLP_TRY(cudaMemcpy(grads, n->g, sizeof(float) * SPFOM_MLP_PARAMS, cudaMemcpyDeviceToHost));
+  return SPFOM_OK;
+}
+
+spfom_status spfom_mlp_forward(spfom_mlp* n, const float* x, int64_t rows, float* out, void* stream) {
+  if (!n || rows < 0 || (rows > 0 && (!x || !out)) || rows > (1ll << 28)) return SPFOM_EINVAL;
+  if (rows == 0) return SPFOM_OK;
+  MLP_TRY(cudaSetDevice(n->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  MLP_TRY(ensure_rows(n, rows));
+  MLP_TRY(refresh_weights(n, s));
+  const long long zp = spfom::mlp::round64(rows);
+  spfom::mlp::k_inputs<<<spfom::mlp::blocks(zp * spfom::mlp::kKPad), spfom::mlp::kEw, 0, s>>>(x, rows, zp, n->xb,
+                                                                                              nullptr, n->cap);
+  MLP_TRY(cudaGetLastError());
+  MLP_TRY(forward_rows(n, rows, false, s));
+  spfom::mlp::k_take_output<<<spfom::mlp::blocks(rows), spfom::mlp::kEw, 0, s>>>(n->o16, rows, out);
+  MLP_TRY(cudaGetLastError());
+  return check_error(n, s);
+}
+
+spfom_status spfom_mlp_loss_grad(spfom_mlp* n, const float* x, const float* t, int64_t rows, double* loss,
+                                 void* stream) {
+  using spfom::mlp::gemm_tn;
+  if (!n || rows <= 0 || !x || !t || rows > (1ll << 28)) return SPFOM_EINVAL;
+  MLP_TRY(cudaSetDevice(n->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int H = SPFOM_MLP_HIDDEN, KP = spfom::mlp::kKPad;
+  MLP_TRY(ensure_rows(n, rows));
+  MLP_TRY(refresh_weights(n, s));
+  const long long ldt = n->cap, zp = spfom::mlp::round64(rows);
+  spfom::mlp::k_inputs<<<spfom::mlp::blocks(zp * KP), spfom::mlp::kEw, 0, s>>>(x, rows, zp, n->xb, n->xt, ldt);
+  MLP_TRY(cudaGetLastError());
+  MLP_TRY(forward_rows(n, rows, true, s));
+  const int lb = spfom::mlp::blocks(zp);
+  spfom::mlp::k_loss<<<lb, spfom::mlp::kEw, 0, s>>>(n->o16, t, rows, zp, n->d16, n->d16t, ldt, n->lpart);
+  spfom::mlp::k_loss_finish<<<1, 256, 0, s>>>(n->lpart, lb, rows, n->d_loss);
+  MLP_TRY(cudaGetLastError());
+  float* g = n->g;
+  // output layer: dw3 = h2^T dO (a [256][16] product, column 0), db3 = sum dO
+  MLP_TRY(weight_grad(n, n->h2t, n->d16t, 16, rows, g + spfom::mlp::kOffW3, true, s));
+  spfom::mlp::k_bias_grad<<<1, 256, 0, s>>>(n->d16t, ldt, rows, g + spfom::mlp::kOffB3);
+  // dH2 = (dO w3^T) masked by h2 > 0
+  {
+    Epi E = epi(n);
+    E.mask = n->h2;
+    E.ldmask = H;
+    E.out16 = n->dh2;
+    E.ld16 = H;
+    E.out16t = n->dh2t;
+    E.ld16t = (int)ldt;
+    E.zpad = (int)zp;
+    MLP_TRY(gemm_tn(n->d16, KP, n->w3pt, KP, (int)rows, H, 16, 1, E, s));
+  }
+  // dW2 = dH2^T h1, db2 = sum dH2
+  MLP_TRY(weight_grad(n, n->dh2t, n->h1t, H, rows, g + spfom::mlp::kOffW2, false, s));
+  spfom::mlp::k_bias_grad<<<H, 256, 0, s>>>(n->dh2t, ldt, rows, g + spfom::mlp::kOffB2);
+  // dH1 = (dH2 W2) masked by h1 > 0 (transposed copy only)
+  {
+    Epi E = epi(n);
+    E.mask = n->h1;
+    E.ldmask = H;
+    E.out16t = n->dh1t;
+    E.ld16t = (int)ldt;
+    E.zpad = (int)zp;
+    MLP_TRY(gemm_tn(n->dh2, H, n->w2t, H, (int)rows, H, H, 1, E, s));
+  }
+  // dW1 = dH1^T x, db1 = sum dH1
+  MLP_TRY(weight_grad(n, n->dh1t, n->xt, 16, rows, g + spfom::mlp::kOffW1, false, s));
+  spfom::mlp::k_bias_grad<<<H, 256, 0, s>>>(n->dh1t, ldt, rows, g + spfom::mlp::kOffB1);
+  MLP_TRY(cudaGetLastError());
+  if (loss) MLP_TRY(cudaMemcpyAsync(loss, n->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
+  return check_error(n, s);
+}
+
+spfom_status spfom_mlp_adam(spfom_mlp* n, float lr, void* stream) {
+  if (!n || !(lr > 0.f) || !std::isfinite(lr)) return SPFOM_EINVAL;
+  MLP_TRY(cudaSetDevice(n->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  n->adam_t += 1;
+  const float bc1 = 1.f - (float)std::pow(0.9, (double)n->adam_t);
+  const float bc2 = 1.f - (float)std::pow(0.999, (double)n->adam_t);
+  spfom::mlp::k_adam<<<spfom::mlp::blocks(SPFOM_MLP_PARAMS), spfom::mlp::kEw, 0, s>>>(
+      n->p, n->g, n->m1, n->m2, SPFOM_MLP_PARAMS, lr, bc1, bc2);
+  n->weights_stale = true;
+  MLP_TRY(cudaGetLastError());
+  return SPFOM_OK;
+}
+
+spfom_status spfom_mlp_train_step(spfom_mlp* n, const float* x, const float* t, int64_t rows, float lr, double* loss,
+                                  void* stream) {
+  spfom_status st = spfom_mlp_loss_grad(n, x, t, rows, loss, stream);
+  if (st != SPFOM_OK) return st;
+  return spfom_mlp_adam(n, lr, stream);
+}
+
+}  // extern "C"

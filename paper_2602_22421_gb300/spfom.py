@@ -1,4 +1,4 @@
-"""Python binding of libspfom.so (the C ABI of include/spfom.h).
+"""Python binding of libspfom.so (the C ABI of include/spfom.h and include/spfom_mlp.h).
 
 Argument marshalling only: every step of the iteration runs in the library's
 sm_103a kernels. The library must be built (``build.build()``); importing this
@@ -19,11 +19,17 @@ LIB = os.path.join(HERE, "libspfom.so")
 OK, EINVAL, ENOMEM, ECUDA, ESTATE, ETIMEOUT, ENOTCONV, ENOTSUP = range(8)
 VEC_Y, VEC_YBAR, VEC_SUM_Y, VEC_SUM_G, VEC_G, VEC_S, VEC_MARGINS = range(7)
 
-# Every function include/spfom.h declares.
+# Every function the headers under include/ declare.
 EXPORTS = ("spfom_default_params", "spfom_create", "spfom_load_instance", "spfom_reset", "spfom_step",
            "spfom_solve", "spfom_vector", "spfom_duals", "spfom_evaluate", "spfom_get_stats", "spfom_destroy",
            "spfom_last_error", "spfom_status_string", "spfom_sales_noalloc", "spfom_load_batch",
-           "spfom_batch_stats", "spfom_update", "spfom_sales_at", "spfom_autotune")
+           "spfom_batch_stats", "spfom_update", "spfom_sales_at", "spfom_autotune",
+           "spfom_mlp_create", "spfom_mlp_destroy", "spfom_mlp_set_params", "spfom_mlp_get_params",
+           "spfom_mlp_get_grads", "spfom_mlp_forward", "spfom_mlp_loss_grad", "spfom_mlp_adam",
+           "spfom_mlp_train_step", "spfom_features", "spfom_solve_warm")
+
+MLP_FEATURES, MLP_HIDDEN = 16, 256
+MLP_PARAMS = 256 * 16 + 256 + 256 * 256 + 256 + 256 + 1
 
 _f64p = C.POINTER(C.c_double)
 _i32p = C.POINTER(C.c_int32)
@@ -112,6 +118,24 @@ def lib():
         h.spfom_sales_at.argtypes = [C.c_void_p, _f64p, _f64p]
         h.spfom_autotune.argtypes = [C.c_void_p, C.c_int32, P(C.c_int32)]
         for f in ("spfom_load_batch", "spfom_batch_stats", "spfom_update", "spfom_sales_at", "spfom_autotune"):
+            getattr(h, f).restype = C.c_int
+        _f32p = C.POINTER(C.c_float)
+        h.spfom_mlp_create.argtypes = [C.c_int32, C.c_uint64, P(C.c_void_p)]
+        h.spfom_mlp_destroy.argtypes = [C.c_void_p]
+        h.spfom_mlp_destroy.restype = None
+        h.spfom_mlp_set_params.argtypes = [C.c_void_p, _f32p]
+        h.spfom_mlp_get_params.argtypes = [C.c_void_p, _f32p]
+        h.spfom_mlp_get_grads.argtypes = [C.c_void_p, _f32p]
+        h.spfom_mlp_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+        h.spfom_mlp_loss_grad.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, _f64p, C.c_void_p]
+        h.spfom_mlp_adam.argtypes = [C.c_void_p, C.c_float, C.c_void_p]
+        h.spfom_mlp_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, _f64p,
+                                           C.c_void_p]
+        h.spfom_features.argtypes = [C.c_void_p, C.c_void_p]
+        h.spfom_solve_warm.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, P(Stats), P(C.c_int32)]
+        for f in ("spfom_mlp_create", "spfom_mlp_set_params", "spfom_mlp_get_params", "spfom_mlp_get_grads",
+                  "spfom_mlp_forward", "spfom_mlp_loss_grad", "spfom_mlp_adam", "spfom_mlp_train_step",
+                  "spfom_features", "spfom_solve_warm"):
             getattr(h, f).restype = C.c_int
         for f in ("spfom_create", "spfom_load_instance", "spfom_reset", "spfom_step", "spfom_solve", "spfom_vector",
                   "spfom_duals", "spfom_evaluate", "spfom_get_stats"):
@@ -237,6 +261,24 @@ class Solver:
         self._check(self._lib.spfom_autotune(self._h, int(iters), C.byref(ch)))
         return ch.value
 
+    def features(self, out=None):
+        """Per-resource warm-start features (spfom_features) as a CUDA torch
+        tensor [m, 16] (float32); ``out`` may supply it."""
+        import torch
+        if out is None:
+            out = torch.empty((max(self.m, 1), MLP_FEATURES), dtype=torch.float32, device="cuda")
+        self._check(self._lib.spfom_features(self._h, C.c_void_p(out.data_ptr())))
+        return out[:self.m]
+
+    def solve_warm(self, net: "MLP", warm_iters: int = 0):
+        """spfom_solve_warm: (stats, mode) with mode 0 = prediction rejected
+        (cold start), 1 = warm start converged, 2 = fell back to a cold start."""
+        st, mode = Stats(), C.c_int32(-1)
+        rc = self._lib.spfom_solve_warm(self._h, net._h, int(warm_iters), C.byref(st), C.byref(mode))
+        if rc not in (OK, ENOTCONV):
+            self._check(rc)
+        return st.as_dict(), mode.value
+
     def reset(self, y0=None):
         y = None if y0 is None else np.ascontiguousarray(y0, np.float64)
         self._check(self._lib.spfom_reset(self._h, _p(y, _f64p)))
@@ -280,6 +322,90 @@ class Solver:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.spfom_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class MLP:
+    """The warm-start network of include/spfom_mlp.h (spfom_mlp_*). Device
+    arrays are CUDA torch tensors (float32, contiguous)."""
+
+    def __init__(self, device: int = 0, seed: int = 0):
+        self._lib = lib()
+        h = C.c_void_p()
+        st = self._lib.spfom_mlp_create(int(device), int(seed) & (2**64 - 1), C.byref(h))
+        if st != OK:
+            raise SpfomError(st, "spfom_mlp_create: " + self._lib.spfom_status_string(st).decode())
+        self._h = h
+
+    def _check(self, st: int, what: str):
+        if not getattr(self, "_h", None):
+            raise SpfomError(ESTATE, "network is closed")
+        if st != OK:
+            raise SpfomError(st, f"{what}: " + self._lib.spfom_status_string(st).decode())
+
+    @staticmethod
+    def _dev(t, rows, cols=None):
+        import torch
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+        assert t.shape[0] >= rows and (cols is None or (t.dim() == 2 and t.shape[1] == cols))
+        return C.c_void_p(t.data_ptr())
+
+    @property
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, np.float32)
+        self._check(self._lib.spfom_mlp_get_params(self._h, out.ctypes.data_as(C.POINTER(C.c_float))), "get_params")
+        return out
+
+    @params.setter
+    def params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        assert p.shape == (MLP_PARAMS,)
+        self._check(self._lib.spfom_mlp_set_params(self._h, p.ctypes.data_as(C.POINTER(C.c_float))), "set_params")
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, np.float32)
+        self._check(self._lib.spfom_mlp_get_grads(self._h, out.ctypes.data_as(C.POINTER(C.c_float))), "get_grads")
+        return out
+
+    def forward(self, x, out=None):
+        import torch
+        rows = int(x.shape[0])
+        if out is None:
+            out = torch.empty(max(rows, 1), dtype=torch.float32, device=x.device)
+        self._check(self._lib.spfom_mlp_forward(self._h, self._dev(x, rows, MLP_FEATURES), rows,
+                                                self._dev(out, rows), _current_stream()), "forward")
+        return out[:rows]
+
+    def loss_grad(self, x, t) -> float:
+        rows, loss = int(x.shape[0]), C.c_double(0.0)
+        self._check(self._lib.spfom_mlp_loss_grad(self._h, self._dev(x, rows, MLP_FEATURES), self._dev(t, rows), rows,
+                                                  C.byref(loss), _current_stream()), "loss_grad")
+        return loss.value
+
+    def adam(self, lr: float):
+        self._check(self._lib.spfom_mlp_adam(self._h, float(lr), _current_stream()), "adam")
+
+    def train_step(self, x, t, lr: float) -> float:
+        rows, loss = int(x.shape[0]), C.c_double(0.0)
+        self._check(self._lib.spfom_mlp_train_step(self._h, self._dev(x, rows, MLP_FEATURES), self._dev(t, rows),
+                                                   rows, float(lr), C.byref(loss), _current_stream()), "train_step")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.spfom_mlp_destroy(self._h)
             self._h = None
 
     def __del__(self):

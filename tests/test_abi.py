@@ -8,6 +8,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "spfom.h")
+HEADERS = [os.path.join(ROOT, "include", f) for f in ("spfom.h", "spfom_mlp.h")]
 
 
 @pytest.fixture(scope="module")
@@ -17,9 +18,11 @@ def libpath():
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(spfom_[a-z_]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(spfom_[a-z_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_the_api():
