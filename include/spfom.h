@@ -88,6 +88,10 @@ typedef struct {
   int32_t polish;            /* precision 32 only, 1 (default): once a binary64 evaluation finds
                                 KKT <= kkt_tol, spfom_solve continues with binary64 iterations
                                 until the next evaluation confirms it; 0: stop at the first */
+  int32_t track_xbar;        /* 0 (default); 1: keep, per nonzero, the sum of every segment's
+                                response since the last restart (x-bar of spfom_xbar, 8 B per
+                                nonzero read and written each iteration); needs precision 64,
+                                batch_frac 1 and a single instance, and runs the general kernel */
   void* stream;              /* cudaStream_t to run on; NULL (default): the ctx creates one */
 } spfom_params;
 
@@ -242,6 +246,33 @@ spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out);
  * iteration from those duals. *choice_out (or NULL) gets the choice; with a
  * single candidate it just reports it. */
 spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* choice_out);
+
+/* ---- Recovering assortments (Section 4.4) ----------------------------------
+ * The sales-based LP the iteration solves has one variable per (segment,
+ * product); a recommendation needs the choice-based LP's variables, the
+ * probability with which each assortment is offered. */
+
+/* The primal average x-bar (host [nnz] out, CSR order of the consideration
+ * sets): the mean of every segment's responses over the iterations since the
+ * last restart -- the primal point whose consumption is g-bar (solver
+ * addition). ESTATE unless the ctx was created with track_xbar = 1 and has
+ * iterated. */
+spfom_status spfom_xbar(spfom_ctx* ctx, double* out);
+
+/* Assortment probabilities from sales (Lemma recover): for each segment l,
+ * with u_k = x_k / v_k ranked descending (ties: lower CSR position first),
+ * x_0 = lam - sum_k (vt_k / v_k) x_k, u_0 = x_0 / vt_0, D_r = vt_0 + the vt of
+ * the top r products:
+ *   alpha[seg_ptr[l] + l]     = (u_0 - u_(1)) vt_0 / lam  (the empty assortment)
+ *   alpha[seg_ptr[l] + l + r] = (u_(r) - u_(r+1)) D_r / lam, r = 1..K, u_(K+1) = 0
+ * (the top-r products, r = 1..K), so that lam sum_r alpha_r v_j / D_r over the
+ * sets holding j gives x_j back and the alphas of a segment sum to 1;
+ * order[seg_ptr[l] + r - 1] = CSR position within the segment of the rank-r
+ * product. x: host [nnz] sales, or NULL for spfom_xbar's x-bar. alpha: host
+ * [nnz + L] out; order: host [nnz] out or NULL. A segment with lam = 0 gets
+ * alpha = (1, 0, ..., 0). Sales outside the sales-based LP's polytope give
+ * negative alphas (no error). Sets of <= 32 products. */
+spfom_status spfom_recover(spfom_ctx* ctx, const double* x, double* alpha, int32_t* order);
 
 /* Free the ctx and all its device memory (NULL is a no-op). */
 void spfom_destroy(spfom_ctx* ctx);

@@ -224,6 +224,38 @@ def paper_shaped(seed: int = 3, L: int = 100_000, n: int = 100) -> Instance:
                          name=f"paper_shaped(n={n},L={L},seed={seed})")
 
 
+def batch_base(seed: int, k: int) -> Instance:
+    """Base instance k of the batched multi-period family: n ~ U{200..5000},
+    m = ceil(n / 5), L = floor(10^U(3, 5)), |C_l| ~ U{3..20}, the mid
+    instance's distributions (c = 0.6 x demand of one period)."""
+    rng = np.random.default_rng([seed, k])
+    n = int(rng.integers(200, 5001))
+    m = -(-n // 5)
+    L = int(10.0 ** rng.uniform(3.0, 5.0))
+    return make_instance(n=n, m=m, L=L, kmin=3, kmax=20, res_min=1, res_max=3, gam=True, tightness=0.6,
+                         seed=int(rng.integers(1 << 62)), name=f"batch_base(seed={seed},k={k},n={n},L={L})")
+
+
+def batch_family(seed: int = 4, count: int = 256) -> list:
+    """The batched multi-period family: `count` base instances of uneven size."""
+    return [batch_base(seed, k) for k in range(count)]
+
+
+def period_rates(seed: int, count: int, periods: int = 16) -> np.ndarray:
+    """Arrival-rate multipliers rho[period, instance] ~ U(0.5, 1.5)."""
+    return np.random.default_rng([seed, 99]).uniform(0.5, 1.5, (periods, count))
+
+
+def warm_family(seed: int, k: int, L_lo: float = 1e4, L_hi: float = 5e4) -> Instance:
+    """Instance k of the learned-warm-start family: the huge instance's
+    distributions (|C_l| ~ U{10..30}, c = 0.4 x demand) at reduced size,
+    n = 2000 products, m = 400 resources, L = floor(10^U(log10 L_lo, log10 L_hi))."""
+    rng = np.random.default_rng([seed, k, 5])
+    L = int(10.0 ** rng.uniform(np.log10(L_lo), np.log10(L_hi)))
+    return make_instance(n=2000, m=400, L=L, kmin=10, kmax=30, res_min=1, res_max=3, gam=True, tightness=0.4,
+                         seed=int(rng.integers(1 << 62)), name=f"warm_family(seed={seed},k={k},L={L})")
+
+
 def seeded_duals(m: int, seed: int, scale: float, frac_zero: float = 0.3) -> np.ndarray:
     """A seeded nonnegative dual vector: zero with probability frac_zero,
     else scale x U(0,1)."""

@@ -54,7 +54,7 @@ class _Params(C.Structure):
 
 class _State(C.Structure):
     _fields_ = [("y", _f64p), ("sum_y", _f64p), ("sum_g", _f64p), ("s", _f64p), ("g", _f64p), ("x_cur", _f64p),
-                ("sum_P", C.c_double), ("count", C.c_int64), ("t", C.c_int64), ("restarts", C.c_int64),
+                ("sum_x", _f64p), ("sum_P", C.c_double), ("count", C.c_int64), ("t", C.c_int64), ("restarts", C.c_int64),
                 ("mu_cur", C.c_double), ("tau_used", C.c_double), ("kkt_anchor", C.c_double),
                 ("z_sum", C.c_double), ("P", C.c_double), ("dual_iter", C.c_double),
                 ("kkt", C.c_double), ("pinf", C.c_double), ("gap", C.c_double), ("dual_avg", C.c_double),
@@ -86,6 +86,8 @@ def lib():
         h.orc_state_init.argtypes = [P(_Inst), P(_Params), P(_State)]
         h.orc_run.argtypes = [P(_Inst), P(_Params), P(_State), C.c_int64]
         h.orc_run.restype = C.c_int
+        h.orc_recover.argtypes = [P(_Inst), _f64p, _f64p, _i32p]
+        h.orc_recover.restype = None
         _lib = h
     return _lib
 
@@ -177,8 +179,18 @@ class Oracle:
     def default_tau(self, tau0: float) -> float:
         return self._lib.orc_default_tau(C.byref(self._c), tau0)
 
-    def run(self, params: Optional[Params] = None, y0=None) -> "OracleRun":
-        return OracleRun(self, params or Params(), y0)
+    def run(self, params: Optional[Params] = None, y0=None, track_x: bool = False) -> "OracleRun":
+        return OracleRun(self, params or Params(), y0, track_x)
+
+    # --- f4 -------------------------------------------------------------------
+    def recover(self, x):
+        """Assortment probabilities (Lemma recover): (alpha [nnz + L], order [nnz])."""
+        x = np.ascontiguousarray(x, np.float64)
+        I = self.inst
+        alpha = np.empty(I.nnz + I.L)
+        order = np.empty(max(I.nnz, 1), np.int32)
+        self._lib.orc_recover(C.byref(self._c), _p(x, _f64p), _p(alpha, _f64p), _p(order, _i32p))
+        return alpha, order[:I.nnz]
 
 
 def sample_hash(seed: int, t: int, l: int) -> int:
@@ -188,16 +200,17 @@ def sample_hash(seed: int, t: int, l: int) -> int:
 class OracleRun:
     """SPFOM run state on the oracle: ``step(k)`` advances k iterations."""
 
-    def __init__(self, orc: Oracle, params: Params, y0=None):
+    def __init__(self, orc: Oracle, params: Params, y0=None, track_x: bool = False):
         I = orc.inst
         self.orc, self.params = orc, params
         self.y = np.zeros(I.m) if y0 is None else np.array(y0, np.float64)
         self.sum_y, self.sum_g = np.zeros(I.m), np.zeros(I.m)
         self.s, self.g = np.zeros(I.n), np.zeros(I.m)
         self.x_cur = np.zeros(I.nnz) if params.batch_frac < 1.0 else None
+        self.sum_x = np.zeros(max(I.nnz, 1)) if track_x else None
         self._pc = params._c()
         self._st = _State(_p(self.y, _f64p), _p(self.sum_y, _f64p), _p(self.sum_g, _f64p), _p(self.s, _f64p),
-                          _p(self.g, _f64p), _p(self.x_cur, _f64p))
+                          _p(self.g, _f64p), _p(self.x_cur, _f64p), _p(self.sum_x, _f64p))
         orc._lib.orc_state_init(C.byref(orc._c), C.byref(self._pc), C.byref(self._st))
         if y0 is not None:  # orc_state_init leaves y alone
             self.y[:] = np.asarray(y0, np.float64)
@@ -210,7 +223,16 @@ class OracleRun:
 
     def stats(self) -> dict:
         st = self._st
-        return {k: getattr(st, k) for k, _ in _State._fields_ if k not in ("y", "sum_y", "sum_g", "s", "g", "x_cur")}
+        return {k: getattr(st, k) for k, _ in _State._fields_
+                if k not in ("y", "sum_y", "sum_g", "s", "g", "x_cur", "sum_x")}
+
+    @property
+    def xbar(self) -> np.ndarray:
+        """Epoch average of every segment's response, per nonzero (track_x runs)."""
+        if self.sum_x is None:
+            raise RuntimeError("run made without track_x")
+        c = self._st.count
+        return self.sum_x[:self.orc.inst.nnz] / c if c > 0 else np.full(self.orc.inst.nnz, math.nan)
 
     @property
     def ybar(self) -> np.ndarray:

@@ -36,6 +36,11 @@
  *       instances; y >= 0; y stays 0 when capacities do not bind;
  *   orc_run KKT residual and restart  -- parity unpinned beyond the
  *       convergence test: the paper defines neither.
+ *   orc_recover (Lemma recover, Section 4.4) -- the recovered assortment
+ *       probabilities reproduce the sales through the closed-form choice
+ *       probabilities, sum to one, and turn the SBLP optimum (HiGHS) into a
+ *       CBLP solution with the CBLP optimum's revenue (HiGHS on the
+ *       enumerated CBLP).
  */
 #include <math.h>
 #include <stdint.h>
@@ -79,6 +84,7 @@ typedef struct {
   double* s;       /* [n] product sales of the last iteration */
   double* g;       /* [m] resource consumption of the last iteration */
   double* x_cur;   /* [nnz] current response of every segment (batch_frac < 1 only) */
+  double* sum_x;   /* [nnz] epoch sum of every segment's response (solver addition), or NULL */
   /* scalars */
   double sum_P;
   int64_t count;   /* iterations in the current restart epoch */
@@ -462,6 +468,11 @@ int orc_run(const orc_instance* I, const orc_params* P, orc_state* S, int64_t it
           for (int64_t p = b; p < e; ++p) S->x_cur[p] = xbuf[p - b];
       }
       for (int64_t p = b; p < e; ++p) S->s[I->seg_prod[p]] += full ? xbuf[p - b] : S->x_cur[p];
+      if (S->sum_x)  /* the first iteration of an epoch starts the sums afresh */
+        for (int64_t p = b; p < e; ++p) {
+          double x = full ? xbuf[p - b] : S->x_cur[p];
+          S->sum_x[p] = S->count == 0 ? x : S->sum_x[p] + x;
+        }
     }
     double Pv;
     aggregate(I, S->s, S->g, &Pv);
@@ -488,4 +499,70 @@ int orc_run(const orc_instance* I, const orc_params* P, orc_state* S, int64_t it
   free(marg);
   free(yprev);
   return 0;
+}
+
+/* ------------------------------------------------------------ f4 -------- */
+/* Assortment probabilities from sales (Lemma recover, Section 4.4), GAM form
+ * in build letters. For segment l with sales x_k (k in C_l, CSR order):
+ *   u_k = x_k / v_k, the no-purchase sales x_0 = lam - sum_k (vt_k / v_k) x_k
+ *   (the balance row), u_0 = x_0 / vt_0;
+ *   rank the products by u descending (ties: lower CSR position first):
+ *   u_(1) >= ... >= u_(K), u_(K+1) = 0; D_r = vt_0 + sum_{q <= r} vt_(q);
+ *   alpha_0 = (u_0 - u_(1)) vt_0 / lam            (the empty assortment),
+ *   alpha_r = (u_(r) - u_(r+1)) D_r / lam, r = 1..K (the top-r products).
+ * Since the choice probability of product j in the top-r set is v_j / D_r,
+ * lam sum_{r >= rank(j)} alpha_r v_j / D_r = v_j u_(rank j) = x_j (the sum
+ * telescopes), and sum_r alpha_r = (x_0 + sum_k (vt_k / v_k) x_k) / lam = 1;
+ * SBLP feasibility (x >= 0, x_k / v_k <= x_0 / vt_0) makes every alpha >= 0.
+ * The paper sorts by y_ij / w_ij and sums the attractions of S_il = {0..l}
+ * (no-purchase included): the same construction with its letters.
+ * Output: alpha[seg_ptr[l] + l + r] for r = 0..K; order[seg_ptr[l] + r - 1] =
+ * CSR position (within the segment) of the rank-r product. A segment with
+ * lam = 0 gets alpha_0 = 1 and zeros. */
+void orc_recover(const orc_instance* I, const double* x, double* alpha, int32_t* order) {
+  int32_t pos[ORC_KMAX];
+  double u[ORC_KMAX];
+  for (int64_t l = 0; l < I->L; ++l) {
+    int64_t b = I->seg_ptr[l];
+    int K = (int)(I->seg_ptr[l + 1] - b);
+    double lam = I->lam[l], vt0 = I->v0[l], bal = 0.0;
+    for (int k = 0; k < K; ++k) {
+      double w = I->w ? I->w[b + k] : 0.0;
+      vt0 += w;
+    }
+    for (int k = 0; k < K; ++k) {
+      double v = I->v[b + k], vt = v - (I->w ? I->w[b + k] : 0.0);
+      u[k] = x[b + k] / v;
+      bal += (vt / v) * x[b + k];
+      pos[k] = k;
+    }
+    /* insertion sort of positions by u descending, stable */
+    for (int a = 1; a < K; ++a) {
+      int p = pos[a];
+      int q = a - 1;
+      while (q >= 0 && u[pos[q]] < u[p]) {
+        pos[q + 1] = pos[q];
+        --q;
+      }
+      pos[q + 1] = p;
+    }
+    double* al = alpha + b + l;
+    if (!(lam > 0.0)) {
+      al[0] = 1.0;
+      for (int r = 1; r <= K; ++r) al[r] = 0.0;
+    } else {
+      double u0 = (lam - bal) / vt0;
+      al[0] = ((u0 - (K > 0 ? u[pos[0]] : 0.0)) * vt0) / lam;
+      double D = vt0;
+      for (int r = 1; r <= K; ++r) {
+        int p = pos[r - 1];
+        double vt = I->v[b + p] - (I->w ? I->w[b + p] : 0.0);
+        D += vt;
+        double next = r < K ? u[pos[r]] : 0.0;
+        al[r] = ((u[p] - next) * D) / lam;
+      }
+    }
+    if (order)
+      for (int r = 0; r < K; ++r) order[b + r] = pos[r];
+  }
 }

@@ -487,7 +487,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
     std::frexp(mass > 1.0 ? mass : 1.0, &e2);  // mass < 2^e2
     const int F = 61 - e2;
     spfom::FastPlan plan{};
-    if (ctx->p.path == 0 && F >= 30 && spfom::fast_plan(n, kmax, ctx->sms, &plan)) {
+    if (ctx->p.path == 0 && !ctx->p.track_xbar && F >= 30 && spfom::fast_plan(n, kmax, ctx->sms, &plan)) {
       W.fast = true;
       if (ctx->p.pipeline && !ctx->loading_batch && spfom::pipe_plan(n, ctx->sms, &plan)) {
         // tiles of consecutive segments for the binary64 pipeline
@@ -539,6 +539,16 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   SPFOM_TRY(dalloc(ctx, &W.Ppart, (size_t)W.vec_blocks));
   W.x_cur = nullptr;
   if (ctx->p.batch_frac < 1.0) SPFOM_TRY(dalloc(ctx, &W.x_cur, (size_t)nnz));
+  W.xsum = nullptr;
+  if (ctx->p.track_xbar) {
+    if (ctx->p.precision != 64 || ctx->p.batch_frac < 1.0 || ctx->loading_batch || kmax > 32) {
+      free_instance(ctx);
+      return fail(ctx, SPFOM_ENOTSUP, "track_xbar needs precision 64, batch_frac 1, a single instance and sets "
+                                      "of <= 32 products");
+    }
+    SPFOM_TRY(dalloc(ctx, &W.xsum, (size_t)(nnz > 0 ? nnz : 1)));
+    SPFOM_CUDA(ctx, cudaMemsetAsync(W.xsum, 0, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1), ctx->stream));
+  }
 #undef SPFOM_TRY
   ctx->P = P;
   if (W.v32) {
@@ -1166,4 +1176,59 @@ extern "C" spfom_status spfom_solve_warm(spfom_ctx* ctx, spfom_mlp* net, int64_t
   if (mode_out) *mode_out = mode;
   if (out) out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   return s;
+}
+
+// ---- assortment recovery (Section 4.4) ------------------------------------------
+
+extern "C" spfom_status spfom_xbar(spfom_ctx* ctx, double* out) {
+  if (!ctx || !out) return SPFOM_EINVAL;
+  if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
+  if (!ctx->W.xsum) return fail(ctx, SPFOM_ESTATE, "x-bar is kept only when the ctx is created with track_xbar = 1");
+  if (ctx->host_t <= 0) return fail(ctx, SPFOM_ESTATE, "no iteration since the last reset");
+  SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
+  const long long nnz = ctx->P.nnz;
+  if (nnz == 0) return SPFOM_OK;
+  double* d = nullptr;
+  SPFOM_CUDA(ctx, cudaMalloc(&d, sizeof(double) * (size_t)nnz));
+  cudaError_t e = spfom::launch_xbar(ctx->P, ctx->W, d, ctx->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, d, sizeof(double) * (size_t)nnz, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "x-bar");
+  return SPFOM_OK;
+}
+
+extern "C" spfom_status spfom_recover(spfom_ctx* ctx, const double* x, double* alpha, int32_t* order) {
+  if (!ctx || !alpha) return SPFOM_EINVAL;
+  if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
+  if (ctx->W.W > 32) return fail(ctx, SPFOM_ENOTSUP, "recovery needs sets of <= 32 products");
+  if (!x && (!ctx->W.xsum || ctx->host_t <= 0))
+    return fail(ctx, SPFOM_ESTATE, "no x given and no x-bar kept (track_xbar = 1 and at least one iteration)");
+  SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
+  const Problem& P = ctx->P;
+  const size_t nnz = (size_t)P.nnz, L = (size_t)P.L;
+  if (x)
+    for (size_t p = 0; p < nnz; ++p)
+      if (!is_finite(x[p])) return fail(ctx, SPFOM_EINVAL, "x[%zu] is not finite", p);
+  char* buf = nullptr;
+  const size_t bx = ((nnz * 8 + 255) / 256) * 256, ba = (((nnz + L) * 8 + 255) / 256) * 256;
+  SPFOM_CUDA(ctx, cudaMalloc(&buf, bx + ba + nnz * 4 + 256));
+  double* dx = reinterpret_cast<double*>(buf);
+  double* da = reinterpret_cast<double*>(buf + bx);
+  int* dord = reinterpret_cast<int*>(buf + bx + ba);
+  cudaError_t e = cudaSuccess;
+  if (x) {
+    if (nnz) e = cudaMemcpyAsync(dx, x, sizeof(double) * nnz, cudaMemcpyHostToDevice, ctx->stream);
+  } else {
+    e = spfom::launch_xbar(P, ctx->W, dx, ctx->stream);
+  }
+  if (e == cudaSuccess) e = spfom::launch_recover(P, ctx->W, dx, da, dord, ctx->stream);
+  if (e == cudaSuccess && nnz + L)
+    e = cudaMemcpyAsync(alpha, da, sizeof(double) * (nnz + L), cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess && order && nnz)
+    e = cudaMemcpyAsync(order, dord, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  cudaFree(buf);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "recovery");
+  return SPFOM_OK;
 }

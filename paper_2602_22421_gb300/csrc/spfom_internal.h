@@ -108,6 +108,7 @@ struct Work {
   double* marg_eval;
   double* y_eval;      // dual point handed to spfom_evaluate / spfom_sales_at
   double* s_eval;      // [n] product sales of spfom_sales_at
+  double* xsum;        // [nnz] epoch sums of every segment's response (track_xbar), or null
   double* z_seg;       // [L] per-segment values of spfom_evaluate
   double* zpart;       // per-block partial sums of z (iterate)
   double* zpart_eval;  // per-block partial sums of z (evaluation)
@@ -205,6 +206,11 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
 cudaError_t launch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s);
 cudaError_t launch_evaluate_at(const Problem& P, const Work& Wk, bool want_seg, cudaStream_t s);
 cudaError_t launch_sales_at(const Problem& P, const Work& Wk, cudaStream_t s);
+// assortment recovery (spfom_kernels.cu): x-bar = xsum / count into out [nnz];
+// alpha [nnz + L] and order [nnz] from sales x [nnz] (Lemma recover)
+cudaError_t launch_xbar(const Problem& P, const Work& Wk, double* out, cudaStream_t s);
+cudaError_t launch_recover(const Problem& P, const Work& Wk, const double* x, double* alpha, int* order,
+                           cudaStream_t s);
 // learned warm start (spfom_warm.cu)
 cudaError_t launch_features(const Problem& P, const double* s0, double* d, double* rho, double* totals, float* f,
                             cudaStream_t s);

@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kSegThreads) k_segments(Problem P, const doubl
                                                           double* __restrict__ s, double* __restrict__ x_cur,
                                                           double* __restrict__ z_seg, double* __restrict__ zpart,
                                                           const DevState* st, unsigned long long seed,
-                                                          unsigned long long thr) {
+                                                          unsigned long long thr, double* __restrict__ xsum) {
   if (st && MODE != kEvalSeg && st->converged) return;
   __shared__ double sh[32];
   const int lane = threadIdx.x & (W - 1);
@@ -200,6 +200,11 @@ __global__ void __launch_bounds__(kSegThreads) k_segments(Problem P, const doubl
         }
       } else if (lane < kstar) {
         atomicAdd(s + j_r, x);
+      }
+      if (!SAMPLED && xsum && lane < K) {
+        // epoch sums of the responses (x-bar); the first iteration of an epoch starts them afresh
+        const long long p = b + idx;
+        xsum[p] = st->count == 0 ? x : __dadd_rn(xsum[p], x);
       }
     }
     if (lane == 0) {
@@ -359,13 +364,13 @@ __global__ void __launch_bounds__(1024) k_evaluate_finish(Problem P, Work Wk) {
 
 template <int MODE, bool SAMPLED>
 cudaError_t launch_segments_w(const Problem& P, const Work& Wk, const double* marg, double* zpart,
-                              const DevState* st, const RunConfig& cfg, cudaStream_t s) {
+                              const DevState* st, const RunConfig& cfg, cudaStream_t s, double* xsum = nullptr) {
   const int g = Wk.seg_blocks;
   switch (Wk.W) {
 #define SPFOM_SEG_CASE(WW)                                                                              \
   case WW:                                                                                              \
     k_segments<WW, MODE, SAMPLED><<<g, kSegThreads, 0, s>>>(P, marg, Wk.s, Wk.x_cur, Wk.z_seg, zpart, st, \
-                                                            cfg.seed, cfg.sample_thr);                 \
+                                                            cfg.seed, cfg.sample_thr, xsum);           \
     break;
     SPFOM_SEG_CASE(1)
     SPFOM_SEG_CASE(2)
@@ -439,7 +444,7 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
     e = launch_segment_pass(P, Wk, cfg, Wk.marg, true, s, &zparts);
   } else {
     e = sampled ? launch_segments_w<kIterate, true>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s)
-                : launch_segments_w<kIterate, false>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s);
+                : launch_segments_w<kIterate, false>(P, Wk, Wk.marg, Wk.zpart, Wk.st, cfg, s, Wk.xsum);
   }
   if (seg_end) cudaEventRecord(seg_end, s);
   if (e != cudaSuccess) return e;
@@ -484,6 +489,103 @@ cudaError_t launch_evaluate_at(const Problem& P, const Work& Wk, bool want_seg, 
                            : launch_segments_w<kEvalSum, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, nullptr, cfg, s);
   if (e != cudaSuccess) return e;
   k_evaluate_finish<<<1, 1024, 0, s>>>(P, Wk);
+  return cudaGetLastError();
+}
+
+namespace {
+
+__global__ void k_xbar(long long nnz, const double* __restrict__ xsum, const DevState* st, double* __restrict__ out) {
+  const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (p >= nnz) return;
+  const double cnt = (double)st->count;
+  out[p] = st->count > 0 ? __ddiv_rn(xsum[p], cnt) : CUDART_NAN;
+}
+
+// Lemma recover, one group of W lanes per segment: ranks by u = x / v
+// (bitonic sort on the binary64 values, ties by lower CSR position), the
+// balance row gives x_0, and alpha_r = (u_(r) - u_(r+1)) D_r / lam with D_r the
+// prefix of vt over the ranking started at vt_0.
+template <int W>
+__global__ void __launch_bounds__(kSegThreads) k_recover(Problem P, const double* __restrict__ x,
+                                                         double* __restrict__ alpha, int* __restrict__ order) {
+  const int lane = threadIdx.x & (W - 1);
+  const int gbase = (threadIdx.x & 31) & ~(W - 1);
+  const unsigned mask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << gbase);
+  const long long gpb = kSegThreads / W, ngroups = (long long)gridDim.x * gpb;
+  for (long long l = blockIdx.x * gpb + threadIdx.x / W; l < P.L; l += ngroups) {
+    const long long b = P.seg_ptr[l];
+    const int K = (int)(P.seg_ptr[l + 1] - b);
+    const double lam = P.lam[l], vt0 = P.vt0[l];
+    double u = -CUDART_INF, vt = 0.0, bal = 0.0;
+    if (lane < K) {
+      const double v = P.v[b + lane], xv = x[b + lane];
+      vt = P.vt[b + lane];
+      u = __ddiv_rn(xv, v);
+      bal = __dmul_rn(__ddiv_rn(vt, v), xv);
+    }
+#pragma unroll
+    for (int o = W >> 1; o > 0; o >>= 1) bal = __dadd_rn(bal, __shfl_xor_sync(mask, bal, o, W));
+    int idx = lane;
+#pragma unroll
+    for (int k = 2; k <= W; k <<= 1)
+#pragma unroll
+      for (int d = k >> 1; d > 0; d >>= 1) {
+        const double ou = __shfl_xor_sync(mask, u, d, W);
+        const int oi = __shfl_xor_sync(mask, idx, d, W);
+        const bool other_first = (ou > u) || (ou == u && oi < idx);
+        if (((lane & k) == 0) == ((lane & d) == 0) ? other_first : !other_first) {
+          u = ou;
+          idx = oi;
+        }
+      }
+    const double vt_r = __shfl_sync(mask, vt, idx, W);
+    double D = lane < K ? vt_r : 0.0;
+#pragma unroll
+    for (int d = 1; d < W; d <<= 1) {
+      const double t = __shfl_up_sync(mask, D, d, W);
+      if (lane >= d) D = __dadd_rn(D, t);
+    }
+    D = __dadd_rn(vt0, D);
+    const double nxt = __shfl_down_sync(mask, u, 1, W);
+    const double u1 = __shfl_sync(mask, u, 0, W);
+    double* al = alpha + b + l;
+    if (!(lam > 0.0)) {
+      if (lane == 0) al[0] = 1.0;
+      if (lane < K) al[lane + 1] = 0.0;
+    } else {
+      if (lane == 0) {
+        const double u0 = __ddiv_rn(__dsub_rn(lam, bal), vt0);
+        al[0] = __ddiv_rn(__dmul_rn(__dsub_rn(u0, K > 0 ? u1 : 0.0), vt0), lam);
+      }
+      if (lane < K) {
+        const double next = lane + 1 < K ? nxt : 0.0;
+        al[lane + 1] = __ddiv_rn(__dmul_rn(__dsub_rn(u, next), D), lam);
+      }
+    }
+    if (order && lane < K) order[b + lane] = idx;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_xbar(const Problem& P, const Work& Wk, double* out, cudaStream_t s) {
+  if (!Wk.xsum) return cudaErrorInvalidValue;
+  if (P.nnz > 0) k_xbar<<<(unsigned)((P.nnz + 255) / 256), 256, 0, s>>>(P.nnz, Wk.xsum, Wk.st, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recover(const Problem& P, const Work& Wk, const double* x, double* alpha, int* order,
+                           cudaStream_t s) {
+  const int g = Wk.seg_blocks;
+  switch (Wk.W) {
+    case 1: k_recover<1><<<g, kSegThreads, 0, s>>>(P, x, alpha, order); break;
+    case 2: k_recover<2><<<g, kSegThreads, 0, s>>>(P, x, alpha, order); break;
+    case 4: k_recover<4><<<g, kSegThreads, 0, s>>>(P, x, alpha, order); break;
+    case 8: k_recover<8><<<g, kSegThreads, 0, s>>>(P, x, alpha, order); break;
+    case 16: k_recover<16><<<g, kSegThreads, 0, s>>>(P, x, alpha, order); break;
+    case 32: k_recover<32><<<g, kSegThreads, 0, s>>>(P, x, alpha, order); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

@@ -26,7 +26,7 @@ EXPORTS = ("spfom_default_params", "spfom_create", "spfom_load_instance", "spfom
            "spfom_batch_stats", "spfom_update", "spfom_sales_at", "spfom_autotune",
            "spfom_mlp_create", "spfom_mlp_destroy", "spfom_mlp_set_params", "spfom_mlp_get_params",
            "spfom_mlp_get_grads", "spfom_mlp_forward", "spfom_mlp_loss_grad", "spfom_mlp_adam",
-           "spfom_mlp_train_step", "spfom_features", "spfom_solve_warm")
+           "spfom_mlp_train_step", "spfom_features", "spfom_solve_warm", "spfom_xbar", "spfom_recover")
 
 MLP_FEATURES, MLP_HIDDEN = 16, 256
 MLP_PARAMS = 256 * 16 + 256 + 256 * 256 + 256 + 256 + 1
@@ -43,7 +43,7 @@ class Params(C.Structure):
                 ("restart_tau_decay", C.c_double), ("kkt_tol", C.c_double), ("max_iters", C.c_int64),
                 ("device", C.c_int32), ("profile", C.c_int32), ("path", C.c_int32), ("pipeline", C.c_int32),
                 ("graphs", C.c_int32),
-                ("polish", C.c_int32),
+                ("polish", C.c_int32), ("track_xbar", C.c_int32),
                 ("stream", C.c_void_p)]
 
 
@@ -132,6 +132,10 @@ def lib():
         h.spfom_mlp_train_step.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float, _f64p,
                                            C.c_void_p]
         h.spfom_features.argtypes = [C.c_void_p, C.c_void_p]
+        h.spfom_xbar.argtypes = [C.c_void_p, _f64p]
+        h.spfom_recover.argtypes = [C.c_void_p, _f64p, _f64p, _i32p]
+        h.spfom_xbar.restype = C.c_int
+        h.spfom_recover.restype = C.c_int
         h.spfom_solve_warm.argtypes = [C.c_void_p, C.c_void_p, C.c_int64, P(Stats), P(C.c_int32)]
         for f in ("spfom_mlp_create", "spfom_mlp_set_params", "spfom_mlp_get_params", "spfom_mlp_get_grads",
                   "spfom_mlp_forward", "spfom_mlp_loss_grad", "spfom_mlp_adam", "spfom_mlp_train_step",
@@ -209,7 +213,7 @@ class Solver:
         self._check(self._lib.spfom_create(C.byref(p), C.byref(h)), ctx=None)
         self._h = h
         self.params = p
-        self.n = self.m = self.L = 0
+        self.n = self.m = self.L = self.nnz = 0
         if inst is not None:
             self.load(inst)
 
@@ -225,6 +229,7 @@ class Solver:
         arrs = inst if isinstance(inst, InstanceArrays) else InstanceArrays(inst)
         self._check(self._lib.spfom_load_instance(self._h, C.byref(arrs.c)))
         self.n, self.m, self.L = arrs.c.n, arrs.c.m, arrs.c.L
+        self.nnz = int(arrs.keep["seg_ptr"][-1])
         return self
 
     def load_batch(self, insts):
@@ -236,6 +241,7 @@ class Solver:
         self.n = sum(a.c.n for a in arrs)
         self.m = sum(a.c.m for a in arrs)
         self.L = sum(a.c.L for a in arrs)
+        self.nnz = sum(int(a.keep["seg_ptr"][-1]) for a in arrs)
         self.batch_sizes = [(a.c.n, a.c.m, a.c.L) for a in arrs]
         return self
 
@@ -260,6 +266,21 @@ class Solver:
         ch = C.c_int32(0)
         self._check(self._lib.spfom_autotune(self._h, int(iters), C.byref(ch)))
         return ch.value
+
+    def xbar(self) -> np.ndarray:
+        """Epoch-averaged responses per nonzero (spfom_xbar; needs track_xbar=1)."""
+        out = np.empty(max(self.nnz, 1))
+        self._check(self._lib.spfom_xbar(self._h, _p(out, _f64p)))
+        return out[:self.nnz]
+
+    def recover(self, x=None):
+        """Assortment probabilities (spfom_recover): (alpha [nnz + L], order [nnz]);
+        x None recovers from x-bar."""
+        alpha = np.empty(max(self.nnz + self.L, 1))
+        order = np.empty(max(self.nnz, 1), np.int32)
+        xc = None if x is None else np.ascontiguousarray(x, np.float64)
+        self._check(self._lib.spfom_recover(self._h, _p(xc, _f64p), _p(alpha, _f64p), _p(order, _i32p)))
+        return alpha[:self.nnz + self.L], order[:self.nnz]
 
     def features(self, out=None):
         """Per-resource warm-start features (spfom_features) as a CUDA torch

@@ -52,7 +52,7 @@ def sales_of(inst, l: int, S: np.ndarray) -> np.ndarray:
     return inst.lam[l] * gam_prob(v, w, inst.v0[l], S)
 
 
-def sblp_highs(inst):
+def sblp_highs(inst, return_x: bool = False):
     """GAM sales-based LP: max sum r_j x_lj s.t. A x <= c; x_l0 + sum (vt/v) x_lj = lam_l;
     x_lj / v_lj <= x_l0 / vt_l0; x >= 0. Returns (OPT, capacity duals y*)."""
     from scipy.optimize import linprog
@@ -86,6 +86,8 @@ def sblp_highs(inst):
     A_eq = coo_matrix((ev, (er, ec)), shape=(L, nv)).tocsr()
     res = linprog(cost, A_ub=A_ub, b_ub=b_ub, A_eq=A_eq, b_eq=inst.lam, bounds=(0, None), method="highs")
     assert res.status == 0, res.message
+    if return_x:
+        return -res.fun, -res.ineqlin.marginals[:m], res.x[:nnz]
     return -res.fun, -res.ineqlin.marginals[:m]
 
 

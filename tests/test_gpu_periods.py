@@ -1,0 +1,55 @@
+"""Batched multi-period re-solves (paper_2602_22421_gb300.periods) against
+one-at-a-time plain solves of the same problems (needs a GPU).
+
+Every (period, instance) problem of the batched binary32 run, warm-started
+from the previous period's bid prices, must reach KKT <= 1e-4 and the dual
+objective the plain binary64 method reaches from y = 0 on the same capacities
+and rates. Two points with KKT <= 1e-4 each lie within about 1e-4 of the
+optimum, so their objectives are compared at 3e-4 relative.
+"""
+import numpy as np
+import pytest
+
+from instances import batch_base, period_rates
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def small_family(count=6):
+    out = []
+    for k in range(count):
+        inst = batch_base(11, k)
+        if inst.L > 20_000:  # keep the test quick: same distributions, fewer segments
+            from instances import make_instance
+            rng = np.random.default_rng([11, k, 1])
+            inst = make_instance(n=inst.n, m=inst.m, L=int(rng.integers(1000, 20_000)), kmin=3, kmax=20,
+                                 tightness=0.6, seed=int(rng.integers(1 << 40)))
+        out.append(inst)
+    return out
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_batched_periods_match_sequential_plain_solves(precision):
+    from paper_2602_22421_gb300 import periods as PR
+    insts = small_family()
+    rho = period_rates(11, len(insts), 3)
+    summary, path, per = PR.run_batched(insts, rho, periods=3, precision=precision)
+    assert summary["autotune_choice"] in (1, 2)
+    assert all(r["converged"] == 1 for r in summary["records"])
+    for c_k, lam_k in path:
+        assert all((c >= 0).all() for c in c_k)
+    # inventory is consumed: later periods never get more capacity in total than the first
+    tot = [sum(float(c.sum()) for c in c_k) for c_k, _ in path]
+    assert tot[-1] <= tot[0] * (1 + 1e-12)
+    seq = PR.run_sequential(insts, path)
+    for r in seq:
+        b, k = r["instance"], r["period"]
+        st = per[k][b]
+        assert r["converged"] == 1 and st["converged"] == 1 and st["kkt"] <= 1e-4
+        assert st["dual_avg"] == pytest.approx(r["dual"], rel=3e-4), (b, k)
