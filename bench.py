@@ -51,6 +51,17 @@ def parse():
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-huge", action="store_true", help="skip the 1e7-segment instance")
+    ap.add_argument("--huge-segments", type=int, default=10_000_000)
+    ap.add_argument("--huge-steps", type=int, default=6)
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched multi-period re-solves")
+    ap.add_argument("--batched-count", type=int, default=256)
+    ap.add_argument("--periods", type=int, default=16)
+    ap.add_argument("--seq-sample", type=int, default=16,
+                    help="instances of the batched family re-solved one at a time for the plain reference "
+                         "(0 = all)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned warm start")
+    ap.add_argument("--learned-test", type=int, default=32)
     return ap.parse_args()
 
 
@@ -223,10 +234,11 @@ def run_gpu(args):
     ips = args.iters_per_step
     stream = torch.cuda.Stream()  # a real stream handle: the ctx runs on it, the events bracket it
 
-    def measure(precision, with_clocks):
+    def measure(precision, with_clocks, path=0, solve=True):
         """Timed iterations (kkt_tol = 0: nothing is skipped), then a profiled
         pass for the segment kernel's roofline, then a solve to KKT <= 1e-4."""
-        s = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, precision=precision)
+        s = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, precision=precision, path=path)
+        tiling = s.autotune(ips) if path == 0 else 0  # segment-kernel tiling for this instance
         s.step(args.warmup * ips)
         barrier()
         clk = Clocks(local) if (rank == 0 and with_clocks) else None
@@ -240,9 +252,10 @@ def run_gpu(args):
         ms = allmax(e0.elapsed_time(e1))
         s.close()
         out = {"value": ws * args.steps * ips / (ms * 1e-3), "ms": ms, "launches": st["kernel_launches"],
-               "clocks": clocks, "iter_precision": st["iter_precision"]}
+               "clocks": clocks, "iter_precision": st["iter_precision"], "tiling": tiling}
         if rank == 0:
-            sp = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, profile=1, precision=precision)
+            sp = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, profile=1, precision=precision,
+                        path=path, tiling=tiling)
             sp.step(2 * ips)
             pst = sp.step(min(args.steps, 10) * ips)
             sp.close()
@@ -252,8 +265,12 @@ def run_gpu(args):
                 kname, ksrc = "k_seg_f32", "spfom_segments_fast.cu"
             else:
                 alg = BYTES_PER_NNZ * inst.nnz + BYTES_PER_SEGMENT * inst.L
-                kname, ksrc = ("k_seg_fast", "spfom_segments_fast.cu") if pst["fast_path"] else \
-                    ("k_segments", "spfom_kernels.cu")
+                if not pst["fast_path"]:
+                    kname, ksrc = "k_segments", "spfom_kernels.cu"
+                elif path == 2:
+                    kname, ksrc = "k_seg_fast", "spfom_segments_fast.cu"
+                else:
+                    kname, ksrc = "k_seg_dd", "spfom_segments_dd.cu"
             peak, src = measured_peaks()
             achieved = alg / per_launch / 1e9
             traffic, cap = kernel_traffic(kname, ksrc, inst.nnz)
@@ -263,9 +280,9 @@ def run_gpu(args):
                                "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch * 1e3,
                                "peak_source": f"{src} hbm_gbs", "traffic_note": cap,
                                "binary64_redo_fraction": pst["fallback_segments"] / solves}
-        if not args.no_solve:
+        if solve and not args.no_solve:
             sv = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=1e-4, max_iters=20000,
-                        precision=precision)
+                        precision=precision, path=path, tiling=tiling)
             barrier()
             w0 = time.perf_counter()
             sst = sv.solve()
@@ -279,12 +296,16 @@ def run_gpu(args):
 
     m64 = measure(64, True)
     m32 = measure(32, False)
+    m64b = measure(64, False, path=2, solve=False)
     value, ms, launches, clocks = m64["value"], m64["ms"], m64["launches"], m64["clocks"]
     roof = m64.get("roofline")
     ttk = m64.get("ttk")
-    fp32 = {"value": m32["value"], "unit": "iters/s", "ms_per_step": m32["ms"] / args.steps,
+    fp32 = {"value": m32["value"], "unit": "iters/s", "ms_per_step": m32["ms"] / args.steps, "tiling": m32["tiling"],
             "roofline": m32.get("roofline"), "time_to_kkt_1e-4": m32.get("ttk"), "gpu_launches": m32["launches"],
             "dtype": "f32 segment solves, f64 dual step / residuals / evaluations"}
+    f64_sums = {"value": m64b["value"], "unit": "iters/s", "ms_per_step": m64b["ms"] / args.steps,
+                "roofline": m64b.get("roofline"), "gpu_launches": m64b["launches"],
+                "dtype": "f64: certified decisions, binary64 value sums (path 2)"}
     if ttk and m32.get("ttk"):
         fp32["objective_rel_diff_vs_f64"] = abs(m32["ttk"]["dual_obj"] / ttk["dual_obj"] - 1)
         fp32["speedup_time_to_kkt_vs_f64"] = ttk["seconds_device"] / m32["ttk"]["seconds_device"]
@@ -312,16 +333,170 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(inst, args.cpu_seconds)
+    legs = {}
+    if rank == 0:
+        for name, skip, fn in (("huge", args.no_huge, lambda: huge_leg(args, stream, local)),
+                               ("batched", args.no_batched, lambda: batched_leg(args, local)),
+                               ("learned", args.no_learned, lambda: learned_leg(args, local))):
+            if skip:
+                continue
+            t0 = time.perf_counter()
+            legs[name] = fn()
+            legs[name]["leg_seconds"] = time.perf_counter() - t0
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+               "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "dtype_note": "binary64 inputs, margins, dual step, averages and KKT; certified segment decisions "
+                             "(exact); chosen-assortment values in double-binary32 (48-bit) arithmetic, "
+                             "about 1e-13 relative to binary64",
+               "data": "synthetic (seeded generator)",
                "config": config_of(inst, args), "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-               "roofline": roof, "cpu_baseline": cpu, "time_to_kkt_1e-4": ttk, "fp32_bulk": fp32}
+               "roofline": roof, "cpu_baseline": cpu, "time_to_kkt_1e-4": ttk, "fp32_bulk": fp32,
+               "f64_binary64_value_sums": f64_sums, "tiling": m64["tiling"]}
+        out.update(legs)
         print(json.dumps(out), flush=True)
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def roofline_of(s_prof, inst, precision, ips, steps):
+    """Segment-kernel roofline of a profiled solver (the per-launch time of the
+    iterate pass from its CUDA event pairs)."""
+    pst = s_prof.step(steps * ips)
+    per_launch = pst["seg_kernel_seconds"] / max(1, pst["seg_kernel_launches"])
+    if precision == 32:
+        alg = BYTES_PER_NNZ_F32 * inst.nnz + BYTES_PER_SEGMENT_F32 * inst.L
+        kname = "k_seg_f32"
+    else:
+        alg = BYTES_PER_NNZ * inst.nnz + BYTES_PER_SEGMENT * inst.L
+        kname = "k_seg_dd" if pst["fast_path"] else "k_segments"
+    peak, src = measured_peaks()
+    achieved = alg / per_launch / 1e9
+    return {"bound": "hbm", "kernel": kname + " (iterate)", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch * 1e3,
+            "peak_source": f"{src} hbm_gbs", "traffic": None,
+            "binary64_redo_fraction": pst["fallback_segments"] / (steps * ips * inst.L)}
+
+
+def huge_leg(args, stream, local):
+    """The 1e7-segment GAM instance (|C_l| ~ U{10..30}, ~2e8 nonzeros, c = 0.4 x
+    demand): iterations/s and the segment kernel's roofline in binary64 and in
+    the binary32 bulk mode, and the binary32 solve to KKT <= 1e-4 (with its
+    binary64 residuals and polish)."""
+    import torch
+    from instances import huge_gam
+    from paper_2602_22421_gb300 import Solver
+    t0 = time.perf_counter()
+    inst = huge_gam(2, L=args.huge_segments, workers=12)
+    gen_s = time.perf_counter() - t0
+    out = {"workload": f"huge GAM instance: n={inst.n}, m={inst.m}, L={inst.L}, nnz={inst.nnz}, "
+                       "|C_l|~U{10..30}, c = 0.4 x demand", "nnz": inst.nnz, "generate_seconds": gen_s}
+    ips = args.iters_per_step
+    for precision in (64, 32):
+        t0 = time.perf_counter()
+        s = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, precision=precision)
+        load_s = time.perf_counter() - t0
+        tiling = s.autotune(16)
+        s.step(2 * ips)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(args.huge_steps * ips)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        s.close()
+        sp = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, profile=1, precision=precision,
+                    tiling=tiling)
+        sp.step(ips)
+        roof = roofline_of(sp, inst, precision, ips, 2)
+        sp.close()
+        out[f"f{precision}"] = {"value": args.huge_steps * ips / (ms * 1e-3), "unit": "iters/s", "tiling": tiling,
+                                "ms_per_iter": ms / (args.huge_steps * ips), "load_seconds": load_s,
+                                "roofline": roof}
+    sv = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=1e-4, max_iters=20000, precision=32,
+                tiling=out["f32"]["tiling"])
+    w0 = time.perf_counter()
+    st = sv.solve()
+    out["f32"]["time_to_kkt_1e-4"] = {"seconds_wall": time.perf_counter() - w0, "seconds_device": st["seconds"],
+                                      "iterations": st["iters"], "converged": bool(st["converged"]),
+                                      "kkt": st["kkt"], "dual_obj": st["dual_avg"],
+                                      "final_iter_precision": st["iter_precision"]}
+    sv.close()
+    # the binary64 time to 1e-4 at the measured iteration rate (same iteration count as the binary32 solve)
+    out["f64"]["time_to_kkt_1e-4_at_f32_iterations_s"] = st["iters"] * out["f64"]["ms_per_iter"] * 1e-3
+    return out
+
+
+def batched_leg(args, local):
+    """Batched multi-period re-solves (count base instances of uneven size, 16
+    periods each): all instances of a period in one batch, binary32 bulk,
+    autotuned segment kernel, graph-replayed evaluation periods, warm-started
+    from the previous period's bid prices -- against the plain binary64 method
+    re-solving the same problems one at a time from y = 0 (on a seeded sample
+    of the instances when seq-sample > 0, scaled to all of them)."""
+    from concurrent.futures import ProcessPoolExecutor
+    from multiprocessing import get_context
+
+    import numpy as np
+    from instances import batch_base, period_rates
+    from paper_2602_22421_gb300 import periods as PR
+    count = args.batched_count
+    t0 = time.perf_counter()
+    with ProcessPoolExecutor(12, mp_context=get_context("spawn")) as pool:
+        insts = list(pool.map(batch_base, [4] * count, range(count)))
+    gen_s = time.perf_counter() - t0
+    rho = period_rates(4, count, args.periods)
+    prm = dict(restart_tau_balance=0.5, max_iters=20000)
+    summary, path, per = PR.run_batched(insts, rho, periods=args.periods, precision=32, **prm)
+    batched_s = sum(r["seconds"] for r in summary["records"])
+    if args.seq_sample and args.seq_sample < count:
+        which = sorted(np.random.default_rng(7).choice(count, args.seq_sample, replace=False).tolist())
+    else:
+        which = list(range(count))
+    seq = PR.run_sequential(insts, path, which=which, precision=64, **prm)
+    seq_s = sum(r["seconds"] for r in seq)
+    nnz_all = sum(i.nnz for i in insts)
+    nnz_sample = sum(insts[b].nnz for b in which)
+    scale = len(insts) / len(which)
+    rel = [abs(per[r["period"]][r["instance"]]["dual_avg"] / r["dual"] - 1) for r in seq]
+    return {"workload": f"{count} GAM instances, n~U{{200..5000}}, m=ceil(n/5), L=10^U(3,5), |C_l|~U{{3..20}}, "
+                        f"{args.periods} periods (capacity = remaining inventory / remaining periods, "
+                        f"lambda x U(0.5,1.5))",
+            "solver_params": prm,
+            "instances": count, "periods": args.periods, "nnz_total": nnz_all, "generate_seconds": gen_s,
+            "batched_seconds": batched_s, "batched_load_seconds": summary["load_seconds"],
+            "autotune_choice": summary["autotune_choice"],
+            "periods_converged": sum(r["converged"] for r in summary["records"]),
+            "batched_iterations_per_period": [r["iters"] for r in summary["records"]],
+            "sequential_plain_seconds": seq_s * scale, "sequential_sample": len(which),
+            "sequential_scale": scale, "sequential_sample_nnz_share": nnz_sample / nnz_all,
+            "speedup_vs_sequential_plain": seq_s * scale / batched_s,
+            "max_objective_rel_diff_vs_plain": max(rel),
+            "sequential_all_converged": all(r["converged"] for r in seq)}
+
+
+def learned_leg(args, local):
+    """Learned warm start: the committed network, on held-out instances of its
+    training family (n=2000, m=400, L=10^U(4,4.7), |C_l|~U{10..30}, c=0.4 x
+    demand): cold and warm solves to KKT <= 1e-4 per instance, wall clock."""
+    from concurrent.futures import ProcessPoolExecutor
+    from multiprocessing import get_context
+
+    from paper_2602_22421_gb300 import warmstart as W
+    if not os.path.exists(W.DEFAULT_WEIGHTS):
+        return {"unavailable": f"no trained network at {os.path.relpath(W.DEFAULT_WEIGHTS, ROOT)}"}
+    with ProcessPoolExecutor(8, mp_context=get_context("spawn")) as pool:
+        test = W.instances(W.TEST_SEED, range(args.learned_test), pool=pool)
+    net = W.load()
+    recs = W.evaluate(net, test)
+    net.close()
+    out = W.summarize(recs)
+    out["workload"] = ("held-out warm_family(seed 6) instances: n=2000, m=400, L=10^U(4,4.7), |C_l|~U{10..30}, "
+                       "c=0.4 x demand")
+    return out
 
 
 def sub_instance(inst, Ls):

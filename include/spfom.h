@@ -69,15 +69,24 @@ typedef struct {
   double restart_beta;       /* 0.2: restart when KKT <= beta * KKT at the last restart */
   double restart_artificial; /* 0.36: or when the epoch holds this fraction of all iterations */
   double restart_tau_decay;  /* 1.0: tau <- tau * decay at each restart */
+  double restart_tau_balance;/* 0 (default): off. b in (0, 1]: at a restart forced by the epoch-
+                                length rule (the KKT did not drop by restart_beta), also
+                                tau <- tau * clamp(sqrt(pinf / gap), b, 1 / b): a constant step
+                                leaves an O(tau) duality gap on instances with few segments, and
+                                this balances the gap against the infeasibility (solver addition) */
   double kkt_tol;            /* 1e-4: spfom_solve stops when KKT <= kkt_tol */
   int64_t max_iters;         /* 100000: spfom_solve iteration cap */
   int32_t device;            /* CUDA device ordinal (0) */
   int32_t profile;           /* 0; nonzero: time every segment-kernel launch of spfom_step with
                                 a CUDA event pair (spfom_stats.seg_kernel_seconds) */
   int32_t path;              /* 0 (default): the certified-decision segment kernel whenever the
-                                instance allows it (sets of <= 32 products, full batch), else the
-                                general kernel; 1: always the general kernel */
-  int32_t pipeline;          /* 0 (default): the binary64 certified pass reads with plain loads;
+                                instance allows it (sets of <= 32 products, full batch), with the
+                                values of the chosen assortments in double-binary32 arithmetic
+                                (binary64 inputs held as (hi, lo) binary32 pairs, about 1e-13
+                                relative; binary64 for uncertified segments), else the general
+                                kernel; 1: always the general kernel; 2: the certified-decision
+                                kernel with binary64 value sums */
+  int32_t pipeline;          /* path 2 only. 0 (default): the binary64 certified pass reads with plain loads;
                                 1: it streams tiles of segments into shared memory through a
                                 warp-specialised bulk-copy (TMA) pipeline when shared memory allows
                                 (slower on the mid instance: the stages crowd the L1 cache that
@@ -92,6 +101,9 @@ typedef struct {
                                 response since the last restart (x-bar of spfom_xbar, 8 B per
                                 nonzero read and written each iteration); needs precision 64,
                                 batch_frac 1 and a single instance, and runs the general kernel */
+  int32_t tiling;            /* 0 (default): tiling 1 of the active segment pass until
+                                spfom_autotune picks one; 1..3: that tiling (see spfom_autotune),
+                                ENOTSUP at load when the instance does not allow it */
   void* stream;              /* cudaStream_t to run on; NULL (default): the ctx creates one */
 } spfom_params;
 
@@ -239,12 +251,14 @@ spfom_status spfom_update(spfom_ctx* ctx, const double* c, const double* lam);
 spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out);
 
 /* Segment-to-warp tiling autotuner (no counterpart in the paper). Times each
- * candidate segment kernel of the loaded instance or batch -- for the
- * precision-32 pass: 1 = plain loads with 4 lanes x 4 products per segment,
- * 2 = tiles staged by bulk copies with 8 products per lane -- for `iters`
- * iterations each from the current duals, keeps the fastest, and restarts the
- * iteration from those duals. *choice_out (or NULL) gets the choice; with a
- * single candidate it just reports it. */
+ * candidate segment kernel of the loaded instance or batch for `iters`
+ * iterations from the current duals, keeps the fastest, and restarts the
+ * iteration from those duals. Candidates: precision 32: 1 = plain loads with
+ * 4 products per lane, 2 = tiles staged by bulk copies with 8 products per
+ * lane (when shared memory allows), 3 = plain loads with 8 products per lane;
+ * precision 64 (path 0): 1 = 8 products per lane at two 512-thread blocks per
+ * SM, 2 = 8 per lane at three blocks per SM, 3 = 4 per lane at three blocks
+ * per SM. *choice_out (or NULL) gets the choice (1 when there is none). */
 spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* choice_out);
 
 /* ---- Recovering assortments (Section 4.4) ----------------------------------

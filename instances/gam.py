@@ -135,14 +135,30 @@ def full_offer_demand(inst: Instance) -> np.ndarray:
     return np.bincount(inst.a_idx, weights=a_val * sales[prod_of], minlength=inst.m)
 
 
+def _segment_chunk(args):
+    """Draws of one chunk of segments: product ids, v, theta, v0, lambda, from
+    the chunk's own stream (seed, 1, chunk index)."""
+    seed, ci, n, Kc, gam, v_dist, theta_dist, v0_dist, lam_dist = args
+    rng = np.random.default_rng([seed, 1, ci])
+    prod = _distinct_sorted(rng, n, Kc)
+    v = _draw(rng, v_dist, int(Kc.sum()))
+    w = np.repeat(_draw(rng, theta_dist, Kc.size), Kc) * v if gam else None
+    v0 = _draw(rng, v0_dist, Kc.size)
+    lam = _draw(rng, lam_dist, Kc.size)
+    return prod, v, w, v0, lam
+
+
 def make_instance(*, n: int, m: int, L: int, kmin: int, kmax: int, res_min: int = 1, res_max: int = 3,
                   gam: bool = True, v_dist=("uniform", 0.1, 1.0), theta_dist=("uniform", 0.0, 1.0),
                   v0_dist=("uniform", 0.5, 2.0), r_dist=("lognormal", 3.0, 0.5), lam_dist=("exp", 1.0),
                   tightness: Optional[float] = 0.6, c_dist=None, identity_A: bool = False,
-                  seed: int = 1, name: str = "") -> Instance:
-    """Draw one instance. Order of draws: incidence, prices, set sizes, then per
-    chunk of segments: product ids, v, theta, v0, lambda. ``tightness=None``
-    makes capacities non-binding (1e30); ``c_dist`` draws capacities directly."""
+                  seed: int = 1, name: str = "", workers: int = 1) -> Instance:
+    """Draw one instance. The stream of `seed` draws the incidence, the prices,
+    the set sizes and (last) capacities drawn directly; each chunk of 2^20
+    segments draws its product ids, v, theta, v0 and lambda from its own stream
+    (seed, 1, chunk), so chunks can be drawn in parallel (`workers` processes)
+    with identical results. ``tightness=None`` makes capacities non-binding
+    (1e30); ``c_dist`` draws capacities directly."""
     rng = np.random.default_rng(seed)
     # incidence: product j uses U{res_min..res_max} distinct resources
     if identity_A:
@@ -165,17 +181,25 @@ def make_instance(*, n: int, m: int, L: int, kmin: int, kmax: int, res_min: int 
     w = np.empty(nnz) if gam else None
     v0 = np.empty(L)
     lam = np.empty(L)
-    for s in range(0, L, _CHUNK):
+    starts = list(range(0, L, _CHUNK))
+    jobs = [(seed, ci, n, K[s:min(L, s + _CHUNK)], gam, v_dist, theta_dist, v0_dist, lam_dist)
+            for ci, s in enumerate(starts)]
+    if workers > 1 and len(jobs) > 1:
+        from concurrent.futures import ProcessPoolExecutor
+        from multiprocessing import get_context
+        with ProcessPoolExecutor(min(workers, len(jobs)), mp_context=get_context("spawn")) as pool:
+            parts = list(pool.map(_segment_chunk, jobs))
+    else:
+        parts = [_segment_chunk(j) for j in jobs]
+    for s, (pp, vv, ww, vv0, ll) in zip(starts, parts):
         e = min(L, s + _CHUNK)
         b0, b1 = int(seg_ptr[s]), int(seg_ptr[e])
-        Kc = K[s:e]
-        seg_prod[b0:b1] = _distinct_sorted(rng, n, Kc)
-        v[b0:b1] = _draw(rng, v_dist, b1 - b0)
+        seg_prod[b0:b1] = pp
+        v[b0:b1] = vv
         if gam:
-            theta = _draw(rng, theta_dist, e - s)
-            w[b0:b1] = np.repeat(theta, Kc) * v[b0:b1]
-        v0[s:e] = _draw(rng, v0_dist, e - s)
-        lam[s:e] = _draw(rng, lam_dist, e - s)
+            w[b0:b1] = ww
+        v0[s:e] = vv0
+        lam[s:e] = ll
     inst = Instance(n=n, m=m, L=L, r=r, c=np.zeros(m), a_ptr=a_ptr, a_idx=a_idx, a_val=None,
                     seg_ptr=seg_ptr, seg_prod=seg_prod, v=v, w=w, lam=lam, v0=v0, name=name)
     if c_dist is not None:
@@ -207,11 +231,12 @@ def mid_gam(seed: int = 1, L: int = 1_000_000, n: int = 10_000, m: int = 2000, k
                          tightness=tightness, seed=seed, name=f"mid_gam(n={n},m={m},L={L},K={kmin}..{kmax},seed={seed})")
 
 
-def huge_gam(seed: int = 2, L: int = 10_000_000, n: int = 100_000, m: int = 20_000) -> Instance:
+def huge_gam(seed: int = 2, L: int = 10_000_000, n: int = 100_000, m: int = 20_000, workers: int = 1) -> Instance:
     """Huge GAM instance: 1e5 products, 2e4 resources, 1e7 segments,
-    |C_l|~U{10..30}, the mid instance's distributions, c = 0.4 x demand."""
+    |C_l|~U{10..30}, the mid instance's distributions, c = 0.4 x demand
+    (chunks drawn by `workers` processes; the result does not depend on it)."""
     return make_instance(n=n, m=m, L=L, kmin=10, kmax=30, res_min=1, res_max=3, gam=True, tightness=0.4,
-                         seed=seed, name=f"huge_gam(n={n},m={m},L={L},seed={seed})")
+                         seed=seed, name=f"huge_gam(n={n},m={m},L={L},seed={seed})", workers=workers)
 
 
 def paper_shaped(seed: int = 3, L: int = 100_000, n: int = 100) -> Instance:

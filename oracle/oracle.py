@@ -49,7 +49,8 @@ class _Inst(C.Structure):
 class _Params(C.Structure):
     _fields_ = [("tau", C.c_double), ("tau0", C.c_double), ("mu", C.c_double), ("batch_frac", C.c_double),
                 ("seed", C.c_uint64), ("eval_every", C.c_int64), ("restart_beta", C.c_double),
-                ("restart_artificial", C.c_double), ("restart_tau_decay", C.c_double), ("kkt_tol", C.c_double)]
+                ("restart_artificial", C.c_double), ("restart_tau_decay", C.c_double),
+                ("restart_tau_balance", C.c_double), ("kkt_tol", C.c_double)]
 
 
 class _State(C.Structure):
@@ -108,11 +109,13 @@ class Params:
     restart_beta: float = 0.2
     restart_artificial: float = 0.36
     restart_tau_decay: float = 1.0
+    restart_tau_balance: float = 0.0
     kkt_tol: float = 1e-4
 
     def _c(self) -> _Params:
         return _Params(self.tau, self.tau0, self.mu, self.batch_frac, self.seed, self.eval_every,
-                       self.restart_beta, self.restart_artificial, self.restart_tau_decay, self.kkt_tol)
+                       self.restart_beta, self.restart_artificial, self.restart_tau_decay,
+                       self.restart_tau_balance, self.kkt_tol)
 
 
 class Oracle:

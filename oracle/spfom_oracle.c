@@ -73,6 +73,8 @@ typedef struct {
   double restart_beta;  /* restart when KKT(avg) <= beta * KKT(anchor) (solver addition) */
   double restart_artificial; /* or when the epoch holds >= this fraction of all iterations */
   double restart_tau_decay;  /* tau <- tau * decay at each restart (1 = constant step) */
+  double restart_tau_balance;/* > 0: restarts forced by the epoch length also scale tau by
+                                clamp(sqrt(pinf / gap), b, 1 / b) (solver addition) */
   double kkt_tol;
 } orc_params;
 
@@ -391,7 +393,9 @@ void orc_state_init(const orc_instance* I, const orc_params* P, orc_state* S) {
  * Restart (solver addition): when KKT <= beta * KKT at the last restart, or the
  * epoch holds at least restart_artificial of all iterations: y <- ybar, the
  * epoch sums are cleared, mu is halved (mu continuation, Theorem 1) and tau is
- * multiplied by restart_tau_decay (a restarted subgradient schedule). */
+ * multiplied by restart_tau_decay (a restarted subgradient schedule); a restart
+ * forced by the epoch length (no progress) also multiplies tau by
+ * clamp(sqrt(pinf / gap), b, 1 / b) when restart_tau_balance = b > 0. */
 static void evaluate(const orc_instance* I, const orc_params* P, orc_state* S) {
   int32_t m = I->m;
   double* ybar = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
@@ -413,8 +417,8 @@ static void evaluate(const orc_instance* I, const orc_params* P, orc_state* S) {
   S->primal_avg = Pbar;
   S->evals += 1;
   S->converged = S->kkt <= P->kkt_tol;
-  if (!S->converged &&
-      (S->kkt <= P->restart_beta * S->kkt_anchor || (double)S->count >= P->restart_artificial * (double)S->t)) {
+  int progress = S->kkt <= P->restart_beta * S->kkt_anchor;
+  if (!S->converged && (progress || (double)S->count >= P->restart_artificial * (double)S->t)) {
     for (int32_t i = 0; i < m; ++i) {
       S->y[i] = ybar[i];
       S->sum_y[i] = 0.0;
@@ -425,6 +429,16 @@ static void evaluate(const orc_instance* I, const orc_params* P, orc_state* S) {
     S->kkt_anchor = S->kkt;
     if (S->mu_cur > 0.0) S->mu_cur *= 0.5;
     S->tau_used *= P->restart_tau_decay;
+    if (!progress && P->restart_tau_balance > 0.0) {
+      /* a constant step leaves a duality gap of order tau; when the epoch
+       * rule (not progress) forces the restart, move tau towards the step
+       * that balances the gap against the infeasibility */
+      double b = P->restart_tau_balance, f = 1.0;
+      if (S->pinf > 0.0 && S->gap > 0.0) f = sqrt(S->pinf / S->gap);
+      if (f < b) f = b;
+      if (f > 1.0 / b) f = 1.0 / b;
+      S->tau_used *= f;
+    }
     S->restarts += 1;
   }
   free(ybar);

@@ -351,7 +351,8 @@ spfom_status spfom_create(const spfom_params* p, spfom_ctx** out) {
   if (p) prm = *p; else spfom_default_params(&prm);
   if (prm.precision != 64 && prm.precision != 32) return SPFOM_ENOTSUP;
   if (!(prm.batch_frac > 0.0) || !(prm.restart_beta >= 0.0) || !(prm.kkt_tol >= 0.0) || prm.tau0 < 0 ||
-      prm.mu < 0 || !(prm.restart_tau_decay > 0.0))
+      prm.mu < 0 || !(prm.restart_tau_decay > 0.0) ||
+      !(prm.restart_tau_balance >= 0.0 && prm.restart_tau_balance <= 1.0) || prm.tiling < 0 || prm.tiling > 3)
     return SPFOM_EINVAL;
   spfom_ctx* ctx = new (std::nothrow) spfom_ctx;
   if (!ctx) return SPFOM_ENOMEM;
@@ -487,7 +488,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
     std::frexp(mass > 1.0 ? mass : 1.0, &e2);  // mass < 2^e2
     const int F = 61 - e2;
     spfom::FastPlan plan{};
-    if (ctx->p.path == 0 && !ctx->p.track_xbar && F >= 30 && spfom::fast_plan(n, kmax, ctx->sms, &plan)) {
+    if (ctx->p.path != 1 && !ctx->p.track_xbar && F >= 30 && spfom::fast_plan(n, kmax, ctx->sms, &plan)) {
       W.fast = true;
       if (ctx->p.pipeline && !ctx->loading_batch && spfom::pipe_plan(n, ctx->sms, &plan)) {
         // tiles of consecutive segments for the binary64 pipeline
@@ -505,6 +506,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
         SPFOM_TRY(upload(ctx, &W.tile_ptr, tiles.data(), tiles.size()));
         W.ntiles = nt;
       }
+      const bool dd = ctx->p.path == 0 && spfom::dd_setup(&plan, ctx->sms);
       W.plan = plan;
       W.fx_scale = std::ldexp(1.0, F);
       W.fx_bits = F;
@@ -512,9 +514,39 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       W.zparts_iter = std::max(std::max(plan.grid, plan.grid32), std::max(plan.pipe ? plan.pipe_grid : 0,
                                                                           plan.tma_ok ? plan.tma_grid : 0));
       W.zparts_eval = plan.grid_eval;
+      if (dd)
+        for (int v = 1; v <= 3; ++v) {
+          W.zparts_iter = std::max(W.zparts_iter, plan.dd_grid[v]);
+          W.zparts_eval = std::max(W.zparts_eval, plan.dd_grid_eval[v]);
+        }
+      W.dd_ok = dd;
+      if (ctx->p.tiling > 0) {  // a requested tiling of the active segment pass
+        const int t = ctx->p.tiling;
+        bool ok = t <= 3;
+        if (ok && ctx->p.precision == 32) {
+          ok = t != 2 || W.plan.tma_ok;
+          W.plan.tma = t == 2 ? 1 : 0;
+          W.plan.f32_p8 = t == 3 ? 1 : 0;
+        } else if (ok) {
+          ok = dd && spfom::dd_variant_ok(W.plan, t);
+          W.plan.dd_variant = t;
+        }
+        if (!ok) {
+          free_instance(ctx);
+          return fail(ctx, SPFOM_ENOTSUP, "tiling %d is not available for this instance", t);
+        }
+      }
       if (plan.scatter == 1)
         SPFOM_TRY(dalloc(ctx, &W.part, (size_t)W.zparts_iter * (size_t)(n > 0 ? n : 1)));
       SPFOM_TRY(dalloc(ctx, &W.s_fx, (size_t)n));
+    }
+    if (W.fast && W.dd_ok) {
+      // double-float images for k_seg_dd (the precision-64 iteration and every evaluation pass)
+      SPFOM_TRY(dalloc(ctx, &W.v2, (size_t)(nnz > 0 ? nnz : 1)));
+      SPFOM_TRY(dalloc(ctx, &W.vt2, (size_t)(nnz > 0 ? nnz : 1)));
+      SPFOM_TRY(dalloc(ctx, &W.seg4, (size_t)(L > 0 ? L : 1)));
+      SPFOM_TRY(dalloc(ctx, &W.marg2, (size_t)(n > 0 ? n : 1)));
+      SPFOM_TRY(dalloc(ctx, &W.marg2_eval, (size_t)(n > 0 ? n : 1)));
     }
     if (ctx->p.precision == 32) {
       if (!W.fast) {
@@ -551,6 +583,10 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   }
 #undef SPFOM_TRY
   ctx->P = P;
+  if (W.v2) {
+    e = spfom::launch_dd_prep(P, W.v2, W.vt2, W.seg4, ctx->stream);
+    if (e != cudaSuccess) { free_instance(ctx); return cuda_fail(ctx, e, "double-float images"); }
+  }
   if (W.v32) {
     e = spfom::launch_prep_f32(P, W, ctx->stream);
     if (e != cudaSuccess) { free_instance(ctx); return cuda_fail(ctx, e, "binary32 copies"); }
@@ -568,6 +604,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   cfg.restart_beta = ctx->p.restart_beta;
   cfg.restart_artificial = ctx->p.restart_artificial;
   cfg.restart_tau_decay = ctx->p.restart_tau_decay;
+  cfg.restart_tau_balance = ctx->p.restart_tau_balance;
   cfg.kkt_tol = ctx->p.kkt_tol;
   cfg.f32 = ctx->p.precision == 32 ? 1 : 0;
   ctx->loaded = true;
@@ -980,6 +1017,10 @@ spfom_status spfom_update(spfom_ctx* ctx, const double* c, const double* lam) {
       cudaError_t e = spfom::launch_prep_f32(P, ctx->W, ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "binary32 copies");
     }
+    if (ctx->W.v2) {  // the double-float images of lambda
+      cudaError_t e = spfom::launch_dd_prep(P, ctx->W.v2, ctx->W.vt2, ctx->W.seg4, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "double-float images");
+    }
   }
   // step sizes follow the new capacities: tau0 * mean(r) / mean(c), per instance in a batch
   if (c && !(ctx->p.tau > 0.0)) {
@@ -1029,9 +1070,22 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
   if (iters <= 0) return fail(ctx, SPFOM_EINVAL, "iters must be > 0");
   spfom::FastPlan& plan = ctx->W.plan;
-  const bool tunable = ctx->W.fast && ctx->W.v32 && ctx->cfg.f32 && plan.tma_ok;
-  if (!tunable) {
-    if (choice_out) *choice_out = plan.tma ? 2 : 1;
+  // binary32 pass: 1 = plain loads, 4 products per lane; 2 = staged tiles; 3 = plain loads, 8 per lane.
+  // double-float binary64 pass: the tilings of k_seg_dd (1..3).
+  const bool f32 = ctx->W.fast && ctx->W.v32 && ctx->cfg.f32;
+  const bool dd = ctx->W.fast && ctx->W.v2 && !ctx->cfg.f32;
+  auto current = [&]() { return f32 ? (plan.tma ? 2 : (plan.f32_p8 ? 3 : 1)) : (dd ? plan.dd_variant : 1); };
+  auto available = [&](int c) { return f32 ? (c != 2 || plan.tma_ok) : (dd && spfom::dd_variant_ok(plan, c)); };
+  auto select = [&](int c) {
+    if (f32) {
+      plan.tma = c == 2 ? 1 : 0;
+      plan.f32_p8 = c == 3 ? 1 : 0;
+    } else {
+      plan.dd_variant = c;
+    }
+  };
+  if (!f32 && !dd) {
+    if (choice_out) *choice_out = 1;
     return SPFOM_OK;
   }
   SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
@@ -1043,9 +1097,10 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   const double saved_tol = ctx->cfg.kkt_tol;
   ctx->cfg.kkt_tol = -1.0;  // no instance may converge (and stop working) while being timed
   double best = INFINITY;
-  int choice = 1;
-  for (int cand = 1; cand <= 2; ++cand) {
-    plan.tma = cand == 2 ? 1 : 0;
+  int choice = current();
+  for (int cand = 1; cand <= 3; ++cand) {
+    if (!available(cand)) continue;
+    select(cand);
     drop_graphs(ctx);
     spfom_status s = init_state(ctx, y0.data());
     spfom_stats st{};
@@ -1061,7 +1116,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
     }
   }
   ctx->cfg.kkt_tol = saved_tol;
-  plan.tma = choice == 2 ? 1 : 0;
+  select(choice);
   drop_graphs(ctx);
   spfom_status s = init_state(ctx, y0.data());
   if (s != SPFOM_OK) return s;

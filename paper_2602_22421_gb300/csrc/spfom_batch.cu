@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include "spfom_device.cuh"
 #include "spfom_internal.h"
 
 namespace spfom {
@@ -42,7 +43,7 @@ __device__ double bsum(double v, double* sh) {
 // instance); clears the fixed-point sales and fills the binary32 copy if asked.
 __global__ void k_b_margins(Problem P, BatchMaps B, const double* __restrict__ y, const double* __restrict__ sum_y,
                             int avg, double* __restrict__ marg, float* __restrict__ marg32,
-                            unsigned long long* __restrict__ sfx_clear) {
+                            unsigned long long* __restrict__ sfx_clear, float2* __restrict__ marg2) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= P.n) return;
   const InstState& I = B.inst[B.prod_inst[j]];
@@ -55,8 +56,10 @@ __global__ void k_b_margins(Problem P, BatchMaps B, const double* __restrict__ y
     const double yi = avg ? __ddiv_rn(sum_y[i], cnt) : y[i];
     acc = __dadd_rn(acc, __dmul_rn(a, yi));
   }
-  marg[j] = __dsub_rn(P.r[j], acc);
-  if (marg32) marg32[j] = __double2float_rn(marg[j]);
+  const double m = __dsub_rn(P.r[j], acc);
+  marg[j] = m;
+  if (marg32) marg32[j] = __double2float_rn(m);
+  if (marg2) marg2[j] = m > 0.0 ? split_pair(m) : make_float2(m < 0.0 ? -1.f : 0.f, 0.f);
   if (sfx_clear) sfx_clear[j] = 0ull;
 }
 
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) k_b_finish(Problem P, Work Wk) {
 // test, as for a single instance.
 __global__ void __launch_bounds__(kThreads) k_b_eval_finish(Problem P, Work Wk, RunConfig cfg) {
   __shared__ double sh[32];
-  __shared__ int restart;
+  __shared__ int restart, progress;
   const BatchMaps& B = Wk.bm;
   const int b = blockIdx.x;
   InstState& I = B.inst[b];
@@ -150,8 +153,8 @@ __global__ void __launch_bounds__(kThreads) k_b_eval_finish(Problem P, Work Wk, 
     I.evals += 1;
     I.converged = kkt <= cfg.kkt_tol;
     B.conv[b] = I.converged;
-    restart = !I.converged && (kkt <= cfg.restart_beta * I.kkt_anchor ||
-                               (double)I.count >= cfg.restart_artificial * (double)I.t);
+    progress = kkt <= cfg.restart_beta * I.kkt_anchor;
+    restart = !I.converged && (progress || (double)I.count >= cfg.restart_artificial * (double)I.t);
   }
   __syncthreads();
   if (!restart) return;
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(kThreads) k_b_eval_finish(Problem P, Work Wk, 
     I.kkt_anchor = I.kkt;
     if (I.mu > 0.0) I.mu *= 0.5;
     I.tau *= cfg.restart_tau_decay;
+    if (!progress && cfg.restart_tau_balance > 0.0) I.tau *= balance_factor(I.pinf, I.gap, cfg.restart_tau_balance);
     I.restarts += 1;
   }
 }
@@ -177,7 +181,7 @@ int blocks_for(int n) { return n > 0 ? (n + kThreads - 1) / kThreads : 1; }
 cudaError_t launch_batch_iteration(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s) {
   const bool f32 = cfg.f32 && Wk.v32;
   k_b_margins<<<blocks_for(P.n), kThreads, 0, s>>>(P, Wk.bm, Wk.y, nullptr, 0, Wk.marg, f32 ? Wk.marg32 : nullptr,
-                                                    Wk.s_fx);
+                                                    Wk.s_fx, f32 ? nullptr : Wk.marg2);
   int zparts = 0;
   cudaError_t e = launch_segment_pass(P, Wk, cfg, Wk.marg, true, s, &zparts);
   if (e != cudaSuccess) return e;
@@ -189,7 +193,8 @@ cudaError_t launch_batch_iteration(const Problem& P, const Work& Wk, const RunCo
 }
 
 cudaError_t launch_batch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s) {
-  k_b_margins<<<blocks_for(P.n), kThreads, 0, s>>>(P, Wk.bm, nullptr, Wk.sum_y, 1, Wk.marg_eval, nullptr, nullptr);
+  k_b_margins<<<blocks_for(P.n), kThreads, 0, s>>>(P, Wk.bm, nullptr, Wk.sum_y, 1, Wk.marg_eval, nullptr, nullptr,
+                                                    Wk.marg2_eval);
   int zparts = 0;
   cudaError_t e = launch_segment_pass(P, Wk, cfg, Wk.marg_eval, false, s, &zparts);
   if (e != cudaSuccess) return e;

@@ -88,6 +88,25 @@ __device__ __forceinline__ unsigned long long fixed_product32(float a, float b, 
   return (prod + (1ull << (sh - 1))) >> sh;
 }
 
+// (hi, lo) pair of a binary64 value: hi = round(x), lo = round(x - hi). A
+// nonzero value outside [1e-30, 1e30] in magnitude gets hi = NaN, which makes
+// the certificate of the double-float kernel fail (binary64 fallback).
+__device__ __forceinline__ float2 split_pair(double x) {
+  const double ax = fabs(x);
+  if (x != 0.0 && !(ax >= 1e-30 && ax <= 1e30)) return make_float2(__int_as_float(0x7fc00000), 0.f);
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// Step factor of a restart forced by the epoch-length rule (restart_tau_balance
+// = b > 0): clamp(sqrt(pinf / gap), b, 1 / b), 1 when either residual is 0.
+__device__ __forceinline__ double balance_factor(double pinf, double gap, double b) {
+  double f = (pinf > 0.0 && gap > 0.0) ? sqrt(pinf / gap) : 1.0;
+  const double hi = 1.0 / b;
+  f = f < b ? b : f;
+  return f > hi ? hi : f;
+}
+
 __device__ __forceinline__ unsigned smem_addr(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }

@@ -91,6 +91,10 @@ struct FastPlan {
   int tma_W;          // its lanes per segment (8 products per lane)
   int tma_grid;       // its blocks
   int tma_ok;         // 1 when the staged kernel is available (spfom_autotune may switch tma)
+  int f32_p8;         // 1: the plain-load binary32 kernel runs 8 products per lane (W8 lanes)
+  int dd_variant;     // tiling of k_seg_dd (1..3, see spfom_segments_dd.cu)
+  int dd_grid[4];     // its grid per tiling (iterate), 0 = unavailable
+  int dd_grid_eval[4];  // and for the evaluation pass
   int tma_smem;       // its dynamic shared memory: product sums + two stages
   int acc_bytes;      // bytes of the product sums at the start of that memory
   int pipe;           // 1: the binary64 pass runs k_seg_fast_pipe (warp-specialised TMA pipeline)
@@ -109,6 +113,13 @@ struct Work {
   double* y_eval;      // dual point handed to spfom_evaluate / spfom_sales_at
   double* s_eval;      // [n] product sales of spfom_sales_at
   double* xsum;        // [nnz] epoch sums of every segment's response (track_xbar), or null
+  // double-float images for the precision-64 kernel k_seg_dd (null when it is not used)
+  float2* v2;          // [nnz] (hi, lo) of v
+  float2* vt2;         // [nnz] (hi, lo) of v - w
+  float4* seg4;        // [L] (hi, lo) of lambda and of vt_0
+  float2* marg2;       // [n] (hi, lo) of the margins (iterate)
+  float2* marg2_eval;  // [n] (hi, lo) of the margins (evaluation)
+  bool dd_ok;          // k_seg_dd planned (path 0)
   double* z_seg;       // [L] per-segment values of spfom_evaluate
   double* zpart;       // per-block partial sums of z (iterate)
   double* zpart_eval;  // per-block partial sums of z (evaluation)
@@ -163,6 +174,33 @@ struct FastArgs {
   double* z_seg;
 };
 
+// Arguments of k_seg_dd (spfom_segments_dd.cu): double-float images, and the
+// binary64 arrays for the segments whose decision is not certified.
+struct DdArgs {
+  const long long* seg_ptr;
+  const int* seg_prod;
+  const float2* v2;
+  const float2* vt2;
+  const float4* seg4;
+  const float2* marg2;
+  const double* marg;
+  const double* v;
+  const double* vt;
+  const double* lam;
+  const double* vt0;
+  long long L;
+  int n;
+  int fx_bits;
+  unsigned long long* part;
+  unsigned long long* s_fx;
+  double* zpart;
+  const DevState* st;
+  unsigned long long* fallbacks;
+  const int* seg_inst;
+  const int* inst_conv;
+  double* z_seg;
+};
+
 struct F32Args {
   const long long* seg_ptr;
   const int* seg_prod;
@@ -194,6 +232,7 @@ struct RunConfig {
   unsigned long long seed;
   unsigned long long sample_thr;  // segment l is solved at t iff hash < sample_thr
   double restart_beta, restart_artificial, restart_tau_decay, kkt_tol;
+  double restart_tau_balance;
   int f32;  // run the iterations' segment pass in binary32
 };
 
@@ -221,6 +260,11 @@ int kernel_launches_per_eval();
 // spfom_segments_fast.cu
 bool fast_plan(int n, int kmax, int sms, FastPlan* plan);
 cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s);
+// double-float precision-64 kernel (spfom_segments_dd.cu)
+cudaError_t launch_seg_dd(const DdArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s);
+cudaError_t launch_dd_prep(const Problem& P, float2* v2, float2* vt2, float4* seg4, cudaStream_t s);
+bool dd_setup(FastPlan* plan, int sms);
+int dd_variant_ok(const FastPlan& plan, int v);
 cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s);
 bool tma_plan(int n, int kmax, int sms, FastPlan* plan);
 // spfom_batch.cu

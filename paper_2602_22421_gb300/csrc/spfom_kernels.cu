@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include "spfom_device.cuh"
 #include "spfom_internal.h"
 
 namespace spfom {
@@ -87,7 +88,7 @@ __global__ void k_prep_segments(long long L, const long long* __restrict__ seg_p
 __global__ void k_margins(Problem P, const double* __restrict__ y, const double* __restrict__ sum_y, int avg,
                           double* __restrict__ marg, double* __restrict__ s_clear,
                           unsigned long long* __restrict__ sfx_clear, const DevState* st,
-                          float* __restrict__ marg32 = nullptr) {
+                          float* __restrict__ marg32 = nullptr, float2* __restrict__ marg2 = nullptr) {
   if (st && st->converged) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= P.n) return;
@@ -99,8 +100,11 @@ __global__ void k_margins(Problem P, const double* __restrict__ y, const double*
     const double yi = avg ? __ddiv_rn(sum_y[i], cnt) : y[i];
     acc = __dadd_rn(acc, __dmul_rn(a, yi));
   }
-  marg[j] = __dsub_rn(P.r[j], acc);
-  if (marg32) marg32[j] = __double2float_rn(marg[j]);
+  const double m = __dsub_rn(P.r[j], acc);
+  marg[j] = m;
+  if (marg32) marg32[j] = __double2float_rn(m);
+  // pairs for the double-float kernel: only positive margins enter its decision
+  if (marg2) marg2[j] = m > 0.0 ? split_pair(m) : make_float2(m < 0.0 ? -1.f : 0.f, 0.f);
   if (s_clear) s_clear[j] = 0.0;
   if (sfx_clear) sfx_clear[j] = 0ull;
 }
@@ -296,11 +300,11 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
 // ------------------------------------------------------------------- a6 --
 // KKT residual of the epoch averages and the restart test (solver addition;
 // the paper's Remark in Section 4.2 notes SPFOM forms no residuals).
-__global__ void __launch_bounds__(1024) k_eval_finish(Problem P, Work Wk, RunConfig cfg) {
+__global__ void __launch_bounds__(1024) k_eval_finish(Problem P, Work Wk, RunConfig cfg, int zparts) {
   DevState* st = Wk.st;
   if (st->converged) return;
   __shared__ double sh[32];
-  __shared__ int restart;
+  __shared__ int restart, progress;
   const double cnt = (double)st->count;
   double cy = 0.0, over2 = 0.0, c2 = 0.0;
   for (int i = threadIdx.x; i < P.m; i += blockDim.x) {
@@ -311,7 +315,7 @@ __global__ void __launch_bounds__(1024) k_eval_finish(Problem P, Work Wk, RunCon
     c2 += __dmul_rn(c, c);
   }
   double zs = 0.0;
-  for (int b = threadIdx.x; b < Wk.zparts_eval; b += blockDim.x) zs += Wk.zpart_eval[b];
+  for (int b = threadIdx.x; b < zparts; b += blockDim.x) zs += Wk.zpart_eval[b];
   zs = block_sum(zs, sh);
   const double tcy = block_sum(cy, sh);
   const double tover = block_sum(over2, sh);
@@ -329,8 +333,8 @@ __global__ void __launch_bounds__(1024) k_eval_finish(Problem P, Work Wk, RunCon
     st->primal_avg = Pbar;
     st->evals += 1;
     st->converged = kkt <= cfg.kkt_tol;
-    restart = !st->converged && (kkt <= cfg.restart_beta * st->kkt_anchor ||
-                                 (double)st->count >= cfg.restart_artificial * (double)st->t);
+    progress = kkt <= cfg.restart_beta * st->kkt_anchor;
+    restart = !st->converged && (progress || (double)st->count >= cfg.restart_artificial * (double)st->t);
   }
   __syncthreads();
   if (!restart) return;
@@ -345,6 +349,8 @@ __global__ void __launch_bounds__(1024) k_eval_finish(Problem P, Work Wk, RunCon
     st->kkt_anchor = st->kkt;
     if (st->mu > 0.0) st->mu *= 0.5;
     st->tau *= cfg.restart_tau_decay;
+    if (!progress && cfg.restart_tau_balance > 0.0)
+      st->tau *= balance_factor(st->pinf, st->gap, cfg.restart_tau_balance);
     st->restarts += 1;
   }
 }
@@ -404,6 +410,16 @@ cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfi
   const int* seg_inst = Wk.batch ? Wk.bm.seg_inst : nullptr;
   const int* conv = Wk.batch ? Wk.bm.conv : nullptr;
   double* z_seg = Wk.batch ? Wk.bm.z_seg : nullptr;
+  if (Wk.v2 && (!iterate || !(cfg.f32 && Wk.v32))) {
+    // double-float precision-64 kernel (also the evaluation pass of precision 32)
+    const bool it = iterate;
+    DdArgs A{P.seg_ptr, P.seg_prod, Wk.v2, Wk.vt2, Wk.seg4, it ? Wk.marg2 : Wk.marg2_eval, marg, P.v, P.vt, P.lam,
+             P.vt0, P.L, P.n, Wk.fx_bits, it ? Wk.part : nullptr, it ? Wk.s_fx : nullptr,
+             it ? Wk.zpart : Wk.zpart_eval, Wk.st, Wk.fallbacks, seg_inst, conv, z_seg};
+    const int v = Wk.plan.dd_variant >= 1 && Wk.plan.dd_variant <= 3 ? Wk.plan.dd_variant : 1;
+    *zparts_out = it ? Wk.plan.dd_grid[v] : Wk.plan.dd_grid_eval[v];
+    return launch_seg_dd(A, Wk.plan, it, s);
+  }
   if (!iterate) {
     FastArgs A{P, marg, nullptr, Wk.zpart_eval, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, nullptr,
                nullptr, 0, 0, Wk.st, seg_inst, conv, z_seg};
@@ -436,7 +452,8 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
   const int gv = vec_grid(P);
   const int gn = (P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1;
   k_margins<<<gn, kVecThreads, 0, s>>>(P, Wk.y, nullptr, 0, Wk.marg, (sampled || fast) ? nullptr : Wk.s,
-                                       fast ? Wk.s_fx : nullptr, Wk.st, f32 ? Wk.marg32 : nullptr);
+                                       fast ? Wk.s_fx : nullptr, Wk.st, f32 ? Wk.marg32 : nullptr,
+                                       (fast && !f32) ? Wk.marg2 : nullptr);
   if (seg_begin) cudaEventRecord(seg_begin, s);
   cudaError_t e;
   int zparts = Wk.seg_blocks;
@@ -459,16 +476,17 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
 cudaError_t launch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s) {
   if (Wk.batch) return launch_batch_eval(P, Wk, cfg, s);
   const int gn = (P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1;
-  k_margins<<<gn, kVecThreads, 0, s>>>(P, nullptr, Wk.sum_y, 1, Wk.marg_eval, nullptr, nullptr, Wk.st);
+  k_margins<<<gn, kVecThreads, 0, s>>>(P, nullptr, Wk.sum_y, 1, Wk.marg_eval, nullptr, nullptr, Wk.st, nullptr,
+                                       Wk.fast ? Wk.marg2_eval : nullptr);
   cudaError_t e;
+  int zparts = Wk.seg_blocks;
   if (Wk.fast) {
-    int zparts = 0;
     e = launch_segment_pass(P, Wk, cfg, Wk.marg_eval, false, s, &zparts);
   } else {
     e = launch_segments_w<kEvalSum, false>(P, Wk, Wk.marg_eval, Wk.zpart_eval, Wk.st, cfg, s);
   }
   if (e != cudaSuccess) return e;
-  k_eval_finish<<<1, 1024, 0, s>>>(P, Wk, cfg);
+  k_eval_finish<<<1, 1024, 0, s>>>(P, Wk, cfg, zparts);
   return cudaGetLastError();
 }
 

@@ -215,16 +215,16 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
     const long long b = A.seg_ptr[l];
     const int K = (int)(A.seg_ptr[l + 1] - b);
     int jv[P];
-    float vv[P], tv[P], af[P];
+    float tv[P], af[P];
     unsigned cand = 0;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       const int k = lane + p * W;
       jv[p] = 0;
-      vv[p] = tv[p] = af[p] = 0.f;
+      tv[p] = af[p] = 0.f;
       if (k < K) {
         jv[p] = A.seg_prod[b + k];
-        vv[p] = A.v32[b + k];
+        af[p] = A.v32[b + k];
         tv[p] = A.vt32[b + k];
       }
     }
@@ -234,7 +234,9 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
         const float m = A.marg32[jv[p]];
         if (m > 0.f) {
           cand |= 1u << p;
-          af[p] = m * vv[p];
+          af[p] = m * af[p];
+        } else {
+          af[p] = 0.f;
         }
       }
     const float lam = A.lam32[l], vt0 = A.vt0_32[l];
@@ -269,7 +271,8 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
     if (SC != 0) {
 #pragma unroll
       for (int p = 0; p < P; ++p)
-        if ((sel >> p) & 1u) atomicAdd((SC == 1 ? acc : A.s_fx) + jv[p], fixed_product32(q, vv[p], A.fx_bits));
+        if ((sel >> p) & 1u)
+          atomicAdd((SC == 1 ? acc : A.s_fx) + jv[p], fixed_product32(q, A.v32[b + lane + p * W], A.fx_bits));
     }
   }
   const double tot = block_sum_d((double)zacc, sh);
@@ -503,6 +506,17 @@ cudaError_t launch_f32_w(const F32Args& A, int W, int grid, int smem, cudaStream
 }
 
 template <int SC>
+cudaError_t launch_f32_p8(const F32Args& A, int W8, int grid, int smem, cudaStream_t s) {
+  switch (W8) {  // 8 products per lane
+    case 1: k_seg_f32<1, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 2: k_seg_f32<2, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 4: k_seg_f32<4, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int SC>
 cudaError_t launch_tma_w(const F32Args& A, int W, int grid, int smem, cudaStream_t s) {
   switch (W) {  // 8 products per lane
     case 1: k_seg_f32_tma<1, 8, SC><<<grid, kTmaThreads, smem, s>>>(A); break;
@@ -555,6 +569,11 @@ bool fast_plan(int n, int kmax, int sms, FastPlan* plan) {
   const int nb32 = occupancy(W, sc, smem, true);
   const int nbe = occupancy(W8, 0, 0, false);
   if (nb <= 0 || nbe <= 0 || nb32 <= 0) return false;
+  if (sc == 1) {  // the 8-products-per-lane binary32 variant shares the grid of the 4-per-lane one
+    cudaFuncSetAttribute(k_seg_f32<1, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_seg_f32<2, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_seg_f32<4, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  }
   plan->W = W;
   plan->W8 = W8;
   plan->scatter = sc;
@@ -576,6 +595,9 @@ cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t 
   if (plan.tma)
     return plan.scatter == 1 ? launch_tma_w<1>(A, plan.tma_W, plan.tma_grid, plan.tma_smem, s)
                              : launch_tma_w<2>(A, plan.tma_W, plan.tma_grid, plan.tma_smem, s);
+  if (plan.f32_p8)
+    return plan.scatter == 1 ? launch_f32_p8<1>(A, plan.W8, plan.grid32, plan.smem, s)
+                             : launch_f32_p8<2>(A, plan.W8, plan.grid32, 0, s);
   return plan.scatter == 1 ? launch_f32_w<1>(A, plan.W, plan.grid32, plan.smem, s)
                            : launch_f32_w<2>(A, plan.W, plan.grid32, 0, s);
 }

@@ -11,6 +11,10 @@ s = spfom_sales_at(y) -- and the inventory drops by the consumption A s
 (clipped at zero). The initial inventory is `periods` times the base
 capacity (c = 0.6 x one period's full-offer demand).
 
+Both take the solver's parameters; the family's smallest instances (about
+1e3 segments over thousands of products) need restart_tau_balance > 0 to
+reach KKT <= 1e-4 with either form.
+
 ``run_batched`` solves all base instances of a period in one batch
 (spfom_load_batch once, spfom_update per period, warm-started from the
 previous period's bid prices), in the binary32 bulk iteration with the
@@ -44,16 +48,16 @@ def _split(vec, sizes):
     return out
 
 
-def run_batched(insts, rho, periods: int = 16, precision: int = 32, tune: bool = True, log=None):
-    """Solve every period of every instance, one batch per period. Returns
-    (per-period records, the capacity and rate path, per-(period, instance)
-    stats)."""
+def run_batched(insts, rho, periods: int = 16, precision: int = 32, tune: bool = True, log=None, **params):
+    """Solve every period of every instance, one batch per period (solver
+    parameters `params`). Returns (per-period records, the capacity and rate
+    path, per-(period, instance) stats)."""
     import torch
     ms = [i.m for i in insts]
     ns = [i.n for i in insts]
     inv = [periods * np.asarray(i.c, np.float64) for i in insts]
     path, per_stats, recs = [], [], []
-    with Solver(None, device=0, precision=precision) as s:
+    with Solver(None, device=0, precision=precision, **params) as s:
         t = time.perf_counter()
         s.load_batch(insts)
         load_s = time.perf_counter() - t
@@ -83,14 +87,14 @@ def run_batched(insts, rho, periods: int = 16, precision: int = 32, tune: bool =
     return {"records": recs, "load_seconds": load_s, "autotune_choice": choice}, path, per_stats
 
 
-def run_sequential(insts, path, which=None, precision: int = 64, log=None):
+def run_sequential(insts, path, which=None, precision: int = 64, log=None, **params):
     """Plain re-solves of the (period, instance) problems on the recorded
     capacity path, one instance at a time from y = 0. `which` selects
     instance indices (default all). Returns per-solve records."""
     import torch
     idx = list(range(len(insts))) if which is None else list(which)
     out = []
-    with Solver(None, device=0, precision=precision) as s:
+    with Solver(None, device=0, precision=precision, **params) as s:
         for b in idx:
             inst = insts[b]
             s.load(inst)

@@ -40,10 +40,11 @@ class Params(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tau", C.c_double), ("tau0", C.c_double), ("mu", C.c_double),
                 ("batch_frac", C.c_double), ("seed", C.c_uint64), ("eval_every", C.c_int64),
                 ("restart_beta", C.c_double), ("restart_artificial", C.c_double),
-                ("restart_tau_decay", C.c_double), ("kkt_tol", C.c_double), ("max_iters", C.c_int64),
+                ("restart_tau_decay", C.c_double), ("restart_tau_balance", C.c_double), ("kkt_tol", C.c_double),
+                ("max_iters", C.c_int64),
                 ("device", C.c_int32), ("profile", C.c_int32), ("path", C.c_int32), ("pipeline", C.c_int32),
                 ("graphs", C.c_int32),
-                ("polish", C.c_int32), ("track_xbar", C.c_int32),
+                ("polish", C.c_int32), ("track_xbar", C.c_int32), ("tiling", C.c_int32),
                 ("stream", C.c_void_p)]
 
 

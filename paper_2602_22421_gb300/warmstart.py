@@ -44,9 +44,9 @@ def instances(seed: int, ks, L_lo: float = 1e4, L_hi: float = 5e4, pool=None):
     return list(pool.map(_make, jobs)) if pool is not None else [_make(j) for j in jobs]
 
 
-def solve_batch(insts, precision: int = 64):
+def solve_batch(insts, precision: int = 64, **params):
     """Batched plain solve to KKT <= 1e-4: (per-instance averaged duals, stats)."""
-    with Solver(None, device=0, precision=precision) as s:
+    with Solver(None, device=0, precision=precision, **params) as s:
         s.load_batch(insts)
         s.solve()
         y = s.duals(averaged=True)
@@ -74,7 +74,7 @@ def features_of(insts, solver=None):
 
 
 def build_dataset(n_inst: int, seed: int = TRAIN_SEED, chunk: int = 64, L_lo: float = 1e4, L_hi: float = 5e4,
-                  workers: int = 8, log=print):
+                  workers: int = 8, log=print, **params):
     """Generate, solve and featurise n_inst instances in chunks (generation of
     the next chunk overlaps the solves of the current one). Returns X [R, 16],
     T [R] (targets y* / mean(r)) as float32 host arrays and a summary."""
@@ -90,7 +90,7 @@ def build_dataset(n_inst: int, seed: int = TRAIN_SEED, chunk: int = 64, L_lo: fl
             if ci + 1 < len(starts):
                 b = starts[ci + 1]
                 nxt = pool.map(_make, [(seed, k, L_lo, L_hi) for k in range(b, min(b + chunk, n_inst))])
-            ys, per = solve_batch(insts)
+            ys, per = solve_batch(insts, **params)
             unconverged += sum(1 for p in per if not p["converged"])
             feats = features_of(insts, fs)
             for inst, y, f in zip(insts, ys, feats):
@@ -144,7 +144,7 @@ def load(path: str = DEFAULT_WEIGHTS) -> MLP:
     return net
 
 
-def evaluate(net: MLP, insts, precision: int = 64, log=None):
+def evaluate(net: MLP, insts, precision: int = 64, log=None, **params):
     """Cold (spfom_solve from y = 0) and warm (spfom_solve_warm) solves of each
     instance, timed on the host around the call (the warm time includes the
     features and the forward pass). Each instance first runs one evaluation
@@ -152,7 +152,7 @@ def evaluate(net: MLP, insts, precision: int = 64, log=None):
     Returns per-instance records."""
     import torch
     out = []
-    with Solver(None, device=0, precision=precision) as s:
+    with Solver(None, device=0, precision=precision, **params) as s:
         for k, inst in enumerate(insts):
             s.load(inst)
             s.step(s.params.eval_every)

@@ -205,6 +205,29 @@ def test_run_converges_to_lp_optimum_gam():
     assert st["dual_avg"] == pytest.approx(opt, rel=2e-4)
 
 
+def test_balanced_restarts_reach_the_optimum_where_a_constant_step_stalls():
+    """An instance of the batched family with few segments per product (1475
+    segments, 4511 products): with the constant step the averaged duality gap
+    stalls near 1e-3 (an O(tau) gap); balancing tau at the restarts the
+    epoch-length rule forces reaches KKT <= 1e-4 and the HiGHS optimum."""
+    from instances import batch_base
+    inst = batch_base(4, 10)
+    opt, _ = sblp_highs(inst)
+    o = Oracle(inst)
+    const = o.run(Params())
+    for _ in range(60):
+        st = const.step(64)
+    assert st["converged"] == 0 and st["gap"] > 3 * st["pinf"]
+    run = o.run(Params(restart_tau_balance=0.5))
+    for _ in range(300):
+        st = run.step(64)
+        if st["converged"]:
+            break
+    assert st["converged"] == 1, st
+    assert st["dual_avg"] == pytest.approx(opt, rel=2e-4)
+    assert o.dual(run.ybar) >= opt * (1 - 1e-12)
+
+
 def test_regularised_step_shrinks_duals():
     """eq. stronglycvxupdate: with consumption equal to capacity the step
     reduces to y <- (1 - tau mu) y. Capacities are set to the consumption at a
