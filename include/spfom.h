@@ -80,13 +80,13 @@ typedef struct {
   int32_t profile;           /* 0; nonzero: time every segment-kernel launch of spfom_step with
                                 a CUDA event pair (spfom_stats.seg_kernel_seconds) */
   int32_t path;              /* 0 (default): the certified-decision segment kernel whenever the
-                                instance allows it (sets of <= 32 products, full batch), with the
-                                values of the chosen assortments in double-binary32 arithmetic
-                                (binary64 inputs held as (hi, lo) binary32 pairs, about 1e-13
-                                relative; binary64 for uncertified segments), else the general
+                                instance allows it (sets of <= 32 products, full batch), with
+                                binary64 values of the chosen assortments, else the general
                                 kernel; 1: always the general kernel; 2: the certified-decision
-                                kernel with binary64 value sums */
-  int32_t pipeline;          /* path 2 only. 0 (default): the binary64 certified pass reads with plain loads;
+                                kernel with the values in double-binary32 arithmetic (binary64
+                                inputs held as (hi, lo) binary32 pairs, about 1e-13 relative;
+                                binary64 for uncertified segments), three tilings */
+  int32_t pipeline;          /* path 0 only. 0 (default): the binary64 certified pass reads with plain loads;
                                 1: it streams tiles of segments into shared memory through a
                                 warp-specialised bulk-copy (TMA) pipeline when shared memory allows
                                 (slower on the mid instance: the stages crowd the L1 cache that
@@ -256,9 +256,10 @@ spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out);
  * iteration from those duals. Candidates: precision 32: 1 = plain loads with
  * 4 products per lane, 2 = tiles staged by bulk copies with 8 products per
  * lane (when shared memory allows), 3 = plain loads with 8 products per lane;
- * precision 64 (path 0): 1 = 8 products per lane at two 512-thread blocks per
+ * precision 64 with path 2: 1 = 8 products per lane at two 512-thread blocks per
  * SM, 2 = 8 per lane at three blocks per SM, 3 = 4 per lane at three blocks
- * per SM. *choice_out (or NULL) gets the choice (1 when there is none). */
+ * per SM. *choice_out (or NULL) gets the choice (1 when there is none, as for
+ * precision 64 with path 0). */
 spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* choice_out);
 
 /* ---- Recovering assortments (Section 4.4) ----------------------------------

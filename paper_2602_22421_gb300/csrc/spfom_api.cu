@@ -506,7 +506,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
         SPFOM_TRY(upload(ctx, &W.tile_ptr, tiles.data(), tiles.size()));
         W.ntiles = nt;
       }
-      const bool dd = ctx->p.path == 0 && spfom::dd_setup(&plan, ctx->sms);
+      const bool dd = ctx->p.path == 2 && spfom::dd_setup(&plan, ctx->sms);
       W.plan = plan;
       W.fx_scale = std::ldexp(1.0, F);
       W.fx_bits = F;
@@ -528,8 +528,8 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
           W.plan.tma = t == 2 ? 1 : 0;
           W.plan.f32_p8 = t == 3 ? 1 : 0;
         } else if (ok) {
-          ok = dd && spfom::dd_variant_ok(W.plan, t);
-          W.plan.dd_variant = t;
+          ok = dd ? spfom::dd_variant_ok(W.plan, t) != 0 : t == 1;  // the binary64-sum kernel has one tiling
+          if (dd) W.plan.dd_variant = t;
         }
         if (!ok) {
           free_instance(ctx);

@@ -214,6 +214,8 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
     if (A.seg_inst && A.inst_conv[A.seg_inst[l]]) continue;  // batch: instance already converged
     const long long b = A.seg_ptr[l];
     const int K = (int)(A.seg_ptr[l + 1] - b);
+    const int* __restrict__ sp = A.seg_prod + b;  // the segment's slice of the consideration-set CSR
+    const float* __restrict__ v32 = A.v32 + b;
     int jv[P];
     float tv[P], af[P];
     unsigned cand = 0;
@@ -223,8 +225,8 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
       jv[p] = 0;
       tv[p] = af[p] = 0.f;
       if (k < K) {
-        jv[p] = A.seg_prod[b + k];
-        af[p] = A.v32[b + k];
+        jv[p] = sp[k];
+        af[p] = v32[k];
         tv[p] = A.vt32[b + k];
       }
     }
@@ -269,10 +271,10 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
       else zacc += q * Nsel;
     }
     if (SC != 0) {
-#pragma unroll
-      for (int p = 0; p < P; ++p)
-        if ((sel >> p) & 1u)
-          atomicAdd((SC == 1 ? acc : A.s_fx) + jv[p], fixed_product32(q, A.v32[b + lane + p * W], A.fx_bits));
+      for (unsigned msk = sel; msk; msk &= msk - 1) {  // this lane's chosen slots
+        const int k = lane + (__ffs(msk) - 1) * W;
+        atomicAdd((SC == 1 ? acc : A.s_fx) + sp[k], fixed_product32(q, v32[k], A.fx_bits));
+      }
     }
   }
   const double tot = block_sum_d((double)zacc, sh);

@@ -68,8 +68,8 @@ CASES = {"tiny_mnl": lambda: tiny_mnl(0), "small_gam": small_gam, "edge": edge_i
          "wide": wide}
 
 
-@pytest.mark.parametrize("path,tiling", [(0, 1), (0, 2), (0, 3), (1, 0), (2, 0)],
-                         ids=["double_float_t1", "double_float_t2", "double_float_t3", "general", "binary64_sums"])
+@pytest.mark.parametrize("path,tiling", [(0, 0), (1, 0), (2, 1), (2, 2), (2, 3)],
+                         ids=["certified", "general", "double_float_t1", "double_float_t2", "double_float_t3"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_iterates_track_oracle_200(name, path, tiling):
     inst = CASES[name]()
@@ -335,7 +335,7 @@ def test_pipeline_equals_plain_loads(name):
     inst = CASES[name]()
     out = {}
     for pipeline in (0, 1):
-        with Solver(inst, pipeline=pipeline, path=2) as s:
+        with Solver(inst, pipeline=pipeline) as s:
             st = s.step(130)
             out[pipeline] = (s.duals(), s.vector(5), st)
     np.testing.assert_array_equal(out[0][1], out[1][1])
