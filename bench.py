@@ -493,6 +493,23 @@ def learned_leg(args, local):
     recs = W.evaluate(net, test)
     net.close()
     out = W.summarize(recs)
+    # the training step of the network on the tensor cores (BF16 tcgen05 products)
+    from paper_2602_22421_gb300 import mlpbench
+    import contextlib
+    import io
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        mlpbench.main(["--rows", "262144", "--steps", "20"])
+    tr = json.loads(buf.getvalue().strip().splitlines()[-1])
+    peak = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    out["training_step"] = {"rows": tr["rows"], "ms": tr["ms_per_step"],
+                            "roofline": {"bound": "tensor", "achieved": tr["tflops"], "peak": peak or 1900.0,
+                                         "unit": "TFLOP/s", "frac": tr["tflops"] / (peak or 1900.0),
+                                         "peak_source": "measured bf16_tflops" if peak else "fallback"}}
     out["workload"] = ("held-out warm_family(seed 6) instances: n=2000, m=400, L=10^U(4,4.7), |C_l|~U{10..30}, "
                        "c=0.4 x demand")
     return out

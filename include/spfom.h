@@ -102,7 +102,7 @@ typedef struct {
                                 nonzero read and written each iteration); needs precision 64,
                                 batch_frac 1 and a single instance, and runs the general kernel */
   int32_t tiling;            /* 0 (default): tiling 1 of the active segment pass until
-                                spfom_autotune picks one; 1..3: that tiling (see spfom_autotune),
+                                spfom_autotune picks one; 1..4: that tiling (see spfom_autotune),
                                 ENOTSUP at load when the instance does not allow it */
   void* stream;              /* cudaStream_t to run on; NULL (default): the ctx creates one */
 } spfom_params;
@@ -255,7 +255,10 @@ spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out);
  * iterations from the current duals, keeps the fastest, and restarts the
  * iteration from those duals. Candidates: precision 32: 1 = plain loads with
  * 4 products per lane, 2 = tiles staged by bulk copies with 8 products per
- * lane (when shared memory allows), 3 = plain loads with 8 products per lane;
+ * lane (when shared memory allows, not for batches: it copies the tiles of
+ * converged members too), 3 = plain loads with 8 products per lane, 4 = tiles
+ * streamed into shared memory by all threads of a block (coalesced loads and
+ * the margin gather ahead of the solves), 8 products per lane;
  * precision 64 with path 2: 1 = 8 products per lane at two 512-thread blocks per
  * SM, 2 = 8 per lane at three blocks per SM, 3 = 4 per lane at three blocks
  * per SM. *choice_out (or NULL) gets the choice (1 when there is none, as for

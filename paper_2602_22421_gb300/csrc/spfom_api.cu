@@ -352,7 +352,7 @@ spfom_status spfom_create(const spfom_params* p, spfom_ctx** out) {
   if (prm.precision != 64 && prm.precision != 32) return SPFOM_ENOTSUP;
   if (!(prm.batch_frac > 0.0) || !(prm.restart_beta >= 0.0) || !(prm.kkt_tol >= 0.0) || prm.tau0 < 0 ||
       prm.mu < 0 || !(prm.restart_tau_decay > 0.0) ||
-      !(prm.restart_tau_balance >= 0.0 && prm.restart_tau_balance <= 1.0) || prm.tiling < 0 || prm.tiling > 3)
+      !(prm.restart_tau_balance >= 0.0 && prm.restart_tau_balance <= 1.0) || prm.tiling < 0 || prm.tiling > 4)
     return SPFOM_EINVAL;
   spfom_ctx* ctx = new (std::nothrow) spfom_ctx;
   if (!ctx) return SPFOM_ENOMEM;
@@ -498,6 +498,15 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
         SPFOM_TRY(upload(ctx, &W.tile64_ptr, tiles.data(), tiles.size()));
         W.ntiles64 = nt;
       }
+      if (ctx->p.precision == 32 && spfom::coop_plan(n, kmax, ctx->sms, &plan)) {
+        // tiles of consecutive segments for the cooperatively staged binary32 kernel
+        const auto* sp = reinterpret_cast<const long long*>(I->seg_ptr);
+        const long long nt = spfom::make_tiles_lim(sp, L, plan.coop_segs, plan.coop_items, nullptr);
+        std::vector<long long> tiles((size_t)nt + 1);
+        spfom::make_tiles_lim(sp, L, plan.coop_segs, plan.coop_items, tiles.data());
+        SPFOM_TRY(upload(ctx, &W.coop_tile_ptr, tiles.data(), tiles.size()));
+        W.coop_ntiles = nt;
+      }
       if (ctx->p.precision == 32 && spfom::tma_plan(n, kmax, ctx->sms, &plan)) {
         // tiles of consecutive segments for the bulk-copy staging of the binary32 pass
         const long long nt = spfom::make_tiles(reinterpret_cast<const long long*>(I->seg_ptr), L, nullptr);
@@ -513,6 +522,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       W.inv_fx_scale = std::ldexp(1.0, -F);
       W.zparts_iter = std::max(std::max(plan.grid, plan.grid32), std::max(plan.pipe ? plan.pipe_grid : 0,
                                                                           plan.tma_ok ? plan.tma_grid : 0));
+      if (plan.coop_ok) W.zparts_iter = std::max(W.zparts_iter, plan.coop_grid);
       W.zparts_eval = plan.grid_eval;
       if (dd)
         for (int v = 1; v <= 3; ++v) {
@@ -522,11 +532,12 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       W.dd_ok = dd;
       if (ctx->p.tiling > 0) {  // a requested tiling of the active segment pass
         const int t = ctx->p.tiling;
-        bool ok = t <= 3;
+        bool ok = t <= 4;
         if (ok && ctx->p.precision == 32) {
-          ok = t != 2 || W.plan.tma_ok;
+          ok = (t != 2 || W.plan.tma_ok) && (t != 4 || W.plan.coop_ok);
           W.plan.tma = t == 2 ? 1 : 0;
           W.plan.f32_p8 = t == 3 ? 1 : 0;
+          W.plan.coop = t == 4 ? 1 : 0;
         } else if (ok) {
           ok = dd ? spfom::dd_variant_ok(W.plan, t) != 0 : t == 1;  // the binary64-sum kernel has one tiling
           if (dd) W.plan.dd_variant = t;
@@ -1074,12 +1085,21 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   // double-float binary64 pass: the tilings of k_seg_dd (1..3).
   const bool f32 = ctx->W.fast && ctx->W.v32 && ctx->cfg.f32;
   const bool dd = ctx->W.fast && ctx->W.v2 && !ctx->cfg.f32;
-  auto current = [&]() { return f32 ? (plan.tma ? 2 : (plan.f32_p8 ? 3 : 1)) : (dd ? plan.dd_variant : 1); };
-  auto available = [&](int c) { return f32 ? (c != 2 || plan.tma_ok) : (dd && spfom::dd_variant_ok(plan, c)); };
+  auto current = [&]() {
+    return f32 ? (plan.coop ? 4 : (plan.tma ? 2 : (plan.f32_p8 ? 3 : 1))) : (dd ? plan.dd_variant : 1);
+  };
+  // The staged kernel copies whole tiles even when a batch has frozen (converged)
+  // members, which the plain-load kernels skip; its early timing would not
+  // hold over a batched solve, so batches choose among the plain-load tilings.
+  auto available = [&](int c) {
+    if (f32) return c == 4 ? plan.coop_ok != 0 : (c != 2 || (plan.tma_ok && !ctx->W.batch));
+    return c <= 3 && dd && spfom::dd_variant_ok(plan, c);
+  };
   auto select = [&](int c) {
     if (f32) {
       plan.tma = c == 2 ? 1 : 0;
       plan.f32_p8 = c == 3 ? 1 : 0;
+      plan.coop = c == 4 ? 1 : 0;
     } else {
       plan.dd_variant = c;
     }
@@ -1098,7 +1118,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   ctx->cfg.kkt_tol = -1.0;  // no instance may converge (and stop working) while being timed
   double best = INFINITY;
   int choice = current();
-  for (int cand = 1; cand <= 3; ++cand) {
+  for (int cand = 1; cand <= 4; ++cand) {
     if (!available(cand)) continue;
     select(cand);
     drop_graphs(ctx);

@@ -92,6 +92,8 @@ struct FastPlan {
   int tma_grid;       // its blocks
   int tma_ok;         // 1 when the staged kernel is available (spfom_autotune may switch tma)
   int f32_p8;         // 1: the plain-load binary32 kernel runs 8 products per lane (W8 lanes)
+  int coop;           // 1: the binary32 pass runs the cooperatively staged kernel (tiling 4)
+  int coop_ok, coop_items, coop_segs, coop_smem, coop_grid;
   int dd_variant;     // tiling of k_seg_dd (1..3, see spfom_segments_dd.cu)
   int dd_grid[4];     // its grid per tiling (iterate), 0 = unavailable
   int dd_grid_eval[4];  // and for the evaluation pass
@@ -119,6 +121,8 @@ struct Work {
   float4* seg4;        // [L] (hi, lo) of lambda and of vt_0
   float2* marg2;       // [n] (hi, lo) of the margins (iterate)
   float2* marg2_eval;  // [n] (hi, lo) of the margins (evaluation)
+  long long* coop_tile_ptr;  // [coop_ntiles + 1] tiles of k_seg_f32_coop
+  long long coop_ntiles;
   bool dd_ok;          // k_seg_dd planned (path 0)
   double* z_seg;       // [L] per-segment values of spfom_evaluate
   double* zpart;       // per-block partial sums of z (iterate)
@@ -225,6 +229,10 @@ struct F32Args {
   const int* seg_inst;
   const int* inst_conv;
   double* z_seg;
+  // cooperative staging (k_seg_f32_coop)
+  const long long* coop_tile_ptr;
+  long long coop_ntiles;
+  int coop_items, coop_segs;
 };
 
 struct RunConfig {
@@ -264,6 +272,10 @@ cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatte
 cudaError_t launch_seg_dd(const DdArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s);
 cudaError_t launch_dd_prep(const Problem& P, float2* v2, float2* vt2, float4* seg4, cudaStream_t s);
 bool dd_setup(FastPlan* plan, int sms);
+// cooperatively staged binary32 kernel (spfom_segments_coop.cu)
+bool coop_plan(int n, int kmax, int sms, FastPlan* plan);
+long long make_tiles_lim(const long long* seg_ptr, long long L, int max_segs, int max_items, long long* tiles_out);
+cudaError_t launch_seg_f32_coop(const F32Args& A, const FastPlan& plan, cudaStream_t s);
 int dd_variant_ok(const FastPlan& plan, int v);
 cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s);
 bool tma_plan(int n, int kmax, int sms, FastPlan* plan);

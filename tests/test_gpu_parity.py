@@ -342,3 +342,20 @@ def test_pipeline_equals_plain_loads(name):
     np.testing.assert_array_equal(out[0][0], out[1][0])
     assert out[0][2]["restarts"] == out[1][2]["restarts"]
     assert out[0][2]["z_sum"] == pytest.approx(out[1][2]["z_sum"], rel=1e-13)
+
+
+@pytest.mark.parametrize("name", ["mid_small", "wide", "edge"])
+def test_fp32_cooperative_staging_equals_plain_loads(name):
+    """Tiling 4 (tiles streamed into shared memory by the whole block) runs the
+    same slot layout and summation order as tiling 3 (plain loads, 8 products
+    per lane): duals, sales and segment values agree bit for bit."""
+    inst = CASES[name]()
+    out = {}
+    for tiling in (3, 4):
+        with Solver(inst, precision=32, tiling=tiling) as s:
+            st = s.step(130)
+            out[tiling] = (s.duals(), s.vector(5), st)
+    np.testing.assert_array_equal(out[3][0], out[4][0])
+    np.testing.assert_array_equal(out[3][1], out[4][1])
+    assert out[3][2]["restarts"] == out[4][2]["restarts"]
+    assert out[3][2]["z_sum"] == pytest.approx(out[4][2]["z_sum"], rel=1e-6)
