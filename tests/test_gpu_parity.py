@@ -226,6 +226,33 @@ def test_full_size_mid_instance_first_iterations():
         assert dual == pytest.approx(ref["zsum"] + float(inst.c @ y), rel=1e-10)
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", [64, 32])
+def test_full_size_huge_instance_sampled(precision):
+    """The 1e7-segment, 2e8-nonzero GAM instance in the benchmark's launch
+    configuration: one iteration from y = 0 against the oracle's sweep (the
+    product sales and consumption it scatters), and the value of a seeded
+    sample of 4000 segments at a seeded dual point, each solved on its own by
+    the oracle."""
+    from instances import huge_gam
+    inst = huge_gam(2, workers=12)
+    o = Oracle(inst)
+    ref0 = o.sweep(np.zeros(inst.m))
+    y = seeded_duals(inst.m, 9, float(np.mean(inst.r)) / 4)
+    marg = o.margins(y)
+    sample = np.sort(np.random.default_rng(3).choice(inst.L, 4000, replace=False))
+    with Solver(inst, precision=precision) as s:
+        assert s.autotune(8) >= 1
+        s.reset()
+        s.step(1)
+        tol = ITER_RTOL if precision == 64 else 1e-5
+        assert nrel(s.vector(5), ref0["s"]) <= tol
+        assert nrel(s.vector(4), ref0["g"]) <= tol
+        _, z = s.evaluate(y, per_segment=True)
+    want = np.array([o.segment_solve(int(l), marg)[0] for l in sample])
+    np.testing.assert_allclose(z[sample], want, rtol=VALUE_RTOL, atol=VALUE_RTOL * np.abs(want).max())
+
+
 def _bad(mut):
     inst = tiny_mnl(0)
     inst.v = inst.v.copy()
