@@ -255,10 +255,11 @@ spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out);
  * iterations from the current duals, keeps the fastest, and restarts the
  * iteration from those duals. Candidates: precision 32: 1 = plain loads with
  * 4 products per lane, 2 = tiles staged by bulk copies with 8 products per
- * lane (when shared memory allows, not for batches: it copies the tiles of
- * converged members too), 3 = plain loads with 8 products per lane, 4 = tiles
- * streamed into shared memory by all threads of a block (coalesced loads and
- * the margin gather ahead of the solves), 8 products per lane;
+ * lane (when shared memory allows), 3 = plain loads with 8 products per lane,
+ * 4 = tiles streamed into shared memory by all threads of a block (coalesced
+ * loads and the margin gather ahead of the solves), 8 products per lane --
+ * batches choose between 1 and 3 (the staged kernels load the tiles of
+ * converged members too);
  * precision 64 with path 2: 1 = 8 products per lane at two 512-thread blocks per
  * SM, 2 = 8 per lane at three blocks per SM, 3 = 4 per lane at three blocks
  * per SM. *choice_out (or NULL) gets the choice (1 when there is none, as for

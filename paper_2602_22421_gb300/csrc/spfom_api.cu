@@ -550,6 +550,8 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       if (plan.scatter == 1)
         SPFOM_TRY(dalloc(ctx, &W.part, (size_t)W.zparts_iter * (size_t)(n > 0 ? n : 1)));
       SPFOM_TRY(dalloc(ctx, &W.s_fx, (size_t)n));
+      SPFOM_TRY(dalloc(ctx, &W.rprev, (size_t)(L > 0 ? L : 1)));
+      SPFOM_CUDA(ctx, cudaMemsetAsync(W.rprev, 0, sizeof(float) * (size_t)(L > 0 ? L : 1), ctx->stream));
     }
     if (W.fast && W.dd_ok) {
       // double-float images for k_seg_dd (the precision-64 iteration and every evaluation pass)
@@ -1088,11 +1090,12 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   auto current = [&]() {
     return f32 ? (plan.coop ? 4 : (plan.tma ? 2 : (plan.f32_p8 ? 3 : 1))) : (dd ? plan.dd_variant : 1);
   };
-  // The staged kernel copies whole tiles even when a batch has frozen (converged)
-  // members, which the plain-load kernels skip; its early timing would not
-  // hold over a batched solve, so batches choose among the plain-load tilings.
+  // The staged kernels (2, 4) load whole tiles even when a batch has frozen
+  // (converged) members, which the plain-load kernels skip; their early timing
+  // would not hold over a batched solve, so batches choose among the plain-load
+  // tilings.
   auto available = [&](int c) {
-    if (f32) return c == 4 ? plan.coop_ok != 0 : (c != 2 || (plan.tma_ok && !ctx->W.batch));
+    if (f32) return c == 4 ? (plan.coop_ok != 0 && !ctx->W.batch) : (c != 2 || (plan.tma_ok && !ctx->W.batch));
     return c <= 3 && dd && spfom::dd_variant_ok(plan, c);
   };
   auto select = [&](int c) {

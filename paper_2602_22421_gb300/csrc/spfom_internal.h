@@ -121,6 +121,7 @@ struct Work {
   float4* seg4;        // [L] (hi, lo) of lambda and of vt_0
   float2* marg2;       // [n] (hi, lo) of the margins (iterate)
   float2* marg2_eval;  // [n] (hi, lo) of the margins (evaluation)
+  float* rprev;        // [L] last binary32 Dinkelbach ratio of every segment (start of the next solve)
   long long* coop_tile_ptr;  // [coop_ntiles + 1] tiles of k_seg_f32_coop
   long long coop_ntiles;
   bool dd_ok;          // k_seg_dd planned (path 0)
@@ -176,6 +177,7 @@ struct FastArgs {
   const int* seg_inst;
   const int* inst_conv;
   double* z_seg;
+  float* rprev;  // [L] each segment's last Dinkelbach ratio (iterate passes), or null: start at 0
 };
 
 // Arguments of k_seg_dd (spfom_segments_dd.cu): double-float images, and the
@@ -233,6 +235,7 @@ struct F32Args {
   const long long* coop_tile_ptr;
   long long coop_ntiles;
   int coop_items, coop_segs;
+  float* rprev;  // [L] each segment's last Dinkelbach ratio, or null: start at 0
 };
 
 struct RunConfig {

@@ -429,12 +429,13 @@ cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfi
   if (cfg.f32 && Wk.v32) {
     F32Args A{P.seg_ptr, P.seg_prod, Wk.v32, Wk.vt32, Wk.lam32, Wk.vt0_32, P.L, P.n, Wk.fx_bits, Wk.marg32,
               Wk.part, Wk.s_fx, Wk.zpart, Wk.st, Wk.tile_ptr, Wk.ntiles, Wk.plan.acc_bytes, Wk.st,
-              seg_inst, conv, z_seg, Wk.coop_tile_ptr, Wk.coop_ntiles, Wk.plan.coop_items, Wk.plan.coop_segs};
+              seg_inst, conv, z_seg, Wk.coop_tile_ptr, Wk.coop_ntiles, Wk.plan.coop_items, Wk.plan.coop_segs,
+              Wk.rprev};
     *zparts_out = Wk.plan.coop ? Wk.plan.coop_grid : (Wk.plan.tma ? Wk.plan.tma_grid : Wk.plan.grid32);
     return launch_seg_f32(A, Wk.plan, s);
   }
   FastArgs A{P, marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, Wk.s_fx,
-             Wk.tile64_ptr, Wk.ntiles64, Wk.plan.pipe_acc_bytes, Wk.st, seg_inst, conv, z_seg};
+             Wk.tile64_ptr, Wk.ntiles64, Wk.plan.pipe_acc_bytes, Wk.st, seg_inst, conv, z_seg, Wk.rprev};
   if (Wk.plan.pipe && !Wk.batch) {
     *zparts_out = Wk.plan.pipe_grid;
     return launch_seg_fast_pipe(A, Wk.plan, s);

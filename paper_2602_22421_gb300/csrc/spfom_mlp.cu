@@ -41,7 +41,7 @@ namespace {
 
 constexpr int kF = SPFOM_MLP_FEATURES;
 constexpr int kH = SPFOM_MLP_HIDDEN;
-constexpr int kBM = 128, kBK = 64, kStages = 4, kThreads = 128;
+constexpr int kBM = 128, kBK = 64, kThreads = 128;
 constexpr int kOutPad = 16;  // the output layer runs as a 16-column product (column 0 used)
 constexpr int kKPad = 64;    // products with K = 16 read operands padded to one 64-wide TMA box
 
@@ -135,6 +135,9 @@ struct GemmShape {
   static constexpr int kA = kBM * kBK * 2;  // bytes of an A stage (16 KB)
   static constexpr int kB = BN * kBK * 2;   // bytes of a B stage
   static constexpr int kStage = kA + kB;
+  // two stages for the wide tile keep two CTAs (2 x 256 TMEM columns) per SM,
+  // so one CTA's epilogue overlaps the other's loads and MMAs
+  static constexpr int kStages = BN >= 256 ? 2 : 4;
   static constexpr int kSmem = kStages * kStage + 1024;  // + alignment slack
   static constexpr uint32_t kCols = BN < 32 ? 32 : BN;   // TMEM columns (power of two >= 32)
   static_assert(kStage % 1024 == 0, "stages must keep the 1024-byte swizzle alignment");
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   using S = GemmShape<BN>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ __align__(8) unsigned long long full[kStages], empty[kStages], done;
+  __shared__ __align__(8) unsigned long long full[S::kStages], empty[S::kStages], done;
   __shared__ uint32_t tmem_base;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * kBM;
@@ -160,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int nkt = max(0, min(KT, kt0 + E.ksplit) - kt0);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages; ++s) {
+    for (int s = 0; s < S::kStages; ++s) {
       mbar_init(smem_addr(&full[s]), 1);
       mbar_init(smem_addr(&empty[s]), 1);
     }
@@ -177,18 +180,18 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0 && nkt > 0) {
     const uint32_t idesc = idesc_bf16(kBM, BN);
     auto load = [&](int i) {
-      const int s = i % kStages;
+      const int s = i % S::kStages;
       const uint32_t a = smem_addr(base + s * S::kStage), fb = smem_addr(&full[s]);
       mbar_expect_tx(fb, S::kStage);
       tma_load_2d(a, &ta, (kt0 + i) * kBK, m0, fb);
       tma_load_2d(a + S::kA, &tb, (kt0 + i) * kBK, 0, fb);
     };
-    const int pre = nkt < kStages ? nkt : kStages;
+    const int pre = nkt < S::kStages ? nkt : S::kStages;
     for (int i = 0; i < pre; ++i) load(i);
     int issued = pre, consumed = 0;
     for (int i = 0; i < nkt; ++i) {
-      const int s = i % kStages;
-      if (!mbar_wait_bounded(smem_addr(&full[s]), (unsigned)(i / kStages) & 1u)) {
+      const int s = i % S::kStages;
+      if (!mbar_wait_bounded(smem_addr(&full[s]), (unsigned)(i / S::kStages) & 1u)) {
         ok = 0;
         break;
       }
@@ -201,20 +204,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         umma_bf16(tmem, sdesc_sw128(a + kk * 32), sdesc_sw128(b + kk * 32), idesc, (i > 0 || kk > 0) ? 1u : 0u);
       umma_commit(smem_addr(&empty[s]));
       // refill the stage of the previous tile once its MMAs have read it
-      if (i >= 1 && i - 1 + kStages < nkt) {
+      if (i >= 1 && i - 1 + S::kStages < nkt) {
         const int p = i - 1;
-        if (!mbar_wait_bounded(smem_addr(&empty[p % kStages]), (unsigned)(p / kStages) & 1u)) {
+        if (!mbar_wait_bounded(smem_addr(&empty[p % S::kStages]), (unsigned)(p / S::kStages) & 1u)) {
           ok = 0;
           break;
         }
-        load(p + kStages);
+        load(p + S::kStages);
         ++issued;
       }
     }
     umma_commit(smem_addr(&done));
     if (!ok) {
       // let the copies still in flight land before the CTA can exit
-      for (int i = consumed; i < issued; ++i) mbar_wait_bounded(smem_addr(&full[i % kStages]), (unsigned)(i / kStages) & 1u);
+      for (int i = consumed; i < issued; ++i) mbar_wait_bounded(smem_addr(&full[i % S::kStages]), (unsigned)(i / S::kStages) & 1u);
       atomicExch(E.error, 1);
     }
   }

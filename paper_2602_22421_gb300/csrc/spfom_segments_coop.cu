@@ -119,9 +119,9 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32_coop(F32Args A) {
         }
       }
       const float lam = s_lam[ls], vt0 = s_vt0[ls];
-      float R = 0.f, Nsel = 0.f, Dsel = 0.f;
+      float R = A.rprev ? A.rprev[l] : 0.f, Nsel = 0.f, Dsel = 0.f;  // as k_seg_f32
       unsigned sel = 0xffffffffu;
-      for (int it = 0; it < P * W + 2; ++it) {
+      for (int it = 0; it < P * W + 3; ++it) {
         unsigned s = 0;
         float N = 0.f, D = 0.f;
 #pragma unroll
@@ -137,11 +137,12 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32_coop(F32Args A) {
           N += __shfl_xor_sync(gmask, N, o, W);
           D += __shfl_xor_sync(gmask, D, o, W);
         }
-        R = N / (vt0 + D);
+        R = __fdividef(N, vt0 + D);
         sel = s;
         Nsel = N;
         Dsel = D;
       }
+      if (A.rprev && lane == 0) A.rprev[l] = R;
       const float q = lam / (vt0 + Dsel);
       if (lane == 0) {
         if (A.z_seg) A.z_seg[l] = (double)(q * Nsel);

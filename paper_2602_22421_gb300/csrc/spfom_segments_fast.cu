@@ -91,11 +91,14 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
     }
     const double lam = Pr.lam[l], vt0 = Pr.vt0[l];
     const float vt0f = f32_trunc(vt0, ok);
-    // Dinkelbach in binary32 from R = 0.
-    float R = 0.f;
+    // Dinkelbach in binary32, started at the segment's ratio of the previous
+    // iteration (any start reaches a fixed point, and every fixed point is
+    // optimal; the margins move little between iterations, so this one is
+    // usually confirmed by the second pass).
+    float R = A.rprev ? A.rprev[l] : 0.f;
     unsigned sel = 0xffffffffu;  // no previous set
     bool conv = false;
-    for (int it = 0; it < P * W + 2; ++it) {
+    for (int it = 0; it < P * W + 3; ++it) {
       unsigned s = 0;
       float N = 0.f, D = 0.f;
 #pragma unroll
@@ -114,9 +117,10 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
         N += __shfl_xor_sync(gmask, N, o, W);
         D += __shfl_xor_sync(gmask, D, o, W);
       }
-      R = N / (vt0f + D);
+      R = __fdividef(N, vt0f + D);
       sel = s;
     }
+    if (A.rprev && lane == 0 && conv) A.rprev[l] = R;
     bool good = ok && conv;
 #pragma unroll
     for (int p = 0; p < P; ++p)
@@ -242,9 +246,9 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
         }
       }
     const float lam = A.lam32[l], vt0 = A.vt0_32[l];
-    float R = 0.f, Nsel = 0.f, Dsel = 0.f;
+    float R = A.rprev ? A.rprev[l] : 0.f, Nsel = 0.f, Dsel = 0.f;  // Dinkelbach from the last ratio
     unsigned sel = 0xffffffffu;
-    for (int it = 0; it < P * W + 2; ++it) {
+    for (int it = 0; it < P * W + 3; ++it) {
       unsigned s = 0;
       float N = 0.f, D = 0.f;
 #pragma unroll
@@ -260,11 +264,12 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
         N += __shfl_xor_sync(gmask, N, o, W);
         D += __shfl_xor_sync(gmask, D, o, W);
       }
-      R = N / (vt0 + D);
+      R = __fdividef(N, vt0 + D);
       sel = s;
       Nsel = N;
       Dsel = D;
     }
+    if (A.rprev && lane == 0) A.rprev[l] = R;
     const float q = lam / (vt0 + Dsel);
     if (lane == 0) {
       if (A.z_seg) A.z_seg[l] = (double)(q * Nsel);
