@@ -102,7 +102,7 @@ typedef struct {
                                 nonzero read and written each iteration); needs precision 64,
                                 batch_frac 1 and a single instance, and runs the general kernel */
   int32_t tiling;            /* 0 (default): tiling 1 of the active segment pass until
-                                spfom_autotune picks one; 1..4: that tiling (see spfom_autotune),
+                                spfom_autotune picks one; 1..5: that tiling (see spfom_autotune),
                                 ENOTSUP at load when the instance does not allow it */
   void* stream;              /* cudaStream_t to run on; NULL (default): the ctx creates one */
 } spfom_params;
@@ -257,7 +257,8 @@ spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out);
  * 4 products per lane, 2 = tiles staged by bulk copies with 8 products per
  * lane (when shared memory allows), 3 = plain loads with 8 products per lane,
  * 4 = tiles streamed into shared memory by all threads of a block (coalesced
- * loads and the margin gather ahead of the solves), 8 products per lane --
+ * loads and the margin gather ahead of the solves), 8 products per lane,
+ * 5 = plain loads with 16 products per lane (one lane per set of <= 16) --
  * batches choose between 1 and 3 (the staged kernels load the tiles of
  * converged members too);
  * precision 64 with path 2: 1 = 8 products per lane at two 512-thread blocks per

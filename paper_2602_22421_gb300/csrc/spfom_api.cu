@@ -352,7 +352,7 @@ spfom_status spfom_create(const spfom_params* p, spfom_ctx** out) {
   if (prm.precision != 64 && prm.precision != 32) return SPFOM_ENOTSUP;
   if (!(prm.batch_frac > 0.0) || !(prm.restart_beta >= 0.0) || !(prm.kkt_tol >= 0.0) || prm.tau0 < 0 ||
       prm.mu < 0 || !(prm.restart_tau_decay > 0.0) ||
-      !(prm.restart_tau_balance >= 0.0 && prm.restart_tau_balance <= 1.0) || prm.tiling < 0 || prm.tiling > 4)
+      !(prm.restart_tau_balance >= 0.0 && prm.restart_tau_balance <= 1.0) || prm.tiling < 0 || prm.tiling > 5)
     return SPFOM_EINVAL;
   spfom_ctx* ctx = new (std::nothrow) spfom_ctx;
   if (!ctx) return SPFOM_ENOMEM;
@@ -532,12 +532,13 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       W.dd_ok = dd;
       if (ctx->p.tiling > 0) {  // a requested tiling of the active segment pass
         const int t = ctx->p.tiling;
-        bool ok = t <= 4;
+        bool ok = t <= 5;
         if (ok && ctx->p.precision == 32) {
           ok = (t != 2 || W.plan.tma_ok) && (t != 4 || W.plan.coop_ok);
           W.plan.tma = t == 2 ? 1 : 0;
           W.plan.f32_p8 = t == 3 ? 1 : 0;
           W.plan.coop = t == 4 ? 1 : 0;
+          W.plan.f32_p16 = t == 5 ? 1 : 0;
         } else if (ok) {
           ok = dd ? spfom::dd_variant_ok(W.plan, t) != 0 : t == 1;  // the binary64-sum kernel has one tiling
           if (dd) W.plan.dd_variant = t;
@@ -1088,7 +1089,8 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   const bool f32 = ctx->W.fast && ctx->W.v32 && ctx->cfg.f32;
   const bool dd = ctx->W.fast && ctx->W.v2 && !ctx->cfg.f32;
   auto current = [&]() {
-    return f32 ? (plan.coop ? 4 : (plan.tma ? 2 : (plan.f32_p8 ? 3 : 1))) : (dd ? plan.dd_variant : 1);
+    return f32 ? (plan.f32_p16 ? 5 : (plan.coop ? 4 : (plan.tma ? 2 : (plan.f32_p8 ? 3 : 1))))
+               : (dd ? plan.dd_variant : 1);
   };
   // The staged kernels (2, 4) load whole tiles even when a batch has frozen
   // (converged) members, which the plain-load kernels skip; their early timing
@@ -1103,6 +1105,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
       plan.tma = c == 2 ? 1 : 0;
       plan.f32_p8 = c == 3 ? 1 : 0;
       plan.coop = c == 4 ? 1 : 0;
+      plan.f32_p16 = c == 5 ? 1 : 0;
     } else {
       plan.dd_variant = c;
     }
@@ -1121,7 +1124,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   ctx->cfg.kkt_tol = -1.0;  // no instance may converge (and stop working) while being timed
   double best = INFINITY;
   int choice = current();
-  for (int cand = 1; cand <= 4; ++cand) {
+  for (int cand = 1; cand <= 5; ++cand) {
     if (!available(cand)) continue;
     select(cand);
     drop_graphs(ctx);

@@ -92,6 +92,8 @@ struct FastPlan {
   int tma_grid;       // its blocks
   int tma_ok;         // 1 when the staged kernel is available (spfom_autotune may switch tma)
   int f32_p8;         // 1: the plain-load binary32 kernel runs 8 products per lane (W8 lanes)
+  int f32_p16;        // 1: it runs 16 products per lane (W16 lanes: one lane per set of <= 16)
+  int W16;            // lanes per segment with 16 products per lane (1 or 2)
   int coop;           // 1: the binary32 pass runs the cooperatively staged kernel (tiling 4)
   int coop_ok, coop_items, coop_segs, coop_smem, coop_grid;
   int dd_variant;     // tiling of k_seg_dd (1..3, see spfom_segments_dd.cu)

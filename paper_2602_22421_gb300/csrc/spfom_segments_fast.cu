@@ -513,6 +513,16 @@ cudaError_t launch_f32_w(const F32Args& A, int W, int grid, int smem, cudaStream
 }
 
 template <int SC>
+cudaError_t launch_f32_p16(const F32Args& A, int W16, int grid, int smem, cudaStream_t s) {
+  switch (W16) {  // 16 products per lane
+    case 1: k_seg_f32<1, 16, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 2: k_seg_f32<2, 16, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <int SC>
 cudaError_t launch_f32_p8(const F32Args& A, int W8, int grid, int smem, cudaStream_t s) {
   switch (W8) {  // 8 products per lane
     case 1: k_seg_f32<1, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
@@ -576,11 +586,14 @@ bool fast_plan(int n, int kmax, int sms, FastPlan* plan) {
   const int nb32 = occupancy(W, sc, smem, true);
   const int nbe = occupancy(W8, 0, 0, false);
   if (nb <= 0 || nbe <= 0 || nb32 <= 0) return false;
-  if (sc == 1) {  // the 8-products-per-lane binary32 variant shares the grid of the 4-per-lane one
+  if (sc == 1) {  // the 8- and 16-products-per-lane binary32 variants share the grid of the 4-per-lane one
     cudaFuncSetAttribute(k_seg_f32<1, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_seg_f32<2, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_seg_f32<4, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_seg_f32<1, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_seg_f32<2, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   }
+  plan->W16 = kmax <= 16 ? 1 : 2;
   plan->W = W;
   plan->W8 = W8;
   plan->scatter = sc;
@@ -603,6 +616,9 @@ cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t 
   if (plan.tma)
     return plan.scatter == 1 ? launch_tma_w<1>(A, plan.tma_W, plan.tma_grid, plan.tma_smem, s)
                              : launch_tma_w<2>(A, plan.tma_W, plan.tma_grid, plan.tma_smem, s);
+  if (plan.f32_p16)
+    return plan.scatter == 1 ? launch_f32_p16<1>(A, plan.W16, plan.grid32, plan.smem, s)
+                             : launch_f32_p16<2>(A, plan.W16, plan.grid32, 0, s);
   if (plan.f32_p8)
     return plan.scatter == 1 ? launch_f32_p8<1>(A, plan.W8, plan.grid32, plan.smem, s)
                              : launch_f32_p8<2>(A, plan.W8, plan.grid32, 0, s);

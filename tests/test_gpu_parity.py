@@ -388,3 +388,17 @@ def test_fp32_cooperative_staging_equals_plain_loads(name):
     np.testing.assert_array_equal(out[3][1], out[4][1])
     assert out[3][2]["restarts"] == out[4][2]["restarts"]
     assert out[3][2]["z_sum"] == pytest.approx(out[4][2]["z_sum"], rel=1e-6)
+
+
+@pytest.mark.parametrize("tiling", [1, 3, 5])
+def test_fp32_tilings_solve_to_the_binary64_objective(tiling):
+    """Each plain-load binary32 tiling (4, 8 or 16 products per lane) solves
+    the mid-size instance to KKT <= 1e-4 (with binary64 polish) at the
+    binary64 solve's objective."""
+    inst = mid_small()
+    with Solver(inst) as s:
+        ref = s.solve()
+    with Solver(inst, precision=32, tiling=tiling) as s:
+        st = s.solve()
+    assert st["converged"] == 1 and st["kkt"] <= 1e-4
+    assert st["dual_avg"] == pytest.approx(ref["dual_avg"], rel=1e-4)
