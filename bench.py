@@ -162,19 +162,32 @@ def kernel_traffic(kernel, src, nnz):
 
 def cpu_baseline(inst, seconds):
     """The FP64 oracle as it stands, single thread, full iterations of the
-    same instance for about `seconds` (at least 2 iterations)."""
+    same instance for about `seconds` (at least 2 iterations); and its
+    OpenMP timing build (segments over all host cores) for a third of that."""
     from oracle import Oracle, Params
-    run = Oracle(inst).run(Params(kkt_tol=0.0))
-    run.step(1)
-    t0, it = time.perf_counter(), 0
-    while True:
+
+    def rate(omp, secs):
+        run = Oracle(inst, omp=omp).run(Params(kkt_tol=0.0))
         run.step(1)
-        it += 1
-        el = time.perf_counter() - t0
-        if (el >= seconds and it >= 2) or el >= 3 * seconds:
-            break
-    return {"value": it / el, "unit": "iters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{it} full iterations of the {inst.L}-segment instance ({el:.1f} s, single thread)"}
+        t0, it = time.perf_counter(), 0
+        while True:
+            run.step(1)
+            it += 1
+            el = time.perf_counter() - t0
+            if (el >= secs and it >= 2) or el >= 3 * secs:
+                return it, el
+
+    it, el = rate(False, seconds)
+    out = {"value": it / el, "unit": "iters/s", "cores": 1, "kind": "oracle",
+           "sample": f"{it} full iterations of the {inst.L}-segment instance ({el:.1f} s, single thread)"}
+    try:
+        it2, el2 = rate(True, seconds / 3)
+        out["all_cores"] = {"value": it2 / el2, "unit": "iters/s", "cores": os.cpu_count(),
+                            "kind": "oracle, OpenMP timing build (segments over all cores)",
+                            "sample": f"{it2} full iterations ({el2:.1f} s)"}
+    except Exception as e:  # the timing build needs gcc's OpenMP; the single-thread number stands alone
+        out["all_cores"] = {"unavailable": str(e)[:200]}
+    return out
 
 
 def pinned_arrays(inst):
@@ -426,6 +439,17 @@ def huge_leg(args, stream, local):
     sv.close()
     # the binary64 time to 1e-4 at the measured iteration rate (same iteration count as the binary32 solve)
     out["f64"]["time_to_kkt_1e-4_at_f32_iterations_s"] = st["iters"] * out["f64"]["ms_per_iter"] * 1e-3
+    # the oracle on one host core: two full iterations, and its time to 1e-4 extrapolated with the
+    # GPU solve's iteration count (same iterates)
+    if not args.no_cpu_baseline:
+        from oracle import Oracle, Params
+        run = Oracle(inst).run(Params(kkt_tol=0.0))
+        t0 = time.perf_counter()
+        run.step(2)
+        per = (time.perf_counter() - t0) / 2
+        out["cpu_baseline"] = {"seconds_per_iteration": per, "cores": 1, "kind": "oracle",
+                               "sample": "2 full iterations of the 1e7-segment instance, single thread",
+                               "time_to_kkt_1e-4_extrapolated_s": per * st["iters"]}
     return out
 
 

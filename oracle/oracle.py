@@ -22,21 +22,25 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "spfom_oracle.c")
 LIB = os.path.join(HERE, "liboracle.so")
+LIB_OMP = os.path.join(HERE, "liboracle_omp.so")
 
 _f64p = C.POINTER(C.c_double)
 _i32p = C.POINTER(C.c_int32)
 _i64p = C.POINTER(C.c_int64)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle into ``oracle/liboracle.so`` (plain gcc, no SIMD)."""
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
-        return LIB
-    tmp = f"{LIB}.{os.getpid()}.tmp"
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile the oracle into ``oracle/liboracle.so`` (plain gcc, no SIMD);
+    ``omp=True``: the timing build ``liboracle_omp.so`` (segments over all
+    host cores; another summation order, never used for parity)."""
+    lib = LIB_OMP if omp else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(SRC):
+        return lib
+    tmp = f"{lib}.{os.getpid()}.tmp"
     subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
-                           "-fno-fast-math", "-o", tmp, SRC, "-lm"])
-    os.replace(tmp, LIB)
-    return LIB
+                           "-fno-fast-math", *(["-fopenmp"] if omp else []), "-o", tmp, SRC, "-lm"])
+    os.replace(tmp, lib)
+    return lib
 
 
 class _Inst(C.Structure):
@@ -62,13 +66,12 @@ class _State(C.Structure):
                 ("primal_avg", C.c_double), ("evals", C.c_int64), ("converged", C.c_int32)]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        h = C.CDLL(build())
+def lib(omp: bool = False):
+    if omp not in _libs:
+        h = C.CDLL(build(omp=omp))
         P = C.POINTER
         h.orc_margins.argtypes = [P(_Inst), _f64p, _f64p]
         h.orc_segment_solve.argtypes = [P(_Inst), C.c_int64, _f64p, _f64p, _i32p]
@@ -89,8 +92,8 @@ def lib():
         h.orc_run.restype = C.c_int
         h.orc_recover.argtypes = [P(_Inst), _f64p, _f64p, _i32p]
         h.orc_recover.restype = None
-        _lib = h
-    return _lib
+        _libs[omp] = h
+    return _libs[omp]
 
 
 def _p(a, t):
@@ -121,7 +124,8 @@ class Params:
 class Oracle:
     """FP64 oracle bound to one instance (arrays are kept alive here)."""
 
-    def __init__(self, inst):
+    def __init__(self, inst, omp: bool = False):
+        """omp=True binds the all-core timing build (not for parity)."""
         self.inst = inst
         self._keep = dict(
             r=np.ascontiguousarray(inst.r, np.float64), c=np.ascontiguousarray(inst.c, np.float64),
@@ -137,7 +141,7 @@ class Oracle:
                         _p(k["a_idx"], _i32p), _p(k["a_val"], _f64p), _p(k["seg_ptr"], _i64p),
                         _p(k["seg_prod"], _i32p), _p(k["v"], _f64p), _p(k["w"], _f64p), _p(k["lam"], _f64p),
                         _p(k["v0"], _f64p))
-        self._lib = lib()
+        self._lib = lib(omp)
 
     # --- a1 / a2 ---------------------------------------------------------
     def margins(self, y) -> np.ndarray:

@@ -46,6 +46,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 typedef struct {
   int32_t n, m;
@@ -456,6 +459,27 @@ static void evaluate(const orc_instance* I, const orc_params* P, orc_state* S) {
  *      mu = 0 gives the step of Algorithm 2);
  *   a5 epoch sums: sum_y += y^{t-1}, sum_g += g, sum_P += P (solver addition);
  *   a6 every eval_every iterations, KKT of the averages and the restart test. */
+/* One segment of iteration t: its response (solved if drawn, else the stale
+ * one), added to the product sales s_acc and, with sum_x, to the epoch sums;
+ * returns z_l when solved (0 otherwise). */
+static double segment_step(const orc_instance* I, const orc_params* P, orc_state* S, int64_t l, int64_t t,
+                           int full, const double* marg, double* xbuf, double* s_acc) {
+  int64_t b = I->seg_ptr[l], e = I->seg_ptr[l + 1];
+  double z = 0.0;
+  if (full || sampled(P, t, l)) {
+    z = orc_segment_solve(I, l, marg, xbuf, NULL);
+    if (!full)
+      for (int64_t p = b; p < e; ++p) S->x_cur[p] = xbuf[p - b];
+  }
+  for (int64_t p = b; p < e; ++p) s_acc[I->seg_prod[p]] += full ? xbuf[p - b] : S->x_cur[p];
+  if (S->sum_x) /* the first iteration of an epoch starts the sums afresh */
+    for (int64_t p = b; p < e; ++p) {
+      double x = full ? xbuf[p - b] : S->x_cur[p];
+      S->sum_x[p] = S->count == 0 ? x : S->sum_x[p] + x;
+    }
+  return z;
+}
+
 int orc_run(const orc_instance* I, const orc_params* P, orc_state* S, int64_t iters) {
   int32_t n = I->n, m = I->m;
   double* marg = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
@@ -474,20 +498,27 @@ int orc_run(const orc_instance* I, const orc_params* P, orc_state* S, int64_t it
     orc_margins(I, S->y, marg);
     double zsum = 0.0;
     for (int32_t j = 0; j < n; ++j) S->s[j] = 0.0;
-    for (int64_t l = 0; l < I->L; ++l) {
-      int64_t b = I->seg_ptr[l], e = I->seg_ptr[l + 1];
-      if (full || sampled(P, t, l)) {
-        zsum += orc_segment_solve(I, l, marg, xbuf, NULL);
-        if (!full)
-          for (int64_t p = b; p < e; ++p) S->x_cur[p] = xbuf[p - b];
+#ifdef _OPENMP
+    /* Timing build only (liboracle_omp.so): segments split over the host's
+     * cores, per-thread sales summed in thread order afterwards -- a
+     * different summation order, so never used for parity. */
+    {
+      int nt = omp_get_max_threads();
+      double* sl = (double*)calloc((size_t)nt * (size_t)(n > 0 ? n : 1), sizeof(double));
+#pragma omp parallel reduction(+ : zsum)
+      {
+        double xb[ORC_KMAX];
+        double* my = sl + (size_t)omp_get_thread_num() * (size_t)(n > 0 ? n : 1);
+#pragma omp for schedule(static)
+        for (int64_t l = 0; l < I->L; ++l) zsum += segment_step(I, P, S, l, t, full, marg, xb, my);
       }
-      for (int64_t p = b; p < e; ++p) S->s[I->seg_prod[p]] += full ? xbuf[p - b] : S->x_cur[p];
-      if (S->sum_x)  /* the first iteration of an epoch starts the sums afresh */
-        for (int64_t p = b; p < e; ++p) {
-          double x = full ? xbuf[p - b] : S->x_cur[p];
-          S->sum_x[p] = S->count == 0 ? x : S->sum_x[p] + x;
-        }
+      for (int k = 0; k < nt; ++k)
+        for (int32_t j = 0; j < n; ++j) S->s[j] += sl[(size_t)k * (size_t)n + j];
+      free(sl);
     }
+#else
+    for (int64_t l = 0; l < I->L; ++l) zsum += segment_step(I, P, S, l, t, full, marg, xbuf, S->s);
+#endif
     double Pv;
     aggregate(I, S->s, S->g, &Pv);
     double cy = 0.0;
