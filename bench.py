@@ -160,6 +160,26 @@ def kernel_traffic(kernel, src, nnz):
     return d["dram_bytes_per_launch"] * nnz / d["nnz"], d.get("capture")
 
 
+def host_cpu() -> str:
+    """CPU model and core count of this host (lscpu, else /proc/cpuinfo)."""
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model and os.path.exists("/proc/cpuinfo"):
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    import platform
+    return f"{model or platform.machine()}, {os.cpu_count()} cores"
+
+
 def cpu_baseline(inst, seconds):
     """The FP64 oracle as it stands, single thread, full iterations of the
     same instance for about `seconds` (at least 2 iterations); and its
@@ -179,7 +199,8 @@ def cpu_baseline(inst, seconds):
 
     it, el = rate(False, seconds)
     out = {"value": it / el, "unit": "iters/s", "cores": 1, "kind": "oracle",
-           "sample": f"{it} full iterations of the {inst.L}-segment instance ({el:.1f} s, single thread)"}
+           "sample": f"{it} full iterations of the {inst.L}-segment instance ({el:.1f} s, single thread)",
+           "host": host_cpu()}
     try:
         it2, el2 = rate(True, seconds / 3)
         out["all_cores"] = {"value": it2 / el2, "unit": "iters/s", "cores": os.cpu_count(),

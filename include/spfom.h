@@ -158,6 +158,13 @@ typedef struct {
                                   was not certified and was redone in binary64 */
   int32_t fast_path;           /* 1 when the certified-decision kernel runs the iterations */
   int32_t iter_precision;      /* 32 or 64: precision of the last iteration's segment pass */
+  int64_t stall_iters;         /* spfom_solve: iterations since the evaluated dual objective
+                                  Dual(ybar) last improved by more than 1e-9 relative -- the
+                                  paper's stopping rule (Section 4.5) ends a run when the
+                                  objective has not changed for L/100 iterations; logged here,
+                                  the KKT test decides convergence */
+  int32_t stagnated;           /* spfom_solve: 1 once stall_iters >= L / 100 (logged only) */
+  int32_t pad2_;
 } spfom_stats;
 
 /* Which vector spfom_vector() returns. */

@@ -794,11 +794,23 @@ spfom_status spfom_solve(spfom_ctx* ctx, const double* y0, spfom_stats* out) {
   spfom_stats st{};
   double secs = 0.0, seg = 0.0;
   long long segl = 0, launches = 0;
+  // the paper's stagnation rule, logged: iterations since the evaluated dual objective last improved
+  double best_dual = INFINITY;
+  long long last_improved = 0;
+  const long long stall_limit = std::max(1LL, (long long)(ctx->P.L / 100));
   for (;;) {
     long long left = ctx->p.max_iters - ctx->host_t;
     if (left <= 0) break;
     s = spfom_step(ctx, left < E ? left : E, &st);
     if (s != SPFOM_OK) return s;
+    if (st.evals > 0 && std::isfinite(st.dual_avg)) {
+      if (!(st.dual_avg >= best_dual - 1e-9 * std::fabs(best_dual))) {
+        best_dual = st.dual_avg;
+        last_improved = st.iters;
+      }
+    }
+    st.stall_iters = st.iters - last_improved;
+    st.stagnated = st.stall_iters >= stall_limit ? 1 : 0;
     secs += st.seconds;
     seg += st.seg_kernel_seconds;
     segl += st.seg_kernel_launches;

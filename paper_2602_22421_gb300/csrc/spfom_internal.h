@@ -180,6 +180,7 @@ struct FastArgs {
   const int* inst_conv;
   double* z_seg;
   float* rprev;  // [L] each segment's last Dinkelbach ratio (iterate passes), or null: start at 0
+  long long perm_a, perm_d;  // batch: warps visit their segment chunks in the order chunk * perm_a mod #chunks
 };
 
 // Arguments of k_seg_dd (spfom_segments_dd.cu): double-float images, and the
@@ -238,6 +239,7 @@ struct F32Args {
   long long coop_ntiles;
   int coop_items, coop_segs;
   float* rprev;  // [L] each segment's last Dinkelbach ratio, or null: start at 0
+  long long perm_a, perm_d;  // batch: warps visit their segment chunks in the order chunk * perm_a mod #chunks
 };
 
 struct RunConfig {

@@ -47,6 +47,39 @@ namespace spfom {
 
 namespace {
 
+// Segment order of the plain-load kernels. Each warp takes chunks of 32 / W
+// consecutive segments (one per lane group, so a warp's loads stay
+// contiguous), chunk c for c = its global warp id, + #warps, ... In a batch the
+// union's consecutive segments belong to one instance and share its few
+// thousand products, so every SM's fixed-point atomics would hit the same
+// addresses at once; there chunk c is remapped to c * perm_a mod #chunks
+// (perm_a coprime to #chunks: a bijection) and concurrent warps work on
+// segments spread over all instances.
+struct SegOrder {
+  long long nchunks, nwarps, first, pc, step;
+  int g;
+  __device__ SegOrder(long long L, int W, long long perm_a, long long perm_d) {
+    const long long C = 32 / W;
+    nchunks = (L + C - 1) / C;
+    nwarps = (long long)gridDim.x * (blockDim.x >> 5);
+    first = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    g = (int)((threadIdx.x & 31) / W);
+    pc = perm_a ? (first * perm_a) % (nchunks > 0 ? nchunks : 1) : first;
+    step = perm_a ? perm_d : nwarps;
+    C_ = C;
+    perm_ = perm_a != 0;
+  }
+  // segment of this lane's group in the current chunk; advances to the next chunk
+  __device__ long long next() {
+    const long long l = pc * C_ + g;
+    pc += step;
+    if (perm_ && pc >= nchunks) pc -= nchunks;
+    return l;
+  }
+  long long C_;
+  bool perm_;
+};
+
 template <int W, int P, int SC>
 __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
   extern __shared__ unsigned long long acc[];  // [n] product sales (fixed point) when SC == 1
@@ -60,11 +93,12 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
   const int lane = threadIdx.x & (W - 1);
   const int gbase = (threadIdx.x & 31) & ~(W - 1);
   const unsigned gmask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << gbase);
-  const long long gpb = blockDim.x / W;
-  const long long ngroups = (long long)gridDim.x * gpb;
   double zacc = 0.0;
   int fallbacks = 0;
-  for (long long l = blockIdx.x * gpb + threadIdx.x / W; l < Pr.L; l += ngroups) {
+  SegOrder ord(Pr.L, W, A.perm_a, A.perm_d);
+  for (long long ch = ord.first; ch < ord.nchunks; ch += ord.nwarps) {
+    const long long l = ord.next();
+    if (l >= Pr.L) continue;
     if (A.seg_inst && A.inst_conv[A.seg_inst[l]]) continue;  // batch: instance already converged
     const long long b = Pr.seg_ptr[l];
     const int K = (int)(Pr.seg_ptr[l + 1] - b);
@@ -211,10 +245,11 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
   const int lane = threadIdx.x & (W - 1);
   const int gbase = (threadIdx.x & 31) & ~(W - 1);
   const unsigned gmask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << gbase);
-  const long long gpb = blockDim.x / W;
-  const long long ngroups = (long long)gridDim.x * gpb;
   float zacc = 0.f;
-  for (long long l = blockIdx.x * gpb + threadIdx.x / W; l < A.L; l += ngroups) {
+  SegOrder ord(A.L, W, A.perm_a, A.perm_d);
+  for (long long ch = ord.first; ch < ord.nchunks; ch += ord.nwarps) {
+    const long long l = ord.next();
+    if (l >= A.L) continue;
     if (A.seg_inst && A.inst_conv[A.seg_inst[l]]) continue;  // batch: instance already converged
     const long long b = A.seg_ptr[l];
     const int K = (int)(A.seg_ptr[l + 1] - b);
@@ -489,8 +524,32 @@ __global__ void k_reduce_products(int n, int nparts, const unsigned long long* _
   if (acc) atomicAdd(s_fx + j, acc);
 }
 
+// perm_a coprime to the number of chunks, near 0.382 of it; perm_d = #warps * perm_a mod #chunks.
+void set_order(long long L, int W, int grid, bool batch, long long* a, long long* d) {
+  *a = *d = 0;
+  if (!batch || L <= 0) return;
+  const long long C = 32 / W, nch = (L + C - 1) / C;
+  if (nch < 3) return;
+  auto gcd = [](long long x, long long y) {
+    while (y) {
+      const long long t = x % y;
+      x = y;
+      y = t;
+    }
+    return x;
+  };
+  long long pa = (long long)(0.381966 * (double)nch);
+  if (pa < 1) pa = 1;
+  while (gcd(pa, nch) != 1) ++pa;
+  const long long nwarps = (long long)grid * (kFastThreads / 32);
+  *a = pa;
+  *d = (long long)((__int128)nwarps * pa % nch);
+}
+
 template <int SC>
-cudaError_t launch_fast_w(const FastArgs& A, int W, int grid, int smem, cudaStream_t s) {
+cudaError_t launch_fast_w(const FastArgs& A0, int W, int grid, int smem, cudaStream_t s) {
+  FastArgs A = A0;
+  set_order(A0.P.L, W, grid, A0.seg_inst != nullptr, &A.perm_a, &A.perm_d);
   switch (W) {  // 8 products per lane
     case 1: k_seg_fast<1, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     case 2: k_seg_fast<2, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
@@ -501,7 +560,9 @@ cudaError_t launch_fast_w(const FastArgs& A, int W, int grid, int smem, cudaStre
 }
 
 template <int SC>
-cudaError_t launch_f32_w(const F32Args& A, int W, int grid, int smem, cudaStream_t s) {
+cudaError_t launch_f32_w(const F32Args& A0, int W, int grid, int smem, cudaStream_t s) {
+  F32Args A = A0;
+  set_order(A0.L, W, grid, A0.seg_inst != nullptr, &A.perm_a, &A.perm_d);
   switch (W) {
     case 1: k_seg_f32<1, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     case 2: k_seg_f32<2, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
@@ -513,7 +574,9 @@ cudaError_t launch_f32_w(const F32Args& A, int W, int grid, int smem, cudaStream
 }
 
 template <int SC>
-cudaError_t launch_f32_p16(const F32Args& A, int W16, int grid, int smem, cudaStream_t s) {
+cudaError_t launch_f32_p16(const F32Args& A0, int W16, int grid, int smem, cudaStream_t s) {
+  F32Args A = A0;
+  set_order(A0.L, W16, grid, A0.seg_inst != nullptr, &A.perm_a, &A.perm_d);
   switch (W16) {  // 16 products per lane
     case 1: k_seg_f32<1, 16, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     case 2: k_seg_f32<2, 16, SC><<<grid, kFastThreads, smem, s>>>(A); break;
@@ -523,7 +586,9 @@ cudaError_t launch_f32_p16(const F32Args& A, int W16, int grid, int smem, cudaSt
 }
 
 template <int SC>
-cudaError_t launch_f32_p8(const F32Args& A, int W8, int grid, int smem, cudaStream_t s) {
+cudaError_t launch_f32_p8(const F32Args& A0, int W8, int grid, int smem, cudaStream_t s) {
+  F32Args A = A0;
+  set_order(A0.L, W8, grid, A0.seg_inst != nullptr, &A.perm_a, &A.perm_d);
   switch (W8) {  // 8 products per lane
     case 1: k_seg_f32<1, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     case 2: k_seg_f32<2, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;

@@ -71,7 +71,8 @@ class Stats(C.Structure):
                 ("sum_revenue", C.c_double), ("tau", C.c_double), ("mu", C.c_double), ("seconds", C.c_double),
                 ("seg_kernel_seconds", C.c_double), ("seg_kernel_launches", C.c_int64),
                 ("kernel_launches", C.c_int64), ("fallback_segments", C.c_int64), ("fast_path", C.c_int32),
-                ("iter_precision", C.c_int32)]
+                ("iter_precision", C.c_int32), ("stall_iters", C.c_int64), ("stagnated", C.c_int32),
+                ("pad2_", C.c_int32)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("pad")}
