@@ -102,7 +102,7 @@ typedef struct {
                                 nonzero read and written each iteration); needs precision 64,
                                 batch_frac 1 and a single instance, and runs the general kernel */
   int32_t tiling;            /* 0 (default): tiling 1 of the active segment pass until
-                                spfom_autotune picks one; 1..5: that tiling (see spfom_autotune),
+                                spfom_autotune picks one; 1..6: that tiling (see spfom_autotune),
                                 ENOTSUP at load when the instance does not allow it */
   void* stream;              /* cudaStream_t to run on; NULL (default): the ctx creates one */
 } spfom_params;
@@ -265,7 +265,9 @@ spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out);
  * lane (when shared memory allows), 3 = plain loads with 8 products per lane,
  * 4 = tiles streamed into shared memory by all threads of a block (coalesced
  * loads and the margin gather ahead of the solves), 8 products per lane,
- * 5 = plain loads with 16 products per lane (one lane per set of <= 16) --
+ * 5 = plain loads with 16 products per lane (one lane per set of <= 16),
+ * 6 (batches of instances with <= 8192 products each) = chunks of one
+ * instance's segments with shared-memory sums of its products --
  * batches choose between 1 and 3 (the staged kernels load the tiles of
  * converged members too);
  * precision 64 with path 2: 1 = 8 products per lane at two 512-thread blocks per

@@ -352,7 +352,7 @@ spfom_status spfom_create(const spfom_params* p, spfom_ctx** out) {
   if (prm.precision != 64 && prm.precision != 32) return SPFOM_ENOTSUP;
   if (!(prm.batch_frac > 0.0) || !(prm.restart_beta >= 0.0) || !(prm.kkt_tol >= 0.0) || prm.tau0 < 0 ||
       prm.mu < 0 || !(prm.restart_tau_decay > 0.0) ||
-      !(prm.restart_tau_balance >= 0.0 && prm.restart_tau_balance <= 1.0) || prm.tiling < 0 || prm.tiling > 5)
+      !(prm.restart_tau_balance >= 0.0 && prm.restart_tau_balance <= 1.0) || prm.tiling < 0 || prm.tiling > 6)
     return SPFOM_EINVAL;
   spfom_ctx* ctx = new (std::nothrow) spfom_ctx;
   if (!ctx) return SPFOM_ENOMEM;
@@ -498,6 +498,21 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
         SPFOM_TRY(upload(ctx, &W.tile64_ptr, tiles.data(), tiles.size()));
         W.ntiles64 = nt;
       }
+      if (ctx->p.precision == 32 && ctx->loading_batch && plan.scatter == 2) {
+        // instance chunks of the batch for the chunked binary32 kernel (shared sums per instance)
+        const auto& B = *ctx->loading_batch;
+        int maxn = 0;
+        for (int b = 0; b < B.count; ++b) maxn = std::max(maxn, B.prod_ptr[b + 1] - B.prod_ptr[b]);
+        if (spfom::bchunk_plan(maxn, ctx->sms, &plan)) {
+          const long long nc = spfom::make_batch_chunks(B.seg_off, spfom::kBChunkSegs, nullptr, nullptr);
+          std::vector<long long> cseg((size_t)nc + 1);
+          std::vector<int> cinst((size_t)(nc > 0 ? nc : 1));
+          spfom::make_batch_chunks(B.seg_off, spfom::kBChunkSegs, cseg.data(), cinst.data());
+          SPFOM_TRY(upload(ctx, &W.bc_seg, cseg.data(), cseg.size()));
+          SPFOM_TRY(upload(ctx, &W.bc_inst, cinst.data(), cinst.size()));
+          W.bc_count = nc;
+        }
+      }
       if (ctx->p.precision == 32 && spfom::coop_plan(n, kmax, ctx->sms, &plan)) {
         // tiles of consecutive segments for the cooperatively staged binary32 kernel
         const auto* sp = reinterpret_cast<const long long*>(I->seg_ptr);
@@ -523,6 +538,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       W.zparts_iter = std::max(std::max(plan.grid, plan.grid32), std::max(plan.pipe ? plan.pipe_grid : 0,
                                                                           plan.tma_ok ? plan.tma_grid : 0));
       if (plan.coop_ok) W.zparts_iter = std::max(W.zparts_iter, plan.coop_grid);
+      if (plan.bchunk_ok) W.zparts_iter = std::max(W.zparts_iter, plan.bchunk_grid);
       W.zparts_eval = plan.grid_eval;
       if (dd)
         for (int v = 1; v <= 3; ++v) {
@@ -532,9 +548,10 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       W.dd_ok = dd;
       if (ctx->p.tiling > 0) {  // a requested tiling of the active segment pass
         const int t = ctx->p.tiling;
-        bool ok = t <= 5;
+        bool ok = t <= 6;
         if (ok && ctx->p.precision == 32) {
-          ok = (t != 2 || W.plan.tma_ok) && (t != 4 || W.plan.coop_ok);
+          ok = (t != 2 || W.plan.tma_ok) && (t != 4 || W.plan.coop_ok) && (t != 6 || W.plan.bchunk_ok);
+          W.plan.bchunk = t == 6 ? 1 : 0;
           W.plan.tma = t == 2 ? 1 : 0;
           W.plan.f32_p8 = t == 3 ? 1 : 0;
           W.plan.coop = t == 4 ? 1 : 0;
@@ -1101,7 +1118,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   const bool f32 = ctx->W.fast && ctx->W.v32 && ctx->cfg.f32;
   const bool dd = ctx->W.fast && ctx->W.v2 && !ctx->cfg.f32;
   auto current = [&]() {
-    return f32 ? (plan.f32_p16 ? 5 : (plan.coop ? 4 : (plan.tma ? 2 : (plan.f32_p8 ? 3 : 1))))
+    return f32 ? (plan.bchunk ? 6 : (plan.f32_p16 ? 5 : (plan.coop ? 4 : (plan.tma ? 2 : (plan.f32_p8 ? 3 : 1)))))
                : (dd ? plan.dd_variant : 1);
   };
   // The staged kernels (2, 4) load whole tiles even when a batch has frozen
@@ -1109,6 +1126,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   // would not hold over a batched solve, so batches choose among the plain-load
   // tilings.
   auto available = [&](int c) {
+    if (f32 && c == 6) return plan.bchunk_ok != 0 && ctx->W.batch && ctx->W.bc_count > 0;
     if (f32) return c == 4 ? (plan.coop_ok != 0 && !ctx->W.batch) : (c != 2 || (plan.tma_ok && !ctx->W.batch));
     return c <= 3 && dd && spfom::dd_variant_ok(plan, c);
   };
@@ -1118,6 +1136,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
       plan.f32_p8 = c == 3 ? 1 : 0;
       plan.coop = c == 4 ? 1 : 0;
       plan.f32_p16 = c == 5 ? 1 : 0;
+      plan.bchunk = c == 6 ? 1 : 0;
     } else {
       plan.dd_variant = c;
     }
@@ -1136,7 +1155,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   ctx->cfg.kkt_tol = -1.0;  // no instance may converge (and stop working) while being timed
   double best = INFINITY;
   int choice = current();
-  for (int cand = 1; cand <= 5; ++cand) {
+  for (int cand = 1; cand <= 6; ++cand) {
     if (!available(cand)) continue;
     select(cand);
     drop_graphs(ctx);

@@ -178,12 +178,15 @@ int blocks_for(int n) { return n > 0 ? (n + kThreads - 1) / kThreads : 1; }
 
 }  // namespace
 
-cudaError_t launch_batch_iteration(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s) {
+cudaError_t launch_batch_iteration(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s,
+                                   cudaEvent_t seg_begin, cudaEvent_t seg_end) {
   const bool f32 = cfg.f32 && Wk.v32;
   k_b_margins<<<blocks_for(P.n), kThreads, 0, s>>>(P, Wk.bm, Wk.y, nullptr, 0, Wk.marg, f32 ? Wk.marg32 : nullptr,
                                                     Wk.s_fx, f32 ? nullptr : Wk.marg2);
   int zparts = 0;
+  if (seg_begin) cudaEventRecord(seg_begin, s);
   cudaError_t e = launch_segment_pass(P, Wk, cfg, Wk.marg, true, s, &zparts);
+  if (seg_end) cudaEventRecord(seg_end, s);
   if (e != cudaSuccess) return e;
   e = launch_reduce_products(P, Wk.plan, zparts, Wk.part, Wk.s_fx, Wk.st, s);
   if (e != cudaSuccess) return e;

@@ -3,6 +3,8 @@
 // public interface is include/spfom.h.
 #pragma once
 #include <cuda_runtime.h>
+
+#include <vector>
 #include <cstdint>
 
 namespace spfom {
@@ -94,6 +96,8 @@ struct FastPlan {
   int f32_p8;         // 1: the plain-load binary32 kernel runs 8 products per lane (W8 lanes)
   int f32_p16;        // 1: it runs 16 products per lane (W16 lanes: one lane per set of <= 16)
   int W16;            // lanes per segment with 16 products per lane (1 or 2)
+  int bchunk;         // 1: the binary32 pass of a batch runs the instance-chunked kernel (tiling 6)
+  int bchunk_ok, bchunk_smem, bchunk_grid;
   int coop;           // 1: the binary32 pass runs the cooperatively staged kernel (tiling 4)
   int coop_ok, coop_items, coop_segs, coop_smem, coop_grid;
   int dd_variant;     // tiling of k_seg_dd (1..3, see spfom_segments_dd.cu)
@@ -124,6 +128,9 @@ struct Work {
   float2* marg2;       // [n] (hi, lo) of the margins (iterate)
   float2* marg2_eval;  // [n] (hi, lo) of the margins (evaluation)
   float* rprev;        // [L] last binary32 Dinkelbach ratio of every segment (start of the next solve)
+  long long* bc_seg;   // instance chunks of a batch (k_seg_f32_bchunk)
+  int* bc_inst;
+  long long bc_count;
   long long* coop_tile_ptr;  // [coop_ntiles + 1] tiles of k_seg_f32_coop
   long long coop_ntiles;
   bool dd_ok;          // k_seg_dd planned (path 0)
@@ -240,6 +247,11 @@ struct F32Args {
   int coop_items, coop_segs;
   float* rprev;  // [L] each segment's last Dinkelbach ratio, or null: start at 0
   long long perm_a, perm_d;  // batch: warps visit their segment chunks in the order chunk * perm_a mod #chunks
+  // instance chunks of a batch (k_seg_f32_bchunk)
+  long long bc_count;
+  const long long* bc_seg;   // [bc_count + 1] first segment of each chunk
+  const int* bc_inst;        // [bc_count] instance of each chunk
+  const int* bc_prod_ptr;    // [instances + 1] product offsets
 };
 
 struct RunConfig {
@@ -279,6 +291,12 @@ cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatte
 cudaError_t launch_seg_dd(const DdArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s);
 cudaError_t launch_dd_prep(const Problem& P, float2* v2, float2* vt2, float4* seg4, cudaStream_t s);
 bool dd_setup(FastPlan* plan, int sms);
+// instance-chunked binary32 kernel for batches (spfom_segments_bchunk.cu)
+constexpr int kBChunkProducts = 8192;  // shared-memory sums per block (64 KB)
+constexpr int kBChunkSegs = 2048;      // segments per chunk
+bool bchunk_plan(int max_inst_products, int sms, FastPlan* plan);
+long long make_batch_chunks(const std::vector<long long>& seg_off, int max_segs, long long* seg_out, int* inst_out);
+cudaError_t launch_seg_f32_bchunk(const F32Args& A, const FastPlan& plan, cudaStream_t s);
 // cooperatively staged binary32 kernel (spfom_segments_coop.cu)
 bool coop_plan(int n, int kmax, int sms, FastPlan* plan);
 long long make_tiles_lim(const long long* seg_ptr, long long L, int max_segs, int max_items, long long* tiles_out);
@@ -287,7 +305,8 @@ int dd_variant_ok(const FastPlan& plan, int v);
 cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s);
 bool tma_plan(int n, int kmax, int sms, FastPlan* plan);
 // spfom_batch.cu
-cudaError_t launch_batch_iteration(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s);
+cudaError_t launch_batch_iteration(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s,
+                                   cudaEvent_t seg_begin = nullptr, cudaEvent_t seg_end = nullptr);
 cudaError_t launch_batch_eval(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s);
 int batch_launches_per_iteration(const Work& Wk);
 int batch_launches_per_eval();

@@ -430,8 +430,11 @@ cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfi
     F32Args A{P.seg_ptr, P.seg_prod, Wk.v32, Wk.vt32, Wk.lam32, Wk.vt0_32, P.L, P.n, Wk.fx_bits, Wk.marg32,
               Wk.part, Wk.s_fx, Wk.zpart, Wk.st, Wk.tile_ptr, Wk.ntiles, Wk.plan.acc_bytes, Wk.st,
               seg_inst, conv, z_seg, Wk.coop_tile_ptr, Wk.coop_ntiles, Wk.plan.coop_items, Wk.plan.coop_segs,
-              Wk.rprev};
-    *zparts_out = Wk.plan.coop ? Wk.plan.coop_grid : (Wk.plan.tma ? Wk.plan.tma_grid : Wk.plan.grid32);
+              Wk.rprev, 0, 0, Wk.batch ? Wk.bc_count : 0, Wk.bc_seg, Wk.bc_inst,
+              Wk.batch ? Wk.bm.prod_ptr : nullptr};
+    const bool bchunk = Wk.plan.bchunk && Wk.batch && Wk.bc_count > 0;
+    *zparts_out = bchunk ? Wk.plan.bchunk_grid
+                         : (Wk.plan.coop ? Wk.plan.coop_grid : (Wk.plan.tma ? Wk.plan.tma_grid : Wk.plan.grid32));
     return launch_seg_f32(A, Wk.plan, s);
   }
   FastArgs A{P, marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, Wk.s_fx,
@@ -446,7 +449,7 @@ cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfi
 
 cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& cfg, cudaStream_t s,
                              cudaEvent_t seg_begin, cudaEvent_t seg_end) {
-  if (Wk.batch) return launch_batch_iteration(P, Wk, cfg, s);
+  if (Wk.batch) return launch_batch_iteration(P, Wk, cfg, s, seg_begin, seg_end);
   const bool sampled = cfg.batch_frac < 1.0;
   const bool fast = Wk.fast && !sampled;
   const bool f32 = fast && cfg.f32 && Wk.v32;

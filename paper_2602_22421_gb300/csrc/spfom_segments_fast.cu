@@ -677,6 +677,7 @@ cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatte
 }
 
 cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t s) {
+  if (plan.bchunk && A.bc_count > 0) return launch_seg_f32_bchunk(A, plan, s);
   if (plan.coop) return launch_seg_f32_coop(A, plan, s);
   if (plan.tma)
     return plan.scatter == 1 ? launch_tma_w<1>(A, plan.tma_W, plan.tma_grid, plan.tma_smem, s)

@@ -167,3 +167,21 @@ def test_autotune_keeps_the_duals_and_the_solution(batch):
         st = s.solve()
     assert st["converged"] == 1
     assert st["dual_avg"] == pytest.approx(ref["dual_avg"], rel=2e-4)
+
+
+def test_instance_chunked_batch_kernel_equals_plain_loads():
+    """Tiling 6 (chunks of one instance's segments with shared-memory sums of
+    that instance's products) computes what tiling 3 computes on a batch wide
+    enough for global sums: the fixed-point sales make duals and sales equal
+    bit for bit."""
+    from instances import batch_base
+    insts = [batch_base(12, k) for k in range(14)]
+    out = {}
+    for tiling in (3, 6):
+        with Solver(precision=32, tiling=tiling) as s:
+            s.load_batch(insts)
+            st = s.step(130)
+            out[tiling] = (s.duals(), s.vector(5), st, s.batch_stats())
+    np.testing.assert_array_equal(out[3][0], out[6][0])
+    np.testing.assert_array_equal(out[3][1], out[6][1])
+    assert [p["restarts"] for p in out[3][3]] == [p["restarts"] for p in out[6][3]]
