@@ -498,12 +498,14 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
         SPFOM_TRY(upload(ctx, &W.tile64_ptr, tiles.data(), tiles.size()));
         W.ntiles64 = nt;
       }
-      if (ctx->p.precision == 32 && ctx->loading_batch && plan.scatter == 2) {
-        // instance chunks of the batch for the chunked binary32 kernel (shared sums per instance)
+      if (ctx->loading_batch && plan.scatter == 2) {
+        // instance chunks of the batch for the chunked kernels (shared sums per instance)
         const auto& B = *ctx->loading_batch;
         int maxn = 0;
         for (int b = 0; b < B.count; ++b) maxn = std::max(maxn, B.prod_ptr[b + 1] - B.prod_ptr[b]);
-        if (spfom::bchunk_plan(maxn, ctx->sms, &plan)) {
+        const bool c32 = ctx->p.precision == 32 && spfom::bchunk_plan(maxn, ctx->sms, &plan);
+        const bool c64 = spfom::bchunk64_plan(maxn, ctx->sms, &plan);
+        if (c32 || c64) {
           const long long nc = spfom::make_batch_chunks(B.seg_off, spfom::kBChunkSegs, nullptr, nullptr);
           std::vector<long long> cseg((size_t)nc + 1);
           std::vector<int> cinst((size_t)(nc > 0 ? nc : 1));
@@ -539,6 +541,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
                                                                           plan.tma_ok ? plan.tma_grid : 0));
       if (plan.coop_ok) W.zparts_iter = std::max(W.zparts_iter, plan.coop_grid);
       if (plan.bchunk_ok) W.zparts_iter = std::max(W.zparts_iter, plan.bchunk_grid);
+      if (plan.bchunk64_ok) W.zparts_iter = std::max(W.zparts_iter, plan.bchunk64_grid);
       W.zparts_eval = plan.grid_eval;
       if (dd)
         for (int v = 1; v <= 3; ++v) {
@@ -815,6 +818,7 @@ spfom_status spfom_solve(spfom_ctx* ctx, const double* y0, spfom_stats* out) {
   double best_dual = INFINITY;
   long long last_improved = 0;
   const long long stall_limit = std::max(1LL, (long long)(ctx->P.L / 100));
+  bool polished = false;  // precision 32: the binary64 confirmation period has run
   for (;;) {
     long long left = ctx->p.max_iters - ctx->host_t;
     if (left <= 0) break;
@@ -832,7 +836,18 @@ spfom_status spfom_solve(spfom_ctx* ctx, const double* y0, spfom_stats* out) {
     seg += st.seg_kernel_seconds;
     segl += st.seg_kernel_launches;
     launches += st.kernel_launches;
-    if (st.converged && ctx->cfg.f32 && ctx->p.polish) {
+    if (ctx->W.batch && ctx->cfg.f32 && !st.converged && !ctx->h_inst.empty()) {
+      // a few members left: finish them with binary64 iterations (a binary32 run can stall
+      // above the tolerance near ties, and the frozen members cost little either way)
+      long long active = 0;
+      for (const auto& I : ctx->h_inst) active += I.converged ? 0 : 1;
+      if (active * 20 <= (long long)ctx->h_inst.size()) {
+        ctx->cfg.f32 = 0;  // the binary64 period graph is kept apart from the binary32 one
+        ctx->polishing = true;
+      }
+    }
+    if (st.converged && ctx->p.precision == 32 && ctx->p.polish && !polished) {
+      polished = true;
       // binary64 polish: clear the flag(s) and iterate in binary64 until the next evaluation
       ctx->cfg.f32 = 0;
       ctx->polishing = true;

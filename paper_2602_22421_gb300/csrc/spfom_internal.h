@@ -98,6 +98,7 @@ struct FastPlan {
   int W16;            // lanes per segment with 16 products per lane (1 or 2)
   int bchunk;         // 1: the binary32 pass of a batch runs the instance-chunked kernel (tiling 6)
   int bchunk_ok, bchunk_smem, bchunk_grid;
+  int bchunk64_ok, bchunk64_grid;  // the binary64 pass of a batch (k_seg_fast_bchunk), used whenever planned
   int coop;           // 1: the binary32 pass runs the cooperatively staged kernel (tiling 4)
   int coop_ok, coop_items, coop_segs, coop_smem, coop_grid;
   int dd_variant;     // tiling of k_seg_dd (1..3, see spfom_segments_dd.cu)
@@ -188,6 +189,11 @@ struct FastArgs {
   double* z_seg;
   float* rprev;  // [L] each segment's last Dinkelbach ratio (iterate passes), or null: start at 0
   long long perm_a, perm_d;  // batch: warps visit their segment chunks in the order chunk * perm_a mod #chunks
+  // instance chunks of a batch (k_seg_fast_bchunk)
+  long long bc_count;
+  const long long* bc_seg;
+  const int* bc_inst;
+  const int* bc_prod_ptr;
 };
 
 // Arguments of k_seg_dd (spfom_segments_dd.cu): double-float images, and the
@@ -295,6 +301,7 @@ bool dd_setup(FastPlan* plan, int sms);
 constexpr int kBChunkProducts = 8192;  // shared-memory sums per block (64 KB)
 constexpr int kBChunkSegs = 2048;      // segments per chunk
 bool bchunk_plan(int max_inst_products, int sms, FastPlan* plan);
+bool bchunk64_plan(int max_inst_products, int sms, FastPlan* plan);
 long long make_batch_chunks(const std::vector<long long>& seg_off, int max_segs, long long* seg_out, int* inst_out);
 cudaError_t launch_seg_f32_bchunk(const F32Args& A, const FastPlan& plan, cudaStream_t s);
 // cooperatively staged binary32 kernel (spfom_segments_coop.cu)

@@ -438,12 +438,13 @@ cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfi
     return launch_seg_f32(A, Wk.plan, s);
   }
   FastArgs A{P, marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, Wk.s_fx,
-             Wk.tile64_ptr, Wk.ntiles64, Wk.plan.pipe_acc_bytes, Wk.st, seg_inst, conv, z_seg, Wk.rprev};
+             Wk.tile64_ptr, Wk.ntiles64, Wk.plan.pipe_acc_bytes, Wk.st, seg_inst, conv, z_seg, Wk.rprev, 0, 0,
+             Wk.batch ? Wk.bc_count : 0, Wk.bc_seg, Wk.bc_inst, Wk.batch ? Wk.bm.prod_ptr : nullptr};
   if (Wk.plan.pipe && !Wk.batch) {
     *zparts_out = Wk.plan.pipe_grid;
     return launch_seg_fast_pipe(A, Wk.plan, s);
   }
-  *zparts_out = Wk.plan.grid;
+  *zparts_out = (Wk.plan.bchunk64_ok && A.bc_count > 0) ? Wk.plan.bchunk64_grid : Wk.plan.grid;
   return launch_seg_fast(A, Wk.plan, true, s);
 }
 

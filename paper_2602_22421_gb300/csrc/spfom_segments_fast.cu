@@ -80,6 +80,133 @@ struct SegOrder {
   bool perm_;
 };
 
+// One segment of the certified-decision pass (see the file comment): the
+// binary32 Dinkelbach decision with its certificate (binary64 redo when it
+// fails), binary64 values, and the fixed-point sales added to sums[j - base]
+// (none when sums is null). Called by all W lanes of the segment's group.
+template <int W, int P>
+__device__ __forceinline__ void fast_segment(const FastArgs& A, long long l, int lane, unsigned gmask,
+                                             unsigned long long* sums, int base, double& zacc, int& fallbacks) {
+  const Problem& Pr = A.P;
+  const long long b = Pr.seg_ptr[l];
+  const int K = (int)(Pr.seg_ptr[l + 1] - b);
+  // Registers hold the binary32 images a = m v, b = vt and the product ids;
+  // the binary64 values are read again (L1) for the products chosen.
+  int jv[P];
+  float af[P], bf[P];
+  unsigned cand = 0;
+  bool ok = true;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    const int k = lane + p * W;
+    jv[p] = 0;
+    af[p] = bf[p] = 0.f;
+    if (k < K) {
+      jv[p] = Pr.seg_prod[b + k];
+      const double m = A.marg[jv[p]];
+      if (__double_as_longlong(m) > 0) {  // m_j > 0
+        cand |= 1u << p;
+        af[p] = f32_trunc(m, ok) * f32_trunc(Pr.v[b + k], ok);
+        bf[p] = f32_trunc(Pr.vt[b + k], ok);
+      }
+    }
+  }
+  const double lam = Pr.lam[l], vt0 = Pr.vt0[l];
+  const float vt0f = f32_trunc(vt0, ok);
+  // Dinkelbach in binary32, started at the segment's ratio of the previous
+  // iteration (any start reaches a fixed point, and every fixed point is
+  // optimal; the margins move little between iterations, so this one is
+  // usually confirmed by the second pass).
+  float R = A.rprev ? A.rprev[l] : 0.f;
+  unsigned sel = 0xffffffffu;  // no previous set
+  bool conv = false;
+  for (int it = 0; it < P * W + 3; ++it) {
+    unsigned s = 0;
+    float N = 0.f, D = 0.f;
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      if (((cand >> p) & 1u) && af[p] > R * bf[p]) {
+        s |= 1u << p;
+        N += af[p];
+        D += bf[p];
+      }
+    if (__all_sync(gmask, s == sel)) {
+      conv = true;
+      break;
+    }
+#pragma unroll
+    for (int o = W >> 1; o > 0; o >>= 1) {
+      N += __shfl_xor_sync(gmask, N, o, W);
+      D += __shfl_xor_sync(gmask, D, o, W);
+    }
+    R = __fdividef(N, vt0f + D);
+    sel = s;
+  }
+  if (A.rprev && lane == 0 && conv) A.rprev[l] = R;
+  bool good = ok && conv;
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+    if ((cand >> p) & 1u) {
+      const float a = af[p], c = R * bf[p];
+      if (!(fabsf(a - c) > kCertDelta * (a + c))) good = false;
+    }
+  unsigned S = sel;
+  if (!__all_sync(gmask, good)) {
+    // Not certified: the same iteration in binary64.
+    if (lane == 0) ++fallbacks;
+    double Rd = 0.0;
+    unsigned prev = 0xffffffffu;
+    for (int it = 0; it < P * W + 2; ++it) {
+      unsigned s = 0;
+      double N = 0.0, D = 0.0;
+#pragma unroll
+      for (int p = 0; p < P; ++p)
+        if ((cand >> p) & 1u) {
+          const int k = lane + p * W;
+          const double a = A.marg[jv[p]] * Pr.v[b + k], t = Pr.vt[b + k];
+          if (a > Rd * t) {
+            s |= 1u << p;
+            N += a;
+            D += t;
+          }
+        }
+      if (__all_sync(gmask, s == prev)) break;
+#pragma unroll
+      for (int o = W >> 1; o > 0; o >>= 1) {
+        N += __shfl_xor_sync(gmask, N, o, W);
+        D += __shfl_xor_sync(gmask, D, o, W);
+      }
+      Rd = N / (vt0 + D);
+      prev = s;
+    }
+    S = prev;
+  }
+  // binary64 values of the chosen assortment.
+  double Nl = 0.0, Dl = 0.0;
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+    if ((S >> p) & 1u) {
+      const int k = lane + p * W;
+      Dl += Pr.vt[b + k];
+      Nl = fma(A.marg[jv[p]], Pr.v[b + k], Nl);
+    }
+#pragma unroll
+  for (int o = W >> 1; o > 0; o >>= 1) {
+    Nl += __shfl_xor_sync(gmask, Nl, o, W);
+    Dl += __shfl_xor_sync(gmask, Dl, o, W);
+  }
+  const double q = quotient(lam, vt0 + Dl);
+  if (lane == 0) {
+    if (A.z_seg) A.z_seg[l] = q * Nl;
+    else zacc += q * Nl;
+  }
+  if (sums) {
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      if ((S >> p) & 1u) atomicAdd(sums + (jv[p] - base), fixed_product(q, Pr.v[b + lane + p * W], A.fx_bits));
+  }
+}
+
 template <int W, int P, int SC>
 __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
   extern __shared__ unsigned long long acc[];  // [n] product sales (fixed point) when SC == 1
@@ -100,124 +227,7 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
     const long long l = ord.next();
     if (l >= Pr.L) continue;
     if (A.seg_inst && A.inst_conv[A.seg_inst[l]]) continue;  // batch: instance already converged
-    const long long b = Pr.seg_ptr[l];
-    const int K = (int)(Pr.seg_ptr[l + 1] - b);
-    // Registers hold the binary32 images a = m v, b = vt and the product ids;
-    // the binary64 values are read again (L1) for the products chosen.
-    int jv[P];
-    float af[P], bf[P];
-    unsigned cand = 0;
-    bool ok = true;
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-      const int k = lane + p * W;
-      jv[p] = 0;
-      af[p] = bf[p] = 0.f;
-      if (k < K) {
-        jv[p] = Pr.seg_prod[b + k];
-        const double m = A.marg[jv[p]];
-        if (__double_as_longlong(m) > 0) {  // m_j > 0
-          cand |= 1u << p;
-          af[p] = f32_trunc(m, ok) * f32_trunc(Pr.v[b + k], ok);
-          bf[p] = f32_trunc(Pr.vt[b + k], ok);
-        }
-      }
-    }
-    const double lam = Pr.lam[l], vt0 = Pr.vt0[l];
-    const float vt0f = f32_trunc(vt0, ok);
-    // Dinkelbach in binary32, started at the segment's ratio of the previous
-    // iteration (any start reaches a fixed point, and every fixed point is
-    // optimal; the margins move little between iterations, so this one is
-    // usually confirmed by the second pass).
-    float R = A.rprev ? A.rprev[l] : 0.f;
-    unsigned sel = 0xffffffffu;  // no previous set
-    bool conv = false;
-    for (int it = 0; it < P * W + 3; ++it) {
-      unsigned s = 0;
-      float N = 0.f, D = 0.f;
-#pragma unroll
-      for (int p = 0; p < P; ++p)
-        if (((cand >> p) & 1u) && af[p] > R * bf[p]) {
-          s |= 1u << p;
-          N += af[p];
-          D += bf[p];
-        }
-      if (__all_sync(gmask, s == sel)) {
-        conv = true;
-        break;
-      }
-#pragma unroll
-      for (int o = W >> 1; o > 0; o >>= 1) {
-        N += __shfl_xor_sync(gmask, N, o, W);
-        D += __shfl_xor_sync(gmask, D, o, W);
-      }
-      R = __fdividef(N, vt0f + D);
-      sel = s;
-    }
-    if (A.rprev && lane == 0 && conv) A.rprev[l] = R;
-    bool good = ok && conv;
-#pragma unroll
-    for (int p = 0; p < P; ++p)
-      if ((cand >> p) & 1u) {
-        const float a = af[p], c = R * bf[p];
-        if (!(fabsf(a - c) > kCertDelta * (a + c))) good = false;
-      }
-    unsigned S = sel;
-    if (!__all_sync(gmask, good)) {
-      // Not certified: the same iteration in binary64.
-      if (lane == 0) ++fallbacks;
-      double Rd = 0.0;
-      unsigned prev = 0xffffffffu;
-      for (int it = 0; it < P * W + 2; ++it) {
-        unsigned s = 0;
-        double N = 0.0, D = 0.0;
-#pragma unroll
-        for (int p = 0; p < P; ++p)
-          if ((cand >> p) & 1u) {
-            const int k = lane + p * W;
-            const double a = A.marg[jv[p]] * Pr.v[b + k], t = Pr.vt[b + k];
-            if (a > Rd * t) {
-              s |= 1u << p;
-              N += a;
-              D += t;
-            }
-          }
-        if (__all_sync(gmask, s == prev)) break;
-#pragma unroll
-        for (int o = W >> 1; o > 0; o >>= 1) {
-          N += __shfl_xor_sync(gmask, N, o, W);
-          D += __shfl_xor_sync(gmask, D, o, W);
-        }
-        Rd = N / (vt0 + D);
-        prev = s;
-      }
-      S = prev;
-    }
-    // binary64 values of the chosen assortment.
-    double Nl = 0.0, Dl = 0.0;
-#pragma unroll
-    for (int p = 0; p < P; ++p)
-      if ((S >> p) & 1u) {
-        const int k = lane + p * W;
-        Dl += Pr.vt[b + k];
-        Nl = fma(A.marg[jv[p]], Pr.v[b + k], Nl);
-      }
-#pragma unroll
-    for (int o = W >> 1; o > 0; o >>= 1) {
-      Nl += __shfl_xor_sync(gmask, Nl, o, W);
-      Dl += __shfl_xor_sync(gmask, Dl, o, W);
-    }
-    const double q = quotient(lam, vt0 + Dl);
-    if (lane == 0) {
-      if (A.z_seg) A.z_seg[l] = q * Nl;
-      else zacc += q * Nl;
-    }
-    if (SC != 0) {
-#pragma unroll
-      for (int p = 0; p < P; ++p)
-        if ((S >> p) & 1u)
-          atomicAdd((SC == 1 ? acc : A.s_fx) + jv[p], fixed_product(q, Pr.v[b + lane + p * W], A.fx_bits));
-    }
+    fast_segment<W, P>(A, l, lane, gmask, SC == 0 ? nullptr : (SC == 1 ? acc : A.s_fx), 0, zacc, fallbacks);
   }
   const double tot = block_sum_d(zacc, sh);
   if (threadIdx.x == 0) A.zpart[blockIdx.x] = tot;
@@ -227,6 +237,39 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
     unsigned long long* dst = A.part + (size_t)blockIdx.x * Pr.n;
     for (int j = threadIdx.x; j < Pr.n; j += blockDim.x) dst[j] = acc[j];
   }
+}
+
+// Instance chunks of a batch (see spfom_segments_bchunk.cu): the same
+// segment solves as k_seg_fast, with the fixed-point sales summed in shared
+// memory per chunk of one instance's segments and flushed to the global sums
+// once per chunk, instead of one global atomic per chosen product.
+template <int W, int P>
+__global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast_bchunk(FastArgs A) {
+  extern __shared__ unsigned long long acc[];  // [kBChunkProducts]
+  __shared__ double sh[32];
+  if (A.st && A.st->converged) return;
+  const int lane = threadIdx.x & (W - 1);
+  const int gbase = (threadIdx.x & 31) & ~(W - 1);
+  const unsigned gmask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << gbase);
+  const int gpb = blockDim.x / W;
+  double zacc = 0.0;
+  int fallbacks = 0;
+  for (long long c = blockIdx.x; c < A.bc_count; c += gridDim.x) {
+    const int bi = A.bc_inst[c];
+    if (A.inst_conv[bi]) continue;  // uniform over the block
+    const long long l0 = A.bc_seg[c], l1 = A.bc_seg[c + 1];
+    const int pb = A.bc_prod_ptr[bi], nb = A.bc_prod_ptr[bi + 1] - pb;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) acc[i] = 0ull;
+    __syncthreads();
+    for (long long l = l0 + threadIdx.x / W; l < l1; l += gpb) fast_segment<W, P>(A, l, lane, gmask, acc, pb, zacc, fallbacks);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x)
+      if (acc[i]) atomicAdd(A.s_fx + pb + i, acc[i]);
+  }
+  const double tot = block_sum_d(zacc, sh);
+  if (threadIdx.x == 0) A.zpart[blockIdx.x] = tot;
+  if (fallbacks && A.fallbacks) atomicAdd(A.fallbacks, (unsigned long long)fallbacks);
 }
 
 // Binary32 bulk iteration (the precision-32 mode): the same decision as
@@ -671,6 +714,15 @@ bool fast_plan(int n, int kmax, int sms, FastPlan* plan) {
 }
 
 cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatter, cudaStream_t s) {
+  if (scatter && plan.bchunk64_ok && A.bc_count > 0) {
+    switch (plan.W8) {
+      case 1: k_seg_fast_bchunk<1, 8><<<plan.bchunk64_grid, kFastThreads, plan.bchunk_smem, s>>>(A); break;
+      case 2: k_seg_fast_bchunk<2, 8><<<plan.bchunk64_grid, kFastThreads, plan.bchunk_smem, s>>>(A); break;
+      case 4: k_seg_fast_bchunk<4, 8><<<plan.bchunk64_grid, kFastThreads, plan.bchunk_smem, s>>>(A); break;
+      default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+  }
   if (!scatter) return launch_fast_w<0>(A, plan.W8, plan.grid_eval, 0, s);
   return plan.scatter == 1 ? launch_fast_w<1>(A, plan.W8, plan.grid, plan.smem, s)
                            : launch_fast_w<2>(A, plan.W8, plan.grid, 0, s);
@@ -726,6 +778,28 @@ bool tma_plan(int n, int kmax, int sms, FastPlan* plan) {
 
 // Tiles of consecutive segments with at most kTileSegs segments and kTileItems
 // products each (host side; seg_ptr is the caller's host array).
+bool bchunk64_plan(int max_inst_products, int sms, FastPlan* plan) {
+  if (plan->W8 > 4 || max_inst_products > kBChunkProducts) return false;
+  const int smem = kBChunkProducts * (int)sizeof(unsigned long long);
+  int nb = 0;
+#define SPFOM_BC64(WW)                                                                                   \
+  if (plan->W8 == WW) {                                                                                  \
+    if (cudaFuncSetAttribute(k_seg_fast_bchunk<WW, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != \
+        cudaSuccess)                                                                                     \
+      return false;                                                                                      \
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_fast_bchunk<WW, 8>, kFastThreads, smem);    \
+  }
+  SPFOM_BC64(1)
+  SPFOM_BC64(2)
+  SPFOM_BC64(4)
+#undef SPFOM_BC64
+  if (nb < 1) return false;
+  plan->bchunk64_ok = 1;
+  plan->bchunk_smem = smem;
+  plan->bchunk64_grid = nb * sms;
+  return true;
+}
+
 long long make_tiles(const long long* seg_ptr, long long L, long long* tiles_out) {
   long long nt = 0, l = 0;
   if (tiles_out) tiles_out[0] = 0;
