@@ -102,7 +102,7 @@ typedef struct {
                                 nonzero read and written each iteration); needs precision 64,
                                 batch_frac 1 and a single instance, and runs the general kernel */
   int32_t tiling;            /* 0 (default): tiling 1 of the active segment pass until
-                                spfom_autotune picks one; 1..6: that tiling (see spfom_autotune),
+                                spfom_autotune picks one; 1..7: that tiling (see spfom_autotune),
                                 ENOTSUP at load when the instance does not allow it */
   void* stream;              /* cudaStream_t to run on; NULL (default): the ctx creates one */
 } spfom_params;
@@ -267,13 +267,17 @@ spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out);
  * loads and the margin gather ahead of the solves), 8 products per lane,
  * 5 = plain loads with 16 products per lane (one lane per set of <= 16),
  * 6 (batches of instances with <= 8192 products each) = chunks of one
- * instance's segments with shared-memory sums of its products --
- * batches choose between 1 and 3 (the staged kernels load the tiles of
+ * instance's segments with shared-memory sums of its products,
+ * 7 = as 3 with the margins copied into shared memory (one 1024-thread block
+ * per SM; needs 16 n bytes of shared memory, n <= 14464) --
+ * batches do not try 2 and 4 (the staged kernels load the tiles of
  * converged members too);
+ * precision 64 with path 0: 1 = margins read from global memory (two
+ * 512-thread blocks per SM), 2 = margins copied into shared memory (one
+ * 1024-thread block per SM, n <= 14464);
  * precision 64 with path 2: 1 = 8 products per lane at two 512-thread blocks per
  * SM, 2 = 8 per lane at three blocks per SM, 3 = 4 per lane at three blocks
- * per SM. *choice_out (or NULL) gets the choice (1 when there is none, as for
- * precision 64 with path 0). */
+ * per SM. *choice_out (or NULL) gets the choice (1 when there is none). */
 spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* choice_out);
 
 /* ---- Recovering assortments (Section 4.4) ----------------------------------

@@ -352,7 +352,7 @@ spfom_status spfom_create(const spfom_params* p, spfom_ctx** out) {
   if (prm.precision != 64 && prm.precision != 32) return SPFOM_ENOTSUP;
   if (!(prm.batch_frac > 0.0) || !(prm.restart_beta >= 0.0) || !(prm.kkt_tol >= 0.0) || prm.tau0 < 0 ||
       prm.mu < 0 || !(prm.restart_tau_decay > 0.0) ||
-      !(prm.restart_tau_balance >= 0.0 && prm.restart_tau_balance <= 1.0) || prm.tiling < 0 || prm.tiling > 6)
+      !(prm.restart_tau_balance >= 0.0 && prm.restart_tau_balance <= 1.0) || prm.tiling < 0 || prm.tiling > 8)
     return SPFOM_EINVAL;
   spfom_ctx* ctx = new (std::nothrow) spfom_ctx;
   if (!ctx) return SPFOM_ENOMEM;
@@ -542,6 +542,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       if (plan.coop_ok) W.zparts_iter = std::max(W.zparts_iter, plan.coop_grid);
       if (plan.bchunk_ok) W.zparts_iter = std::max(W.zparts_iter, plan.bchunk_grid);
       if (plan.bchunk64_ok) W.zparts_iter = std::max(W.zparts_iter, plan.bchunk64_grid);
+      if (plan.ms_ok) W.zparts_iter = std::max(W.zparts_iter, std::max(plan.ms_grid, plan.ms_grid32));
       W.zparts_eval = plan.grid_eval;
       if (dd)
         for (int v = 1; v <= 3; ++v) {
@@ -549,19 +550,32 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
           W.zparts_eval = std::max(W.zparts_eval, plan.dd_grid_eval[v]);
         }
       W.dd_ok = dd;
+      // slot-major copy for the sliced tilings (single instances, path 0)
+      W.plan.sl_ok = ctx->p.path == 0 && !ctx->loading_batch && L > 0 && plan.sl_attr && plan.W8 <= 4 ? 1 : 0;
       if (ctx->p.tiling > 0) {  // a requested tiling of the active segment pass
         const int t = ctx->p.tiling;
-        bool ok = t <= 6;
+        bool ok = t <= 8;
         if (ok && ctx->p.precision == 32) {
-          ok = (t != 2 || W.plan.tma_ok) && (t != 4 || W.plan.coop_ok) && (t != 6 || W.plan.bchunk_ok);
+          ok = (t != 2 || W.plan.tma_ok) && (t != 4 || W.plan.coop_ok) && (t != 6 || W.plan.bchunk_ok) &&
+               (t != 7 || W.plan.ms_ok) && (t != 8 || W.plan.sl_ok);
           W.plan.bchunk = t == 6 ? 1 : 0;
           W.plan.tma = t == 2 ? 1 : 0;
           W.plan.f32_p8 = t == 3 ? 1 : 0;
           W.plan.coop = t == 4 ? 1 : 0;
           W.plan.f32_p16 = t == 5 ? 1 : 0;
+          W.plan.f32_ms = t == 7 ? 1 : 0;
+          W.plan.f32_sl = t == 8 ? 1 : 0;
         } else if (ok) {
-          ok = dd ? spfom::dd_variant_ok(W.plan, t) != 0 : t == 1;  // the binary64-sum kernel has one tiling
-          if (dd) W.plan.dd_variant = t;
+          // double-float kernel: its tilings 1..3; binary64-sum kernel: 1 = margins read
+          // from global memory, 2 = margins in shared memory, 3 = slot-major copy
+          ok = dd ? spfom::dd_variant_ok(W.plan, t) != 0
+                  : (t == 1 || (t == 2 && W.plan.ms_ok) || (t == 3 && W.plan.sl_ok));
+          if (dd) {
+            W.plan.dd_variant = t;
+          } else {
+            W.plan.fast_ms = t == 2 ? 1 : 0;
+            W.plan.fast_sl = t == 3 ? 1 : 0;
+          }
         }
         if (!ok) {
           free_instance(ctx);
@@ -615,6 +629,33 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
     SPFOM_TRY(dalloc(ctx, &W.xsum, (size_t)(nnz > 0 ? nnz : 1)));
     SPFOM_CUDA(ctx, cudaMemsetAsync(W.xsum, 0, sizeof(double) * (size_t)(nnz > 0 ? nnz : 1), ctx->stream));
   }
+  W.sl = spfom::SlView{};
+  W.sl_perm = nullptr;
+  if (W.fast && W.plan.sl_ok) {
+    // slot-major copy: positions and chunk offsets here, the items gathered on the device below
+    std::vector<long long> perm, off;
+    const long long nch =
+        spfom::sliced_layout(reinterpret_cast<const long long*>(I->seg_ptr), L, W.plan.W8, &perm, &off);
+    const size_t entries = (size_t)std::max(off[(size_t)nch], 1ll), npos = perm.size();
+    SPFOM_TRY(upload(ctx, &W.sl.off, off.data(), off.size()));
+    SPFOM_TRY(upload(ctx, &W.sl_perm, perm.data(), npos));
+    SPFOM_TRY(dalloc(ctx, &W.sl.prod, entries));
+    if (ctx->p.precision == 32) {
+      SPFOM_TRY(dalloc(ctx, &W.sl.v32, entries));
+      SPFOM_TRY(dalloc(ctx, &W.sl.vt32, entries));
+      SPFOM_TRY(dalloc(ctx, &W.sl.lam32, npos));
+      SPFOM_TRY(dalloc(ctx, &W.sl.vt0_32, npos));
+    } else {
+      SPFOM_TRY(dalloc(ctx, &W.sl.v, entries));
+      SPFOM_TRY(dalloc(ctx, &W.sl.vt, entries));
+      SPFOM_TRY(dalloc(ctx, &W.sl.lam, npos));
+      SPFOM_TRY(dalloc(ctx, &W.sl.vt0, npos));
+    }
+    SPFOM_TRY(dalloc(ctx, &W.sl.rprev, npos));
+    SPFOM_CUDA(ctx, cudaMemsetAsync(W.sl.rprev, 0, sizeof(float) * npos, ctx->stream));
+    W.sl.nchunks = nch;
+    SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the host vectors go out of scope
+  }
 #undef SPFOM_TRY
   ctx->P = P;
   if (W.v2) {
@@ -624,6 +665,11 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   if (W.v32) {
     e = spfom::launch_prep_f32(P, W, ctx->stream);
     if (e != cudaSuccess) { free_instance(ctx); return cuda_fail(ctx, e, "binary32 copies"); }
+  }
+  if (W.sl.nchunks > 0) {
+    e = spfom::launch_slice_items(P, W, W.plan.W8, ctx->stream);
+    if (e == cudaSuccess) e = spfom::launch_slice_segments(P, W, W.plan.W8, ctx->stream);
+    if (e != cudaSuccess) { free_instance(ctx); return cuda_fail(ctx, e, "slot-major copy"); }
   }
   // step size: tau, or tau0 * mean(r) / mean(c) (sums in index order)
   double sr = 0.0, sc = 0.0;
@@ -1079,6 +1125,10 @@ spfom_status spfom_update(spfom_ctx* ctx, const double* c, const double* lam) {
       cudaError_t e = spfom::launch_dd_prep(P, ctx->W.v2, ctx->W.vt2, ctx->W.seg4, ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "double-float images");
     }
+    if (ctx->W.sl.nchunks > 0) {  // lambda of the slot-major copy
+      cudaError_t e = spfom::launch_slice_segments(P, ctx->W, ctx->W.plan.W8, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "slot-major copy");
+    }
   }
   // step sizes follow the new capacities: tau0 * mean(r) / mean(c), per instance in a batch
   if (c && !(ctx->p.tau > 0.0)) {
@@ -1128,19 +1178,26 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
   if (iters <= 0) return fail(ctx, SPFOM_EINVAL, "iters must be > 0");
   spfom::FastPlan& plan = ctx->W.plan;
-  // binary32 pass: 1 = plain loads, 4 products per lane; 2 = staged tiles; 3 = plain loads, 8 per lane.
-  // double-float binary64 pass: the tilings of k_seg_dd (1..3).
+  // binary32 pass: the tilings 1..7 of include/spfom.h; double-float binary64 pass: the
+  // tilings of k_seg_dd (1..3); binary64-sum pass: 1, and 2 (margins in shared memory).
   const bool f32 = ctx->W.fast && ctx->W.v32 && ctx->cfg.f32;
   const bool dd = ctx->W.fast && ctx->W.v2 && !ctx->cfg.f32;
+  const bool f64 = ctx->W.fast && !ctx->cfg.f32 && !dd;
   auto current = [&]() {
-    return f32 ? (plan.bchunk ? 6 : (plan.f32_p16 ? 5 : (plan.coop ? 4 : (plan.tma ? 2 : (plan.f32_p8 ? 3 : 1)))))
-               : (dd ? plan.dd_variant : 1);
+    return f32 ? (plan.f32_sl ? 8 : plan.f32_ms ? 7
+                              : (plan.bchunk ? 6
+                                             : (plan.f32_p16 ? 5
+                                                             : (plan.coop ? 4 : (plan.tma ? 2 : (plan.f32_p8 ? 3 : 1))))))
+               : (dd ? plan.dd_variant : (plan.fast_sl ? 3 : (plan.fast_ms ? 2 : 1)));
   };
   // The staged kernels (2, 4) load whole tiles even when a batch has frozen
   // (converged) members, which the plain-load kernels skip; their early timing
   // would not hold over a batched solve, so batches choose among the plain-load
   // tilings.
   auto available = [&](int c) {
+    if (f32 && c == 7) return plan.ms_ok != 0;
+    if (f32 && c == 8) return ctx->W.sl.nchunks > 0;
+    if (f64) return c == 1 || (c == 2 && plan.ms_ok != 0) || (c == 3 && ctx->W.sl.nchunks > 0);
     if (f32 && c == 6) return plan.bchunk_ok != 0 && ctx->W.batch && ctx->W.bc_count > 0;
     if (f32) return c == 4 ? (plan.coop_ok != 0 && !ctx->W.batch) : (c != 2 || (plan.tma_ok && !ctx->W.batch));
     return c <= 3 && dd && spfom::dd_variant_ok(plan, c);
@@ -1152,11 +1209,16 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
       plan.coop = c == 4 ? 1 : 0;
       plan.f32_p16 = c == 5 ? 1 : 0;
       plan.bchunk = c == 6 ? 1 : 0;
-    } else {
+      plan.f32_ms = c == 7 ? 1 : 0;
+      plan.f32_sl = c == 8 ? 1 : 0;
+    } else if (dd) {
       plan.dd_variant = c;
+    } else {
+      plan.fast_ms = c == 2 ? 1 : 0;
+      plan.fast_sl = c == 3 ? 1 : 0;
     }
   };
-  if (!f32 && !dd) {
+  if (!f32 && !dd && !(f64 && (plan.ms_ok || ctx->W.sl.nchunks > 0))) {
     if (choice_out) *choice_out = 1;
     return SPFOM_OK;
   }
@@ -1170,7 +1232,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   ctx->cfg.kkt_tol = -1.0;  // no instance may converge (and stop working) while being timed
   double best = INFINITY;
   int choice = current();
-  for (int cand = 1; cand <= 6; ++cand) {
+  for (int cand = 1; cand <= 8; ++cand) {
     if (!available(cand)) continue;
     select(cand);
     drop_graphs(ctx);

@@ -74,6 +74,7 @@ struct Problem {
 constexpr int kFastThreads = 512;
 constexpr int kFastMaxSmem = 200 * 1024;
 constexpr int kTmaThreads = 1024;
+constexpr int kMsThreads = 1024;  // block of the margins-in-shared segment kernels (one per SM)
 constexpr int kTmaMaxSmem = 226 * 1024;
 constexpr int kPipeThreads = 512;    // binary64 pipeline: 1 producer warp + 15 consumer warps
 constexpr int kTile64Segs = 256;     // binary64 pipeline tile: segments
@@ -106,8 +107,38 @@ struct FastPlan {
   int dd_grid_eval[4];  // and for the evaluation pass
   int tma_smem;       // its dynamic shared memory: product sums + two stages
   int acc_bytes;      // bytes of the product sums at the start of that memory
+  int ms_ok;          // 1 when the margins-in-shared kernels fit (scatter 1, 16 n bytes of shared memory)
+  int ms_smem64, ms_smem32, ms_grid, ms_grid32;
+  int fast_ms;        // 1: the binary64 pass runs k_seg_fast with the margins in shared memory (tiling 2)
+  int f32_ms;         // 1: the binary32 pass runs k_seg_f32 with the margins in shared memory (tiling 7)
+  int fast_sl;        // 1: the binary64 pass reads the slot-major copy (tiling 3; margins shared when ms_ok)
+  int f32_sl;         // 1: the binary32 pass reads the slot-major copy (tiling 8; margins shared when ms_ok)
+  int sl_attr;        // 1 when the slot-major kernels accept the plan's shared memory
+  int sl_ok;          // 1 when the load builds the slot-major copy (single instance, path 0)
   int pipe;           // 1: the binary64 pass runs k_seg_fast_pipe (warp-specialised TMA pipeline)
   int pipe_smem, pipe_acc_bytes, pipe_grid;
+};
+
+// Slot-major copy of the consideration sets (the sliced tilings): positions
+// = the segments sorted by set size, descending (ties: segment order), cut into
+// chunks of C = 32 / W8 positions, one warp per chunk. Chunk c stores its slot
+// rows p = 0 .. rows_c - 1 (rows_c = ceil(largest set of the chunk / W8)), 32
+// entries each, at off[c] + 32 p: entry g W8 + r of row p is product r + p W8
+// of the chunk's g-th segment (id -1, v = vt = 0 past the set's end or for a
+// position past L). Each slot row of a warp is then one contiguous line.
+struct SlView {
+  long long* off;   // [nchunks + 1] first entry of each chunk (multiples of 32)
+  int* prod;        // [off[nchunks]]
+  double* v;        // [off[nchunks]] binary64 v and v - w (precision 64), else null
+  double* vt;
+  float* v32;       // binary32 images (precision 32), else null
+  float* vt32;
+  double* lam;      // [nchunks * C] per position; lam = 0, vt0 = 1 past L
+  double* vt0;
+  float* lam32;
+  float* vt0_32;
+  float* rprev;     // [nchunks * C] carried Dinkelbach ratio per position
+  long long nchunks;
 };
 
 // Work buffers of one ctx.
@@ -166,6 +197,8 @@ struct Work {
   long long ntiles64;
   bool batch;             // instances of a batch (spfom_load_batch)
   BatchMaps bm;
+  SlView sl;              // slot-major copy (sliced tilings), nchunks = 0 when absent
+  long long* sl_perm;     // [nchunks * C] segment at each position, -1 past L
 };
 
 struct FastArgs {
@@ -194,6 +227,7 @@ struct FastArgs {
   const long long* bc_seg;
   const int* bc_inst;
   const int* bc_prod_ptr;
+  SlView sl;  // slot-major copy (sliced tilings)
 };
 
 // Arguments of k_seg_dd (spfom_segments_dd.cu): double-float images, and the
@@ -258,6 +292,7 @@ struct F32Args {
   const long long* bc_seg;   // [bc_count + 1] first segment of each chunk
   const int* bc_inst;        // [bc_count] instance of each chunk
   const int* bc_prod_ptr;    // [instances + 1] product offsets
+  SlView sl;                 // slot-major copy (sliced tilings)
 };
 
 struct RunConfig {
@@ -330,5 +365,11 @@ cudaError_t launch_reduce_products(const Problem& P, const FastPlan& plan, int n
                                    cudaStream_t s);
 // binary32 copies of v, vt, lambda, vt0 for the precision-32 mode
 cudaError_t launch_prep_f32(const Problem& P, Work& Wk, cudaStream_t s);
+// slot-major copy (spfom_sliced.cu): host layout (positions, chunk offsets;
+// returns the chunk count), the gather of the items, and of lambda / vt_0
+long long sliced_layout(const long long* seg_ptr, long long L, int W8, std::vector<long long>* perm,
+                        std::vector<long long>* off);
+cudaError_t launch_slice_items(const Problem& P, const Work& Wk, int W8, cudaStream_t s);
+cudaError_t launch_slice_segments(const Problem& P, const Work& Wk, int W8, cudaStream_t s);
 
 }  // namespace spfom

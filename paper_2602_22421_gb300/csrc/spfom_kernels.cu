@@ -431,20 +431,29 @@ cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfi
               Wk.part, Wk.s_fx, Wk.zpart, Wk.st, Wk.tile_ptr, Wk.ntiles, Wk.plan.acc_bytes, Wk.st,
               seg_inst, conv, z_seg, Wk.coop_tile_ptr, Wk.coop_ntiles, Wk.plan.coop_items, Wk.plan.coop_segs,
               Wk.rprev, 0, 0, Wk.batch ? Wk.bc_count : 0, Wk.bc_seg, Wk.bc_inst,
-              Wk.batch ? Wk.bm.prod_ptr : nullptr};
+              Wk.batch ? Wk.bm.prod_ptr : nullptr, Wk.sl};
     const bool bchunk = Wk.plan.bchunk && Wk.batch && Wk.bc_count > 0;
-    *zparts_out = bchunk ? Wk.plan.bchunk_grid
-                         : (Wk.plan.coop ? Wk.plan.coop_grid : (Wk.plan.tma ? Wk.plan.tma_grid : Wk.plan.grid32));
+    const FastPlan& pl = Wk.plan;
+    if (!bchunk && pl.f32_sl && Wk.sl.nchunks > 0) {
+      *zparts_out = pl.ms_ok ? pl.ms_grid32 : pl.grid32;
+      return launch_seg_f32(A, pl, s);
+    }
+    *zparts_out = bchunk ? pl.bchunk_grid
+                         : (pl.coop ? pl.coop_grid
+                                    : (pl.tma ? pl.tma_grid
+                                              : (pl.f32_p16 ? pl.grid32 : (pl.f32_ms && pl.ms_ok ? pl.ms_grid32 : pl.grid32))));
     return launch_seg_f32(A, Wk.plan, s);
   }
   FastArgs A{P, marg, Wk.part, Wk.zpart, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, Wk.s_fx,
              Wk.tile64_ptr, Wk.ntiles64, Wk.plan.pipe_acc_bytes, Wk.st, seg_inst, conv, z_seg, Wk.rprev, 0, 0,
-             Wk.batch ? Wk.bc_count : 0, Wk.bc_seg, Wk.bc_inst, Wk.batch ? Wk.bm.prod_ptr : nullptr};
+             Wk.batch ? Wk.bc_count : 0, Wk.bc_seg, Wk.bc_inst, Wk.batch ? Wk.bm.prod_ptr : nullptr, Wk.sl};
   if (Wk.plan.pipe && !Wk.batch) {
     *zparts_out = Wk.plan.pipe_grid;
     return launch_seg_fast_pipe(A, Wk.plan, s);
   }
-  *zparts_out = (Wk.plan.bchunk64_ok && A.bc_count > 0) ? Wk.plan.bchunk64_grid : Wk.plan.grid;
+  if (Wk.plan.bchunk64_ok && A.bc_count > 0) *zparts_out = Wk.plan.bchunk64_grid;
+  else if ((Wk.plan.fast_sl && Wk.sl.nchunks > 0) || Wk.plan.fast_ms) *zparts_out = Wk.plan.ms_ok ? Wk.plan.ms_grid : Wk.plan.grid;
+  else *zparts_out = Wk.plan.grid;
   return launch_seg_fast(A, Wk.plan, true, s);
 }
 

@@ -83,13 +83,20 @@ struct SegOrder {
 // One segment of the certified-decision pass (see the file comment): the
 // binary32 Dinkelbach decision with its certificate (binary64 redo when it
 // fails), binary64 values, and the fixed-point sales added to sums[j - base]
-// (none when sums is null). Called by all W lanes of the segment's group.
-template <int W, int P>
-__device__ __forceinline__ void fast_segment(const FastArgs& A, long long l, int lane, unsigned gmask,
-                                             unsigned long long* sums, int base, double& zacc, int& fallbacks) {
-  const Problem& Pr = A.P;
-  const long long b = Pr.seg_ptr[l];
-  const int K = (int)(Pr.seg_ptr[l + 1] - b);
+// (none when sums is null); mg = the margins (global or shared memory).
+// Called by all W lanes of the segment's group. The lane's slot p (product
+// lane + p W of the set) is sp[p T], vv[p T], vtv[p T] with T = W for the CSR
+// layout (slot valid iff lane + p W < lim = K) and T = 32 for the slot-major
+// layout (slot valid iff p < lim = the chunk's slot rows and its id >= 0).
+// rp: the segment's carried Dinkelbach ratio (or null); zs: where to write its
+// value (or null: added to zacc).
+template <int W, int P, bool SL>
+__device__ __forceinline__ void seg_solve(const FastArgs& A, const double* __restrict__ mg,
+                                          const int* __restrict__ sp, const double* __restrict__ vv,
+                                          const double* __restrict__ vtv, int lim, double lam, double vt0, float* rp,
+                                          double* zs, int lane, unsigned gmask, unsigned long long* sums, int base,
+                                          double& zacc, int& fallbacks) {
+  constexpr int T = SL ? 32 : W;
   // Registers hold the binary32 images a = m v, b = vt and the product ids;
   // the binary64 values are read again (L1) for the products chosen.
   int jv[P];
@@ -98,26 +105,27 @@ __device__ __forceinline__ void fast_segment(const FastArgs& A, long long l, int
   bool ok = true;
 #pragma unroll
   for (int p = 0; p < P; ++p) {
-    const int k = lane + p * W;
     jv[p] = 0;
     af[p] = bf[p] = 0.f;
-    if (k < K) {
-      jv[p] = Pr.seg_prod[b + k];
-      const double m = A.marg[jv[p]];
-      if (__double_as_longlong(m) > 0) {  // m_j > 0
-        cand |= 1u << p;
-        af[p] = f32_trunc(m, ok) * f32_trunc(Pr.v[b + k], ok);
-        bf[p] = f32_trunc(Pr.vt[b + k], ok);
+    if (SL ? p < lim : lane + p * W < lim) {
+      const int j = sp[p * T];
+      if (!SL || j >= 0) {
+        jv[p] = j;
+        const double m = mg[j];
+        if (__double_as_longlong(m) > 0) {  // m_j > 0
+          cand |= 1u << p;
+          af[p] = f32_trunc(m, ok) * f32_trunc(vv[p * T], ok);
+          bf[p] = f32_trunc(vtv[p * T], ok);
+        }
       }
     }
   }
-  const double lam = Pr.lam[l], vt0 = Pr.vt0[l];
   const float vt0f = f32_trunc(vt0, ok);
   // Dinkelbach in binary32, started at the segment's ratio of the previous
   // iteration (any start reaches a fixed point, and every fixed point is
   // optimal; the margins move little between iterations, so this one is
   // usually confirmed by the second pass).
-  float R = A.rprev ? A.rprev[l] : 0.f;
+  float R = rp ? *rp : 0.f;
   unsigned sel = 0xffffffffu;  // no previous set
   bool conv = false;
   for (int it = 0; it < P * W + 3; ++it) {
@@ -142,7 +150,7 @@ __device__ __forceinline__ void fast_segment(const FastArgs& A, long long l, int
     R = __fdividef(N, vt0f + D);
     sel = s;
   }
-  if (A.rprev && lane == 0 && conv) A.rprev[l] = R;
+  if (rp && lane == 0 && conv) *rp = R;
   bool good = ok && conv;
 #pragma unroll
   for (int p = 0; p < P; ++p)
@@ -162,8 +170,7 @@ __device__ __forceinline__ void fast_segment(const FastArgs& A, long long l, int
 #pragma unroll
       for (int p = 0; p < P; ++p)
         if ((cand >> p) & 1u) {
-          const int k = lane + p * W;
-          const double a = A.marg[jv[p]] * Pr.v[b + k], t = Pr.vt[b + k];
+          const double a = mg[jv[p]] * vv[p * T], t = vtv[p * T];
           if (a > Rd * t) {
             s |= 1u << p;
             N += a;
@@ -186,9 +193,8 @@ __device__ __forceinline__ void fast_segment(const FastArgs& A, long long l, int
 #pragma unroll
   for (int p = 0; p < P; ++p)
     if ((S >> p) & 1u) {
-      const int k = lane + p * W;
-      Dl += Pr.vt[b + k];
-      Nl = fma(A.marg[jv[p]], Pr.v[b + k], Nl);
+      Dl += vtv[p * T];
+      Nl = fma(mg[jv[p]], vv[p * T], Nl);
     }
 #pragma unroll
   for (int o = W >> 1; o > 0; o >>= 1) {
@@ -197,24 +203,48 @@ __device__ __forceinline__ void fast_segment(const FastArgs& A, long long l, int
   }
   const double q = quotient(lam, vt0 + Dl);
   if (lane == 0) {
-    if (A.z_seg) A.z_seg[l] = q * Nl;
+    if (zs) *zs = q * Nl;
     else zacc += q * Nl;
   }
   if (sums) {
 #pragma unroll
     for (int p = 0; p < P; ++p)
-      if ((S >> p) & 1u) atomicAdd(sums + (jv[p] - base), fixed_product(q, Pr.v[b + lane + p * W], A.fx_bits));
+      if ((S >> p) & 1u) atomicAdd(sums + (jv[p] - base), fixed_product(q, vv[p * T], A.fx_bits));
   }
 }
 
-template <int W, int P, int SC>
-__global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
-  extern __shared__ unsigned long long acc[];  // [n] product sales (fixed point) when SC == 1
+// One segment l of the CSR layout.
+template <int W, int P>
+__device__ __forceinline__ void fast_segment(const FastArgs& A, const double* __restrict__ mg, long long l, int lane,
+                                             unsigned gmask, unsigned long long* sums, int base, double& zacc,
+                                             int& fallbacks) {
+  const Problem& Pr = A.P;
+  const long long b = Pr.seg_ptr[l];
+  const int K = (int)(Pr.seg_ptr[l + 1] - b);
+  seg_solve<W, P, false>(A, mg, Pr.seg_prod + b + lane, Pr.v + b + lane, Pr.vt + b + lane, K, Pr.lam[l], Pr.vt0[l],
+                         A.rprev ? A.rprev + l : nullptr, A.z_seg ? A.z_seg + l : nullptr, lane, gmask, sums, base,
+                         zacc, fallbacks);
+}
+
+// MS = 1 (tilings 2, 3; needs SC == 1): one block of 1024 threads per SM that
+// also copies the n binary64 margins into shared memory after the sums, so the
+// gather of a segment's margins reads shared memory instead of L2.
+// SL = 1 (tiling 3): the slot-major copy, one warp per chunk of 32 / W
+// positions, every slot row one contiguous load of the warp.
+template <int W, int P, int SC, int MS = 0, int SL = 0>
+__global__ void __launch_bounds__(MS ? kMsThreads : kFastThreads, MS ? 1 : 2) k_seg_fast(FastArgs A) {
+  extern __shared__ unsigned long long acc[];  // [n] product sales (fixed point) when SC == 1; MS: + [n] margins
   __shared__ double sh[32];
   if (A.st && A.st->converged) return;
   const Problem& Pr = A.P;
+  const double* mg = A.marg;
   if (SC == 1) {
-    for (int j = threadIdx.x; j < Pr.n; j += blockDim.x) acc[j] = 0ull;
+    double* smg = reinterpret_cast<double*>(acc + Pr.n);
+    for (int j = threadIdx.x; j < Pr.n; j += blockDim.x) {
+      acc[j] = 0ull;
+      if (MS) smg[j] = A.marg[j];
+    }
+    if (MS) mg = smg;
     __syncthreads();
   }
   const int lane = threadIdx.x & (W - 1);
@@ -222,12 +252,25 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast(FastArgs A) {
   const unsigned gmask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << gbase);
   double zacc = 0.0;
   int fallbacks = 0;
-  SegOrder ord(Pr.L, W, A.perm_a, A.perm_d);
-  for (long long ch = ord.first; ch < ord.nchunks; ch += ord.nwarps) {
-    const long long l = ord.next();
-    if (l >= Pr.L) continue;
-    if (A.seg_inst && A.inst_conv[A.seg_inst[l]]) continue;  // batch: instance already converged
-    fast_segment<W, P>(A, l, lane, gmask, SC == 0 ? nullptr : (SC == 1 ? acc : A.s_fx), 0, zacc, fallbacks);
+  unsigned long long* sums = SC == 0 ? nullptr : (SC == 1 ? acc : A.s_fx);
+  if (SL) {
+    const int wl = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < A.sl.nchunks; c += nw) {
+      const long long o = A.sl.off[c] + wl;
+      const int rows = (int)((A.sl.off[c + 1] - A.sl.off[c]) >> 5);
+      const long long pos = c * (32 / W) + wl / W;
+      seg_solve<W, P, true>(A, mg, A.sl.prod + o, A.sl.v + o, A.sl.vt + o, rows, A.sl.lam[pos], A.sl.vt0[pos],
+                            A.sl.rprev ? A.sl.rprev + pos : nullptr, nullptr, lane, gmask, sums, 0, zacc, fallbacks);
+    }
+  } else {
+    SegOrder ord(Pr.L, W, A.perm_a, A.perm_d);
+    for (long long ch = ord.first; ch < ord.nchunks; ch += ord.nwarps) {
+      const long long l = ord.next();
+      if (l >= Pr.L) continue;
+      if (A.seg_inst && A.inst_conv[A.seg_inst[l]]) continue;  // batch: instance already converged
+      fast_segment<W, P>(A, mg, l, lane, gmask, sums, 0, zacc, fallbacks);
+    }
   }
   const double tot = block_sum_d(zacc, sh);
   if (threadIdx.x == 0) A.zpart[blockIdx.x] = tot;
@@ -262,7 +305,7 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast_bchunk(FastArgs A)
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += blockDim.x) acc[i] = 0ull;
     __syncthreads();
-    for (long long l = l0 + threadIdx.x / W; l < l1; l += gpb) fast_segment<W, P>(A, l, lane, gmask, acc, pb, zacc, fallbacks);
+    for (long long l = l0 + threadIdx.x / W; l < l1; l += gpb) fast_segment<W, P>(A, A.marg, l, lane, gmask, acc, pb, zacc, fallbacks);
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += blockDim.x)
       if (acc[i]) atomicAdd(A.s_fx + pb + i, acc[i]);
@@ -272,92 +315,126 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast_bchunk(FastArgs A)
   if (fallbacks && A.fallbacks) atomicAdd(A.fallbacks, (unsigned long long)fallbacks);
 }
 
+// One segment of the binary32 bulk pass (k_seg_f32): the lane's slot p is
+// sp[p T], v32[p T], vt32[p T] with T = W (CSR layout, slot valid iff
+// lane + p W < lim = K) or T = 32 (slot-major layout, slot valid iff p < lim =
+// the chunk's slot rows and its id >= 0); rp / zs as in seg_solve.
+template <int W, int P, int SC, bool SL>
+__device__ __forceinline__ void f32_solve(const F32Args& A, const float* __restrict__ mg, const int* __restrict__ sp,
+                                          const float* __restrict__ v32, const float* __restrict__ vt32, int lim,
+                                          float lam, float vt0, float* rp, double* zs, int lane, unsigned gmask,
+                                          unsigned long long* sums, float& zacc) {
+  constexpr int T = SL ? 32 : W;
+  int jv[P];
+  float tv[P], af[P];
+  unsigned cand = 0;
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    jv[p] = 0;
+    tv[p] = af[p] = 0.f;
+    if (SL ? p < lim : lane + p * W < lim) {
+      jv[p] = sp[p * T];
+      af[p] = v32[p * T];
+      tv[p] = vt32[p * T];
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p)
+    if (SL ? (p < lim && jv[p] >= 0) : lane + p * W < lim) {
+      const float m = mg[jv[p]];
+      if (m > 0.f) {
+        cand |= 1u << p;
+        af[p] = m * af[p];
+      } else {
+        af[p] = 0.f;
+      }
+    }
+  float R = rp ? *rp : 0.f, Nsel = 0.f, Dsel = 0.f;  // Dinkelbach from the last ratio
+  unsigned sel = 0xffffffffu;
+  for (int it = 0; it < P * W + 3; ++it) {
+    unsigned s = 0;
+    float N = 0.f, D = 0.f;
+#pragma unroll
+    for (int p = 0; p < P; ++p)
+      if (((cand >> p) & 1u) && af[p] > R * tv[p]) {
+        s |= 1u << p;
+        N += af[p];
+        D += tv[p];
+      }
+    if (__all_sync(gmask, s == sel)) break;
+#pragma unroll
+    for (int o = W >> 1; o > 0; o >>= 1) {
+      N += __shfl_xor_sync(gmask, N, o, W);
+      D += __shfl_xor_sync(gmask, D, o, W);
+    }
+    R = __fdividef(N, vt0 + D);
+    sel = s;
+    Nsel = N;
+    Dsel = D;
+  }
+  if (rp && lane == 0) *rp = R;
+  const float q = lam / (vt0 + Dsel);
+  if (lane == 0) {
+    if (zs) *zs = (double)(q * Nsel);
+    else zacc += q * Nsel;
+  }
+  if (SC != 0) {
+    for (unsigned msk = sel; msk; msk &= msk - 1) {  // this lane's chosen slots
+      const int k = (__ffs(msk) - 1) * T;
+      atomicAdd(sums + sp[k], fixed_product32(q, v32[k], A.fx_bits));
+    }
+  }
+}
+
 // Binary32 bulk iteration (the precision-32 mode): the same decision as
 // k_seg_fast without certificate, and binary32 values: the final Dinkelbach
 // set's N and D give q = lambda / (vt0 + D) and z = q N; the sales are the exact
 // products q v rounded once to fixed point. Reads 12 B per nonzero.
-template <int W, int P, int SC>
-__global__ void __launch_bounds__(kFastThreads, 2) k_seg_f32(F32Args A) {
-  extern __shared__ unsigned long long acc[];
+// MS = 1 (tilings 7, 8; needs SC == 1): one block of 1024 threads per SM with
+// the binary32 margins copied into shared memory after the sums. SL = 1
+// (tiling 8): the slot-major copy, one warp per chunk.
+template <int W, int P, int SC, int MS = 0, int SL = 0>
+__global__ void __launch_bounds__(MS ? kMsThreads : kFastThreads, MS ? 1 : 2) k_seg_f32(F32Args A) {
+  extern __shared__ unsigned long long acc[];  // [n] sums when SC == 1; MS: + [n] binary32 margins
   __shared__ double sh[32];
   if (A.st->converged) return;
+  const float* mg = A.marg32;
   if (SC == 1) {
-    for (int j = threadIdx.x; j < A.n; j += blockDim.x) acc[j] = 0ull;
+    float* smg = reinterpret_cast<float*>(acc + A.n);
+    for (int j = threadIdx.x; j < A.n; j += blockDim.x) {
+      acc[j] = 0ull;
+      if (MS) smg[j] = A.marg32[j];
+    }
+    if (MS) mg = smg;
     __syncthreads();
   }
   const int lane = threadIdx.x & (W - 1);
   const int gbase = (threadIdx.x & 31) & ~(W - 1);
   const unsigned gmask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << gbase);
   float zacc = 0.f;
-  SegOrder ord(A.L, W, A.perm_a, A.perm_d);
-  for (long long ch = ord.first; ch < ord.nchunks; ch += ord.nwarps) {
-    const long long l = ord.next();
-    if (l >= A.L) continue;
-    if (A.seg_inst && A.inst_conv[A.seg_inst[l]]) continue;  // batch: instance already converged
-    const long long b = A.seg_ptr[l];
-    const int K = (int)(A.seg_ptr[l + 1] - b);
-    const int* __restrict__ sp = A.seg_prod + b;  // the segment's slice of the consideration-set CSR
-    const float* __restrict__ v32 = A.v32 + b;
-    int jv[P];
-    float tv[P], af[P];
-    unsigned cand = 0;
-#pragma unroll
-    for (int p = 0; p < P; ++p) {
-      const int k = lane + p * W;
-      jv[p] = 0;
-      tv[p] = af[p] = 0.f;
-      if (k < K) {
-        jv[p] = sp[k];
-        af[p] = v32[k];
-        tv[p] = A.vt32[b + k];
-      }
+  unsigned long long* sums = SC == 1 ? acc : A.s_fx;
+  if (SL) {
+    const int wl = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < A.sl.nchunks; c += nw) {
+      const long long o = A.sl.off[c] + wl;
+      const int rows = (int)((A.sl.off[c + 1] - A.sl.off[c]) >> 5);
+      const long long pos = c * (32 / W) + wl / W;
+      f32_solve<W, P, SC, true>(A, mg, A.sl.prod + o, A.sl.v32 + o, A.sl.vt32 + o, rows, A.sl.lam32[pos],
+                                A.sl.vt0_32[pos], A.sl.rprev ? A.sl.rprev + pos : nullptr, nullptr, lane, gmask, sums,
+                                zacc);
     }
-#pragma unroll
-    for (int p = 0; p < P; ++p)
-      if (lane + p * W < K) {
-        const float m = A.marg32[jv[p]];
-        if (m > 0.f) {
-          cand |= 1u << p;
-          af[p] = m * af[p];
-        } else {
-          af[p] = 0.f;
-        }
-      }
-    const float lam = A.lam32[l], vt0 = A.vt0_32[l];
-    float R = A.rprev ? A.rprev[l] : 0.f, Nsel = 0.f, Dsel = 0.f;  // Dinkelbach from the last ratio
-    unsigned sel = 0xffffffffu;
-    for (int it = 0; it < P * W + 3; ++it) {
-      unsigned s = 0;
-      float N = 0.f, D = 0.f;
-#pragma unroll
-      for (int p = 0; p < P; ++p)
-        if (((cand >> p) & 1u) && af[p] > R * tv[p]) {
-          s |= 1u << p;
-          N += af[p];
-          D += tv[p];
-        }
-      if (__all_sync(gmask, s == sel)) break;
-#pragma unroll
-      for (int o = W >> 1; o > 0; o >>= 1) {
-        N += __shfl_xor_sync(gmask, N, o, W);
-        D += __shfl_xor_sync(gmask, D, o, W);
-      }
-      R = __fdividef(N, vt0 + D);
-      sel = s;
-      Nsel = N;
-      Dsel = D;
-    }
-    if (A.rprev && lane == 0) A.rprev[l] = R;
-    const float q = lam / (vt0 + Dsel);
-    if (lane == 0) {
-      if (A.z_seg) A.z_seg[l] = (double)(q * Nsel);
-      else zacc += q * Nsel;
-    }
-    if (SC != 0) {
-      for (unsigned msk = sel; msk; msk &= msk - 1) {  // this lane's chosen slots
-        const int k = lane + (__ffs(msk) - 1) * W;
-        atomicAdd((SC == 1 ? acc : A.s_fx) + sp[k], fixed_product32(q, v32[k], A.fx_bits));
-      }
+  } else {
+    SegOrder ord(A.L, W, A.perm_a, A.perm_d);
+    for (long long ch = ord.first; ch < ord.nchunks; ch += ord.nwarps) {
+      const long long l = ord.next();
+      if (l >= A.L) continue;
+      if (A.seg_inst && A.inst_conv[A.seg_inst[l]]) continue;  // batch: instance already converged
+      const long long b = A.seg_ptr[l];
+      f32_solve<W, P, SC, false>(A, mg, A.seg_prod + b + lane, A.v32 + b + lane, A.vt32 + b + lane,
+                                 (int)(A.seg_ptr[l + 1] - b), A.lam32[l], A.vt0_32[l],
+                                 A.rprev ? A.rprev + l : nullptr, A.z_seg ? A.z_seg + l : nullptr, lane, gmask, sums,
+                                 zacc);
     }
   }
   const double tot = block_sum_d((double)zacc, sh);
@@ -641,6 +718,83 @@ cudaError_t launch_f32_p8(const F32Args& A0, int W8, int grid, int smem, cudaStr
   return cudaGetLastError();
 }
 
+// Margins in shared memory (precision-64 tiling 2, precision-32 tiling 7):
+// one block of kMsThreads per SM, shared-memory sums only.
+cudaError_t launch_fast_ms(const FastArgs& A, int W8, int grid, int smem, cudaStream_t s) {
+  switch (W8) {
+    case 1: k_seg_fast<1, 8, 1, 1><<<grid, kMsThreads, smem, s>>>(A); break;
+    case 2: k_seg_fast<2, 8, 1, 1><<<grid, kMsThreads, smem, s>>>(A); break;
+    case 4: k_seg_fast<4, 8, 1, 1><<<grid, kMsThreads, smem, s>>>(A); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f32_ms(const F32Args& A, int W8, int grid, int smem, cudaStream_t s) {
+  switch (W8) {
+    case 1: k_seg_f32<1, 8, 1, 1><<<grid, kMsThreads, smem, s>>>(A); break;
+    case 2: k_seg_f32<2, 8, 1, 1><<<grid, kMsThreads, smem, s>>>(A); break;
+    case 4: k_seg_f32<4, 8, 1, 1><<<grid, kMsThreads, smem, s>>>(A); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Slot-major tilings (precision-64 tiling 3, precision-32 tiling 8): margins
+// in shared memory when they fit (ms_ok), else read from global memory.
+template <int W>
+cudaError_t launch_fast_sl_w(const FastArgs& A, const FastPlan& pl, cudaStream_t s) {
+  if (pl.ms_ok) k_seg_fast<W, 8, 1, 1, 1><<<pl.ms_grid, kMsThreads, pl.ms_smem64, s>>>(A);
+  else if (pl.scatter == 1) k_seg_fast<W, 8, 1, 0, 1><<<pl.grid, kFastThreads, pl.smem, s>>>(A);
+  else k_seg_fast<W, 8, 2, 0, 1><<<pl.grid, kFastThreads, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t launch_f32_sl_w(const F32Args& A, const FastPlan& pl, cudaStream_t s) {
+  if (pl.ms_ok) k_seg_f32<W, 8, 1, 1, 1><<<pl.ms_grid32, kMsThreads, pl.ms_smem32, s>>>(A);
+  else if (pl.scatter == 1) k_seg_f32<W, 8, 1, 0, 1><<<pl.grid32, kFastThreads, pl.smem, s>>>(A);
+  else k_seg_f32<W, 8, 2, 0, 1><<<pl.grid32, kFastThreads, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fast_sl(const FastArgs& A, const FastPlan& pl, cudaStream_t s) {
+  switch (pl.W8) {
+    case 1: return launch_fast_sl_w<1>(A, pl, s);
+    case 2: return launch_fast_sl_w<2>(A, pl, s);
+    case 4: return launch_fast_sl_w<4>(A, pl, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_f32_sl(const F32Args& A, const FastPlan& pl, cudaStream_t s) {
+  switch (pl.W8) {
+    case 1: return launch_f32_sl_w<1>(A, pl, s);
+    case 2: return launch_f32_sl_w<2>(A, pl, s);
+    case 4: return launch_f32_sl_w<4>(A, pl, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// Shared-memory limits of the slot-major kernels (W8 lanes), as the plan needs them.
+template <int W>
+bool sl_attributes(const FastPlan& pl) {
+  bool ok = true;
+  if (pl.ms_ok) {
+    ok &= cudaFuncSetAttribute(k_seg_fast<W, 8, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               pl.ms_smem64) == cudaSuccess;
+    ok &= cudaFuncSetAttribute(k_seg_f32<W, 8, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               pl.ms_smem32) == cudaSuccess;
+  }
+  if (pl.scatter == 1) {
+    ok &= cudaFuncSetAttribute(k_seg_fast<W, 8, 1, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem) ==
+          cudaSuccess;
+    ok &= cudaFuncSetAttribute(k_seg_f32<W, 8, 1, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem) ==
+          cudaSuccess;
+  }
+  return ok;
+}
+
 template <int SC>
 cudaError_t launch_tma_w(const F32Args& A, int W, int grid, int smem, cudaStream_t s) {
   switch (W) {  // 8 products per lane
@@ -653,11 +807,23 @@ cudaError_t launch_tma_w(const F32Args& A, int W, int grid, int smem, cudaStream
 }
 
 template <class K>
-int blocks_per_sm(K kernel, int smem) {
+int blocks_per_sm(K kernel, int smem, int threads = kFastThreads) {
   int nb = 0;
-  if (smem > 0) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kFastThreads, smem);
+  if (smem > 0 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) return 0;
   return nb;
+}
+
+// Blocks per SM of the margins-in-shared kernels (binary64 or binary32).
+int ms_blocks(int W8, int smem, bool f32) {
+  if (W8 == 1) return f32 ? blocks_per_sm(k_seg_f32<1, 8, 1, 1>, smem, kMsThreads)
+                          : blocks_per_sm(k_seg_fast<1, 8, 1, 1>, smem, kMsThreads);
+  if (W8 == 2) return f32 ? blocks_per_sm(k_seg_f32<2, 8, 1, 1>, smem, kMsThreads)
+                          : blocks_per_sm(k_seg_fast<2, 8, 1, 1>, smem, kMsThreads);
+  if (W8 == 4) return f32 ? blocks_per_sm(k_seg_f32<4, 8, 1, 1>, smem, kMsThreads)
+                          : blocks_per_sm(k_seg_fast<4, 8, 1, 1>, smem, kMsThreads);
+  return 0;
 }
 
 int occupancy(int W, int sc, int smem, bool f32) {
@@ -701,6 +867,25 @@ bool fast_plan(int n, int kmax, int sms, FastPlan* plan) {
     cudaFuncSetAttribute(k_seg_f32<1, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_seg_f32<2, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   }
+  // margins in shared memory after the sums: 16 n (binary64) or 12 n (binary32) bytes
+  plan->ms_ok = 0;
+  if (sc == 1 && W8 <= 4 && 16ll * n <= kTmaMaxSmem) {
+    const int b64 = ms_blocks(W8, 16 * n, false), b32 = ms_blocks(W8, 12 * n, true);
+    if (b64 >= 1 && b32 >= 1) {
+      plan->ms_ok = 1;
+      plan->ms_smem64 = 16 * n;
+      plan->ms_smem32 = 12 * n;
+      plan->ms_grid = b64 * sms;
+      plan->ms_grid32 = b32 * sms;
+    }
+  }
+  {  // slot-major kernels: the same grids as their CSR counterparts (equal register and shared-memory needs)
+    FastPlan q = *plan;
+    q.W8 = W8;
+    q.scatter = sc;
+    q.smem = sc == 1 ? smem : 0;
+    plan->sl_attr = W8 == 1 ? sl_attributes<1>(q) : (W8 == 2 ? sl_attributes<2>(q) : sl_attributes<4>(q));
+  }
   plan->W16 = kmax <= 16 ? 1 : 2;
   plan->W = W;
   plan->W8 = W8;
@@ -724,6 +909,8 @@ cudaError_t launch_seg_fast(const FastArgs& A, const FastPlan& plan, bool scatte
     return cudaGetLastError();
   }
   if (!scatter) return launch_fast_w<0>(A, plan.W8, plan.grid_eval, 0, s);
+  if (plan.fast_sl && A.sl.nchunks > 0) return launch_fast_sl(A, plan, s);
+  if (plan.fast_ms && plan.ms_ok) return launch_fast_ms(A, plan.W8, plan.ms_grid, plan.ms_smem64, s);
   return plan.scatter == 1 ? launch_fast_w<1>(A, plan.W8, plan.grid, plan.smem, s)
                            : launch_fast_w<2>(A, plan.W8, plan.grid, 0, s);
 }
@@ -734,6 +921,8 @@ cudaError_t launch_seg_f32(const F32Args& A, const FastPlan& plan, cudaStream_t 
   if (plan.tma)
     return plan.scatter == 1 ? launch_tma_w<1>(A, plan.tma_W, plan.tma_grid, plan.tma_smem, s)
                              : launch_tma_w<2>(A, plan.tma_W, plan.tma_grid, plan.tma_smem, s);
+  if (plan.f32_sl && A.sl.nchunks > 0) return launch_f32_sl(A, plan, s);
+  if (plan.f32_ms && plan.ms_ok) return launch_f32_ms(A, plan.W8, plan.ms_grid32, plan.ms_smem32, s);
   if (plan.f32_p16)
     return plan.scatter == 1 ? launch_f32_p16<1>(A, plan.W16, plan.grid32, plan.smem, s)
                              : launch_f32_p16<2>(A, plan.W16, plan.grid32, 0, s);

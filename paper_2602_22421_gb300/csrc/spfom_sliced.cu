@@ -1,0 +1,113 @@
+// Slot-major copy of the consideration sets for the sliced segment tilings
+// (precision-64 tiling 3, precision-32 tiling 8).
+//
+// In the CSR layout a group of W lanes reads its segment's slice with W-wide
+// strided loads, so one load instruction of a warp touches the slices of 32 / W
+// segments scattered over a few hundred bytes. Here the segments are sorted by
+// set size (so the sets of one chunk are about as long as each other and little
+// padding is needed) and each chunk of 32 / W positions stores its slots as
+// rows of 32 entries: a warp's slot row is one contiguous 128-byte (binary32,
+// ids) or 256-byte (binary64) line. Lane g W + r of the chunk's warp holds
+// products r, r + W, ... of the chunk's g-th segment, as in the CSR kernels, so
+// the two layouts give the same per-lane sums and the same results.
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "spfom_internal.h"
+
+namespace spfom {
+
+namespace {
+
+// One warp per chunk: entry 32 p + wl of chunk c is slot p of lane wl.
+__global__ void k_slice_items(const Problem P, const float* __restrict__ v32, const float* __restrict__ vt32,
+                              SlView S, const long long* __restrict__ perm, int W) {
+  const int wl = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  const int C = 32 / W;
+  for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < S.nchunks; c += nw) {
+    const long long o = S.off[c];
+    const int rows = (int)((S.off[c + 1] - o) >> 5);
+    const long long l = perm[c * C + wl / W];  // -1 past L
+    long long b = 0;
+    int K = 0;
+    if (l >= 0) {
+      b = P.seg_ptr[l];
+      K = (int)(P.seg_ptr[l + 1] - b);
+    }
+    const int r = wl & (W - 1);
+    for (int p = 0; p < rows; ++p) {
+      const int k = r + p * W;
+      const long long e = o + 32ll * p + wl;
+      const bool in = k < K;
+      S.prod[e] = in ? P.seg_prod[b + k] : -1;
+      if (S.v) {
+        S.v[e] = in ? P.v[b + k] : 0.0;
+        S.vt[e] = in ? P.vt[b + k] : 0.0;
+      }
+      if (S.v32) {
+        S.v32[e] = in ? v32[b + k] : 0.f;
+        S.vt32[e] = in ? vt32[b + k] : 0.f;
+      }
+    }
+  }
+}
+
+// Per position: lambda and vt_0 of its segment (0 and 1 past L, so that a
+// padding position has q = 0).
+__global__ void k_slice_segments(const Problem P, const float* __restrict__ lam32, const float* __restrict__ vt0_32,
+                                 SlView S, const long long* __restrict__ perm, long long npos) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < npos;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long l = perm[i];
+    if (S.lam) {
+      S.lam[i] = l >= 0 ? P.lam[l] : 0.0;
+      S.vt0[i] = l >= 0 ? P.vt0[l] : 1.0;
+    }
+    if (S.lam32) {
+      S.lam32[i] = l >= 0 ? lam32[l] : 0.f;
+      S.vt0_32[i] = l >= 0 ? vt0_32[l] : 1.f;
+    }
+  }
+}
+
+}  // namespace
+
+long long sliced_layout(const long long* seg_ptr, long long L, int W8, std::vector<long long>* perm,
+                        std::vector<long long>* off) {
+  const int C = 32 / W8;
+  const long long nch = (L + C - 1) / C, npos = nch * C;
+  // counting sort by set size, descending; equal sizes keep segment order
+  std::vector<long long> start(34, 0);
+  for (long long l = 0; l < L; ++l) ++start[(size_t)(32 - (seg_ptr[l + 1] - seg_ptr[l])) + 1];
+  for (int k = 1; k < 34; ++k) start[k] += start[k - 1];
+  perm->assign((size_t)npos, -1);
+  for (long long l = 0; l < L; ++l) (*perm)[(size_t)start[(size_t)(32 - (seg_ptr[l + 1] - seg_ptr[l]))]++] = l;
+  off->assign((size_t)nch + 1, 0);
+  for (long long c = 0; c < nch; ++c) {
+    const long long l = (*perm)[(size_t)(c * C)];  // the chunk's largest set
+    const long long K = l >= 0 ? seg_ptr[l + 1] - seg_ptr[l] : 0;
+    (*off)[(size_t)c + 1] = (*off)[(size_t)c] + 32 * ((K + W8 - 1) / W8);
+  }
+  return nch;
+}
+
+cudaError_t launch_slice_items(const Problem& P, const Work& Wk, int W8, cudaStream_t s) {
+  if (Wk.sl.nchunks <= 0) return cudaSuccess;
+  const long long blocks = (Wk.sl.nchunks + 7) / 8;  // 8 warps per block
+  k_slice_items<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(P, Wk.v32, Wk.vt32, Wk.sl,
+                                                                                        Wk.sl_perm, W8);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slice_segments(const Problem& P, const Work& Wk, int W8, cudaStream_t s) {
+  if (Wk.sl.nchunks <= 0) return cudaSuccess;
+  const long long npos = Wk.sl.nchunks * (32 / W8);
+  const long long blocks = (npos + 255) / 256;
+  k_slice_segments<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(P, Wk.lam32, Wk.vt0_32,
+                                                                                           Wk.sl, Wk.sl_perm, npos);
+  return cudaGetLastError();
+}
+
+}  // namespace spfom
