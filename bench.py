@@ -47,6 +47,10 @@ def parse():
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
     ap.add_argument("--iters-per-step", type=int, default=64)
     ap.add_argument("--segments", type=int, default=1_000_000)
+    ap.add_argument("--tiling64", type=int, default=0,
+                    help="segment-kernel tiling of the precision-64 legs (0: spfom_autotune picks)")
+    ap.add_argument("--tiling32", type=int, default=0,
+                    help="segment-kernel tiling of the precision-32 legs (0: spfom_autotune picks)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -145,13 +149,13 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_traffic(kernel, src, nnz):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was taken on the current kernel source; scaled by nonzeros."""
+def kernel_traffic(kernel, tiling, src, nnz):
+    """DRAM bytes per launch of `kernel` in `tiling` from the committed ncu
+    summary, if it was taken on the current kernel source; scaled by nonzeros."""
     if not os.path.exists(TRAFFIC):
         return None, None
     with open(TRAFFIC) as f:
-        d = json.load(f).get(kernel)
+        d = json.load(f).get(f"{kernel}/tiling{tiling}")
     if not d:
         return None, None
     sha = hashlib.sha256(open(os.path.join(CSRC, src), "rb").read()).hexdigest()
@@ -271,8 +275,10 @@ def run_gpu(args):
     def measure(precision, with_clocks, path=0, solve=True):
         """Timed iterations (kkt_tol = 0: nothing is skipped), then a profiled
         pass for the segment kernel's roofline, then a solve to KKT <= 1e-4."""
-        s = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, precision=precision, path=path)
-        tiling = s.autotune(ips) if path != 1 else 0  # segment-kernel tiling for this instance
+        forced = (args.tiling64 if precision == 64 else args.tiling32) if path == 0 else 0
+        s = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, precision=precision, path=path,
+                   tiling=forced)
+        tiling = forced or (s.autotune(ips) if path != 1 else 0)  # segment-kernel tiling for this instance
         s.step(args.warmup * ips)
         barrier()
         clk = Clocks(local) if (rank == 0 and with_clocks) else None
@@ -307,7 +313,7 @@ def run_gpu(args):
                     kname, ksrc = "k_seg_fast", "spfom_segments_fast.cu"
             peak, src = measured_peaks()
             achieved = alg / per_launch / 1e9
-            traffic, cap = kernel_traffic(kname, ksrc, inst.nnz)
+            traffic, cap = kernel_traffic(kname, tiling, ksrc, inst.nnz)
             solves = (2 + min(args.steps, 10)) * ips * inst.L
             out["roofline"] = {"bound": "hbm", "kernel": kname + " (iterate)", "achieved": achieved, "peak": peak,
                                "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
@@ -429,9 +435,10 @@ def huge_leg(args, stream, local):
     ips = args.iters_per_step
     for precision in (64, 32):
         t0 = time.perf_counter()
-        s = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, precision=precision)
+        forced = args.tiling64 if precision == 64 else args.tiling32
+        s = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, precision=precision, tiling=forced)
         load_s = time.perf_counter() - t0
-        tiling = s.autotune(16)
+        tiling = forced or s.autotune(16)
         s.step(2 * ips)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

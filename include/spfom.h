@@ -102,7 +102,7 @@ typedef struct {
                                 nonzero read and written each iteration); needs precision 64,
                                 batch_frac 1 and a single instance, and runs the general kernel */
   int32_t tiling;            /* 0 (default): tiling 1 of the active segment pass until
-                                spfom_autotune picks one; 1..7: that tiling (see spfom_autotune),
+                                spfom_autotune picks one; 1..8: that tiling (see spfom_autotune),
                                 ENOTSUP at load when the instance does not allow it */
   void* stream;              /* cudaStream_t to run on; NULL (default): the ctx creates one */
 } spfom_params;
@@ -269,12 +269,15 @@ spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out);
  * 6 (batches of instances with <= 8192 products each) = chunks of one
  * instance's segments with shared-memory sums of its products,
  * 7 = as 3 with the margins copied into shared memory (one 1024-thread block
- * per SM; needs 16 n bytes of shared memory, n <= 14464) --
- * batches do not try 2 and 4 (the staged kernels load the tiles of
- * converged members too);
+ * per SM; needs 16 n bytes of shared memory, n <= 14464),
+ * 8 = a slot-major copy of the consideration sets built at load (segments
+ * sorted by set size, 32-entry slot rows per warp; margins in shared memory
+ * when they fit) -- batches do not try 2, 4 (the staged kernels load the
+ * tiles of converged members too) and 8 (single instances only);
  * precision 64 with path 0: 1 = margins read from global memory (two
  * 512-thread blocks per SM), 2 = margins copied into shared memory (one
- * 1024-thread block per SM, n <= 14464);
+ * 1024-thread block per SM, n <= 14464), 3 = the slot-major copy (single
+ * instances);
  * precision 64 with path 2: 1 = 8 products per lane at two 512-thread blocks per
  * SM, 2 = 8 per lane at three blocks per SM, 3 = 4 per lane at three blocks
  * per SM. *choice_out (or NULL) gets the choice (1 when there is none). */

@@ -108,7 +108,7 @@ __device__ __forceinline__ void seg_solve(const FastArgs& A, const double* __res
     jv[p] = 0;
     af[p] = bf[p] = 0.f;
     if (SL ? p < lim : lane + p * W < lim) {
-      const int j = sp[p * T];
+      const int j = SL ? __ldcg(sp + p * T) : sp[p * T];  // slot-major: ids are not read again, keep L1 for v, vt
       if (!SL || j >= 0) {
         jv[p] = j;
         const double m = mg[j];
@@ -125,7 +125,7 @@ __device__ __forceinline__ void seg_solve(const FastArgs& A, const double* __res
   // iteration (any start reaches a fixed point, and every fixed point is
   // optimal; the margins move little between iterations, so this one is
   // usually confirmed by the second pass).
-  float R = rp ? *rp : 0.f;
+  float R = rp ? (SL ? __ldcg(rp) : *rp) : 0.f;
   unsigned sel = 0xffffffffu;  // no previous set
   bool conv = false;
   for (int it = 0; it < P * W + 3; ++it) {
@@ -213,6 +213,48 @@ __device__ __forceinline__ void seg_solve(const FastArgs& A, const double* __res
   }
 }
 
+// Walk of a warp over its chunks of the slot-major copy (c = first, first + nw,
+// ...): each step returns the chunk's first entry and slot-row count, loads
+// the offsets two chunks ahead and asks L2 for the next chunk's slot rows
+// (ids, and the values v0, v1), so the rows are on chip when the warp gets to
+// them and no offset load stalls the warp.
+struct SlWalk {
+  const long long* off;
+  long long nch, nw, c;
+  long long o0, o1, n0, n1;  // offsets of chunk c and of chunk c + nw
+  __device__ SlWalk(const long long* off_, long long nch_, long long first, long long nw_)
+      : off(off_), nch(nch_), nw(nw_), c(first), o0(0), o1(0), n0(0), n1(0) {
+    if (c < nch) {
+      o0 = off[c];
+      o1 = off[c + 1];
+    }
+    if (c + nw < nch) {
+      n0 = off[c + nw];
+      n1 = off[c + nw + 1];
+    }
+  }
+  template <class T0, class T1, class T2>
+  __device__ void prefetch_next(const T0* a, const T1* b, const T2* d, int wl) const {
+    if (c + nw >= nch) return;
+    const int rn = (int)((n1 - n0) >> 5);
+    for (int p = 0; p < rn; ++p) {
+      const long long e = n0 + wl + 32ll * p;
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(a + e));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(b + e));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(d + e));
+    }
+  }
+  __device__ void advance() {
+    c += nw;
+    o0 = n0;
+    o1 = n1;
+    if (c + nw < nch) {
+      n0 = off[c + nw];
+      n1 = off[c + nw + 1];
+    }
+  }
+};
+
 // One segment l of the CSR layout.
 template <int W, int P>
 __device__ __forceinline__ void fast_segment(const FastArgs& A, const double* __restrict__ mg, long long l, int lane,
@@ -255,13 +297,16 @@ __global__ void __launch_bounds__(MS ? kMsThreads : kFastThreads, MS ? 1 : 2) k_
   unsigned long long* sums = SC == 0 ? nullptr : (SC == 1 ? acc : A.s_fx);
   if (SL) {
     const int wl = threadIdx.x & 31;
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < A.sl.nchunks; c += nw) {
-      const long long o = A.sl.off[c] + wl;
-      const int rows = (int)((A.sl.off[c + 1] - A.sl.off[c]) >> 5);
-      const long long pos = c * (32 / W) + wl / W;
-      seg_solve<W, P, true>(A, mg, A.sl.prod + o, A.sl.v + o, A.sl.vt + o, rows, A.sl.lam[pos], A.sl.vt0[pos],
-                            A.sl.rprev ? A.sl.rprev + pos : nullptr, nullptr, lane, gmask, sums, 0, zacc, fallbacks);
+    SlWalk wk(A.sl.off, A.sl.nchunks, (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+              (long long)gridDim.x * (blockDim.x >> 5));
+    for (; wk.c < wk.nch; wk.advance()) {
+      wk.prefetch_next(A.sl.prod, A.sl.v, A.sl.vt, wl);
+      const long long o = wk.o0 + wl;
+      const int rows = (int)((wk.o1 - wk.o0) >> 5);
+      const long long pos = wk.c * (32 / W) + wl / W;
+      seg_solve<W, P, true>(A, mg, A.sl.prod + o, A.sl.v + o, A.sl.vt + o, rows, __ldcg(A.sl.lam + pos),
+                            __ldcg(A.sl.vt0 + pos), A.sl.rprev ? A.sl.rprev + pos : nullptr, nullptr, lane, gmask,
+                            sums, 0, zacc, fallbacks);
     }
   } else {
     SegOrder ord(Pr.L, W, A.perm_a, A.perm_d);
@@ -415,11 +460,13 @@ __global__ void __launch_bounds__(MS ? kMsThreads : kFastThreads, MS ? 1 : 2) k_
   unsigned long long* sums = SC == 1 ? acc : A.s_fx;
   if (SL) {
     const int wl = threadIdx.x & 31;
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < A.sl.nchunks; c += nw) {
-      const long long o = A.sl.off[c] + wl;
-      const int rows = (int)((A.sl.off[c + 1] - A.sl.off[c]) >> 5);
-      const long long pos = c * (32 / W) + wl / W;
+    SlWalk wk(A.sl.off, A.sl.nchunks, (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
+              (long long)gridDim.x * (blockDim.x >> 5));
+    for (; wk.c < wk.nch; wk.advance()) {
+      if (!MS) wk.prefetch_next(A.sl.prod, A.sl.v32, A.sl.vt32, wl);  // measured: helps only without MS
+      const long long o = wk.o0 + wl;
+      const int rows = (int)((wk.o1 - wk.o0) >> 5);
+      const long long pos = wk.c * (32 / W) + wl / W;
       f32_solve<W, P, SC, true>(A, mg, A.sl.prod + o, A.sl.v32 + o, A.sl.vt32 + o, rows, A.sl.lam32[pos],
                                 A.sl.vt0_32[pos], A.sl.rprev ? A.sl.rprev + pos : nullptr, nullptr, lane, gmask, sums,
                                 zacc);
