@@ -182,6 +182,54 @@ spfom_status validate(spfom_ctx* ctx, const spfom_instance* I, int* kmax_out) {
   return SPFOM_OK;
 }
 
+// The slot-major copy of the loaded single instance (tilings 3 and 8), built
+// on first use: positions and chunk offsets on the host from the segment
+// offsets, then the items and per-position values gathered on the device.
+spfom_status build_sliced(spfom_ctx* ctx) {
+  Work& W = ctx->W;
+  if (W.sl.nchunks > 0 || !W.fast || !W.plan.sl_ok) return SPFOM_OK;
+  const Problem& P = ctx->P;
+  std::vector<long long> seg_ptr((size_t)P.L + 1);
+  SPFOM_CUDA(ctx, cudaMemcpyAsync(seg_ptr.data(), P.seg_ptr, sizeof(long long) * seg_ptr.size(),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::vector<long long> perm, off;
+  const long long nch = spfom::sliced_layout(seg_ptr.data(), P.L, W.plan.W8, &perm, &off);
+  const size_t entries = (size_t)std::max(off[(size_t)nch], 1ll), npos = perm.size();
+  spfom::SlView sl{};
+  long long* d_perm = nullptr;
+#define SPFOM_TRYS(x) do { spfom_status s_ = (x); if (s_ != SPFOM_OK) return s_; } while (0)
+  SPFOM_TRYS(upload(ctx, &sl.off, off.data(), off.size()));
+  SPFOM_TRYS(upload(ctx, &d_perm, perm.data(), npos));
+  SPFOM_TRYS(dalloc(ctx, &sl.prod, entries));
+  if (W.v32) {
+    SPFOM_TRYS(dalloc(ctx, &sl.v32, entries));
+    SPFOM_TRYS(dalloc(ctx, &sl.vt32, entries));
+    SPFOM_TRYS(dalloc(ctx, &sl.lam32, npos));
+    SPFOM_TRYS(dalloc(ctx, &sl.vt0_32, npos));
+  } else {
+    SPFOM_TRYS(dalloc(ctx, &sl.v, entries));
+    SPFOM_TRYS(dalloc(ctx, &sl.vt, entries));
+    SPFOM_TRYS(dalloc(ctx, &sl.lam, npos));
+    SPFOM_TRYS(dalloc(ctx, &sl.vt0, npos));
+  }
+  SPFOM_TRYS(dalloc(ctx, &sl.rprev, npos));
+#undef SPFOM_TRYS
+  SPFOM_CUDA(ctx, cudaMemsetAsync(sl.rprev, 0, sizeof(float) * npos, ctx->stream));
+  sl.nchunks = nch;
+  W.sl = sl;
+  W.sl_perm = d_perm;
+  cudaError_t e = spfom::launch_slice_items(P, W, W.plan.W8, ctx->stream);
+  if (e == cudaSuccess) e = spfom::launch_slice_segments(P, W, W.plan.W8, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the host vectors go out of scope
+  if (e != cudaSuccess) {
+    W.sl = spfom::SlView{};
+    W.sl_perm = nullptr;
+    return cuda_fail(ctx, e, "slot-major copy");
+  }
+  return SPFOM_OK;
+}
+
 spfom_status init_state(spfom_ctx* ctx, const double* y0) {
   Work& W = ctx->W;
   const Problem& P = ctx->P;
@@ -631,31 +679,6 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   }
   W.sl = spfom::SlView{};
   W.sl_perm = nullptr;
-  if (W.fast && W.plan.sl_ok) {
-    // slot-major copy: positions and chunk offsets here, the items gathered on the device below
-    std::vector<long long> perm, off;
-    const long long nch =
-        spfom::sliced_layout(reinterpret_cast<const long long*>(I->seg_ptr), L, W.plan.W8, &perm, &off);
-    const size_t entries = (size_t)std::max(off[(size_t)nch], 1ll), npos = perm.size();
-    SPFOM_TRY(upload(ctx, &W.sl.off, off.data(), off.size()));
-    SPFOM_TRY(upload(ctx, &W.sl_perm, perm.data(), npos));
-    SPFOM_TRY(dalloc(ctx, &W.sl.prod, entries));
-    if (ctx->p.precision == 32) {
-      SPFOM_TRY(dalloc(ctx, &W.sl.v32, entries));
-      SPFOM_TRY(dalloc(ctx, &W.sl.vt32, entries));
-      SPFOM_TRY(dalloc(ctx, &W.sl.lam32, npos));
-      SPFOM_TRY(dalloc(ctx, &W.sl.vt0_32, npos));
-    } else {
-      SPFOM_TRY(dalloc(ctx, &W.sl.v, entries));
-      SPFOM_TRY(dalloc(ctx, &W.sl.vt, entries));
-      SPFOM_TRY(dalloc(ctx, &W.sl.lam, npos));
-      SPFOM_TRY(dalloc(ctx, &W.sl.vt0, npos));
-    }
-    SPFOM_TRY(dalloc(ctx, &W.sl.rprev, npos));
-    SPFOM_CUDA(ctx, cudaMemsetAsync(W.sl.rprev, 0, sizeof(float) * npos, ctx->stream));
-    W.sl.nchunks = nch;
-    SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));  // the host vectors go out of scope
-  }
 #undef SPFOM_TRY
   ctx->P = P;
   if (W.v2) {
@@ -666,10 +689,9 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
     e = spfom::launch_prep_f32(P, W, ctx->stream);
     if (e != cudaSuccess) { free_instance(ctx); return cuda_fail(ctx, e, "binary32 copies"); }
   }
-  if (W.sl.nchunks > 0) {
-    e = spfom::launch_slice_items(P, W, W.plan.W8, ctx->stream);
-    if (e == cudaSuccess) e = spfom::launch_slice_segments(P, W, W.plan.W8, ctx->stream);
-    if (e != cudaSuccess) { free_instance(ctx); return cuda_fail(ctx, e, "slot-major copy"); }
+  if (W.fast && (W.plan.fast_sl || W.plan.f32_sl)) {  // a requested slot-major tiling
+    const spfom_status st = build_sliced(ctx);
+    if (st != SPFOM_OK) { free_instance(ctx); return st; }
   }
   // step size: tau, or tau0 * mean(r) / mean(c) (sums in index order)
   double sr = 0.0, sc = 0.0;
@@ -1218,11 +1240,15 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
       plan.fast_sl = c == 3 ? 1 : 0;
     }
   };
-  if (!f32 && !dd && !(f64 && (plan.ms_ok || ctx->W.sl.nchunks > 0))) {
+  if (!f32 && !dd && !(f64 && (plan.ms_ok || plan.sl_ok))) {
     if (choice_out) *choice_out = 1;
     return SPFOM_OK;
   }
   SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
+  if ((f32 || f64) && plan.sl_ok) {  // the slot-major candidates need their copy
+    const spfom_status sb = build_sliced(ctx);
+    if (sb != SPFOM_OK) return sb;
+  }
   std::vector<double> y0((size_t)ctx->P.m);
   if (ctx->P.m)
     SPFOM_CUDA(ctx, cudaMemcpyAsync(y0.data(), ctx->W.y, sizeof(double) * ctx->P.m, cudaMemcpyDeviceToHost,

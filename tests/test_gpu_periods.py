@@ -40,7 +40,9 @@ def test_batched_periods_match_sequential_plain_solves(precision):
     insts = small_family()
     rho = period_rates(11, len(insts), 3)
     summary, path, per = PR.run_batched(insts, rho, periods=3, precision=precision, restart_tau_balance=0.5)
-    assert 1 <= summary["autotune_choice"] <= 8 and summary["autotune_choice"] not in (2, 4, 8)
+    # batches: binary32 tilings without staging or the slot-major copy; binary64: 1 or 2 (shared margins)
+    choices = (1, 3, 5, 6, 7) if precision == 32 else (1, 2)
+    assert summary["autotune_choice"] in choices
     assert all(r["converged"] == 1 for r in summary["records"])
     for c_k, lam_k in path:
         assert all((c >= 0).all() for c in c_k)
