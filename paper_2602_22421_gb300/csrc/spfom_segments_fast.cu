@@ -458,12 +458,26 @@ __global__ void __launch_bounds__(MS ? kMsThreads : kFastThreads, MS ? 1 : 2) k_
   const unsigned gmask = (W == 32) ? 0xffffffffu : (((1u << W) - 1u) << gbase);
   float zacc = 0.f;
   unsigned long long* sums = SC == 1 ? acc : A.s_fx;
-  if (SL) {
+  if (SL && MS) {
+    // margins in shared memory: the plain chunk loop (measured faster here than the
+    // pipelined walk, whose extra registers cost more than its prefetch gains)
+    const int wl = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < A.sl.nchunks; c += nw) {
+      const long long o = A.sl.off[c] + wl;
+      const int rows = (int)((A.sl.off[c + 1] - A.sl.off[c]) >> 5);
+      const long long pos = c * (32 / W) + wl / W;
+      f32_solve<W, P, SC, true>(A, mg, A.sl.prod + o, A.sl.v32 + o, A.sl.vt32 + o, rows, A.sl.lam32[pos],
+                                A.sl.vt0_32[pos], A.sl.rprev ? A.sl.rprev + pos : nullptr, nullptr, lane, gmask, sums,
+                                zacc);
+    }
+  } else if (SL) {
+    // margins from global memory: the pipelined walk with the next chunk's rows prefetched
     const int wl = threadIdx.x & 31;
     SlWalk wk(A.sl.off, A.sl.nchunks, (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5),
               (long long)gridDim.x * (blockDim.x >> 5));
     for (; wk.c < wk.nch; wk.advance()) {
-      if (!MS) wk.prefetch_next(A.sl.prod, A.sl.v32, A.sl.vt32, wl);  // measured: helps only without MS
+      wk.prefetch_next(A.sl.prod, A.sl.v32, A.sl.vt32, wl);
       const long long o = wk.o0 + wl;
       const int rows = (int)((wk.o1 - wk.o0) >> 5);
       const long long pos = wk.c * (32 / W) + wl / W;
