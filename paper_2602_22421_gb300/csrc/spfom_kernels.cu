@@ -398,6 +398,55 @@ int vec_grid(const Problem& P) {
 
 }  // namespace
 
+namespace {
+
+// One thread per segment, its nonzeros in order: id in range, not repeated
+// earlier in the segment, v finite and > 0, w in [0, v]; with f32, v and v - w
+// normal binary32 numbers (v - w may be 0). Sets of <= 32 products (checked on
+// the host before the launch).
+__global__ void k_validate_items(const Problem P, const double* __restrict__ w, int f32,
+                                 unsigned long long* __restrict__ keys) {
+  for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < P.L;
+       l += (long long)gridDim.x * blockDim.x) {
+    const long long b = P.seg_ptr[l], e = P.seg_ptr[l + 1];
+    for (long long p = b; p < e && p < b + 32; ++p) {
+      const int j = P.seg_prod[p];
+      int code = 0;
+      if (j < 0 || j >= P.n) {
+        code = kBadId;
+      } else {
+        for (long long q = b; q < p; ++q)
+          if (P.seg_prod[q] == j) code = kRepeated;
+      }
+      const double v = P.v[p];
+      if (!code && !(v > 0.0 && isfinite(v))) code = kBadV;
+      const double wp = w ? w[p] : 0.0;
+      if (!code && w && !(wp >= 0.0 && wp <= v)) code = kBadW;
+      if (code) {
+        atomicMin(keys, ((unsigned long long)p << 3) | (unsigned)code);
+        break;  // later nonzeros of this segment sort after this one
+      }
+      if (f32) {
+        const double vt = w ? __dsub_rn(v, wp) : v;
+        const bool ok_v = v >= 1.1754943508222875e-38 && v <= 3.4028234663852886e+38;
+        const bool ok_t = vt == 0.0 || (vt >= 1.1754943508222875e-38 && vt <= 3.4028234663852886e+38);
+        if (!ok_v || !ok_t) atomicMin(keys + 1, ((unsigned long long)p << 3) | (unsigned)kBadF32);
+      }
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_validate_items(const Problem& P, const double* w, bool f32, unsigned long long* keys,
+                                  cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(keys, 0xff, 2 * sizeof(unsigned long long), s);
+  if (e != cudaSuccess || P.L <= 0) return e;
+  const long long blocks = (P.L + 255) / 256;
+  k_validate_items<<<(unsigned)(blocks < 65535ll * 16 ? blocks : 65535ll * 16), 256, 0, s>>>(P, w, f32 ? 1 : 0, keys);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_prep(const Problem& P, const double* w, const double* v0, double* vt, double* vt0,
                         cudaStream_t s) {
   if (P.nnz > 0) k_prep_items<<<(unsigned)((P.nnz + 255) / 256), 256, 0, s>>>(P.nnz, P.v, w, vt);
