@@ -537,8 +537,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   const long long groups = (L * Wl + 255) / 256;
   long long sb = groups < (long long)ctx->sms * 8 ? groups : (long long)ctx->sms * 8;
   W.seg_blocks = (int)(sb > 0 ? sb : 1);
-  const int nv = n > m ? n : m;
-  W.vec_blocks = (nv + 255) / 256 > 0 ? (nv + 255) / 256 : 1;
+  W.vec_blocks = (m + 7) / 8 + (n + 255) / 256 > 0 ? (m + 7) / 8 + (n + 255) / 256 : 1;  // k_dual_step's grid
   SPFOM_TRY(dalloc(ctx, &W.y, (size_t)m));
   SPFOM_TRY(dalloc(ctx, &W.sum_y, (size_t)m));
   SPFOM_TRY(dalloc(ctx, &W.sum_g, (size_t)m));

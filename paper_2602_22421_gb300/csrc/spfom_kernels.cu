@@ -227,43 +227,55 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
   if (st->converged) return;
   __shared__ double sh[32];
   __shared__ bool last;
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const double tau = st->tau, shrink = __dsub_rn(1.0, __dmul_rn(st->tau, st->mu));
   double cy = 0.0, pr = 0.0;
   const bool fx = Wk.fast && full;
-  if (gid < P.m) {
-    double g = 0.0;
-    const int q0 = P.at_ptr[gid], q1 = P.at_ptr[gid + 1];
-    // Eight products at a time: the index loads, then the sales loads, are
-    // issued together; the sum still runs in ascending product order.
-    for (int qb = q0; qb < q1; qb += 8) {
-      int jj[8];
-      double sv[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) jj[k] = qb + k < q1 ? P.at_idx[qb + k] : -1;
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        sv[k] = jj[k] < 0 ? 0.0
-                          : (fx ? __dmul_rn(__ull2double_rn(Wk.s_fx[jj[k]]), Wk.inv_fx_scale) : Wk.s[jj[k]]);
-#pragma unroll
-      for (int k = 0; k < 8; ++k)
-        if (jj[k] >= 0) g = __dadd_rn(g, __dmul_rn(P.at_val ? P.at_val[qb + k] : 1.0, sv[k]));
+  // The first blocks take one resource per warp: the lanes fetch the
+  // resource's products and their sales together (one round of dependent
+  // loads per 32 products), and lane 0 adds the terms in ascending product
+  // order, so g_i is the sequential sum. The remaining blocks convert the
+  // product sales, one product per thread.
+  constexpr int kWarps = kVecThreads / 32;
+  const int rblocks = (P.m + kWarps - 1) / kWarps;
+  if ((int)blockIdx.x < rblocks) {
+    const int i = blockIdx.x * kWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i < P.m) {
+      const double yo = Wk.y[i], c = P.c[i], sy = Wk.sum_y[i], sg = Wk.sum_g[i];
+      const int q0 = P.at_ptr[i], q1 = P.at_ptr[i + 1];
+      double g = 0.0;
+      for (int qb = q0; qb < q1; qb += 32) {
+        const int q = qb + lane;
+        double term = 0.0;
+        if (q < q1) {
+          const int j = P.at_idx[q];
+          const double sv = fx ? __dmul_rn(__ull2double_rn(Wk.s_fx[j]), Wk.inv_fx_scale) : Wk.s[j];
+          term = __dmul_rn(P.at_val ? P.at_val[q] : 1.0, sv);
+        }
+        const int cnt = q1 - qb < 32 ? q1 - qb : 32;
+        for (int k = 0; k < cnt; ++k) {
+          const double t = __shfl_sync(0xffffffffu, term, k);
+          if (lane == 0) g = __dadd_rn(g, t);
+        }
+      }
+      if (lane == 0) {
+        const double yn = __dsub_rn(__dmul_rn(shrink, yo), __dmul_rn(tau, __dsub_rn(c, g)));
+        Wk.y[i] = yn > 0.0 ? yn : 0.0;
+        Wk.g[i] = g;
+        Wk.sum_y[i] = __dadd_rn(sy, yo);
+        Wk.sum_g[i] = __dadd_rn(sg, g);
+        if (yo != 0.0) cy = __dmul_rn(c, yo);
+      }
     }
-    const double yo = Wk.y[gid], c = P.c[gid];
-    const double yn = __dsub_rn(__dmul_rn(shrink, yo), __dmul_rn(tau, __dsub_rn(c, g)));
-    Wk.y[gid] = yn > 0.0 ? yn : 0.0;
-    Wk.g[gid] = g;
-    Wk.sum_y[gid] = __dadd_rn(Wk.sum_y[gid], yo);
-    Wk.sum_g[gid] = __dadd_rn(Wk.sum_g[gid], g);
-    if (yo != 0.0) cy = __dmul_rn(c, yo);
-  }
-  if (gid < P.n) {
-    double sj = Wk.s[gid];
-    if (fx) {
-      sj = __dmul_rn(__ull2double_rn(Wk.s_fx[gid]), Wk.inv_fx_scale);
-      Wk.s[gid] = sj;
+  } else {
+    const int j = (blockIdx.x - rblocks) * blockDim.x + threadIdx.x;
+    if (j < P.n) {
+      double sj = Wk.s[j];
+      if (fx) {
+        sj = __dmul_rn(__ull2double_rn(Wk.s_fx[j]), Wk.inv_fx_scale);
+        Wk.s[j] = sj;
+      }
+      pr = __dmul_rn(P.r[j], sj);
     }
-    pr = __dmul_rn(P.r[gid], sj);
   }
   const double bcy = block_sum(cy, sh);
   const double bpr = block_sum(pr, sh);
@@ -391,9 +403,10 @@ cudaError_t launch_segments_w(const Problem& P, const Work& Wk, const double* ma
   return cudaGetLastError();
 }
 
+// k_dual_step: one warp per resource, then one thread per product.
 int vec_grid(const Problem& P) {
-  const int n = P.n > P.m ? P.n : P.m;
-  return (n + kVecThreads - 1) / kVecThreads > 0 ? (n + kVecThreads - 1) / kVecThreads : 1;
+  const int g = (P.m + kVecThreads / 32 - 1) / (kVecThreads / 32) + (P.n + kVecThreads - 1) / kVecThreads;
+  return g > 0 ? g : 1;
 }
 
 }  // namespace
