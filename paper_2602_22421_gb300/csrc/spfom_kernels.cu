@@ -48,6 +48,33 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long key)
   return z ^ (z >> 31);
 }
 
+// Sums of three doubles per thread over the block, each in block_sum's order;
+// the three trees run side by side (one pass of barriers). sh holds 3 x 32.
+__device__ void block_sum3(double& a, double& b, double& c, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) {
+    sh[w] = a;
+    sh[32 + w] = b;
+    sh[64 + w] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    a = b = c = 0.0;
+    for (int k = 0; k < nw; ++k) {
+      a += sh[k];
+      b += sh[32 + k];
+      c += sh[64 + k];
+    }
+  }
+}
+
 // Sum of one double per thread over the block, in a fixed order.
 __device__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -225,15 +252,16 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
                                                               int zparts) {
   DevState* st = Wk.st;
   if (st->converged) return;
-  __shared__ double sh[32];
+  __shared__ double sh[96];
   __shared__ bool last;
   const double tau = st->tau, shrink = __dsub_rn(1.0, __dmul_rn(st->tau, st->mu));
   double cy = 0.0, pr = 0.0;
   const bool fx = Wk.fast && full;
   // The first blocks take one resource per warp: the lanes fetch the
   // resource's products and their sales together (one round of dependent
-  // loads per 32 products), and lane 0 adds the terms in ascending product
-  // order, so g_i is the sequential sum. The remaining blocks convert the
+  // loads per 32 products). With unit incidence and fixed-point sales the
+  // warp adds the integer sales exactly; otherwise lane 0 adds the binary64
+  // terms in ascending product order. The remaining blocks convert the
   // product sales, one product per thread.
   constexpr int kWarps = kVecThreads / 32;
   const int rblocks = (P.m + kWarps - 1) / kWarps;
@@ -243,7 +271,15 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
       const double yo = Wk.y[i], c = P.c[i], sy = Wk.sum_y[i], sg = Wk.sum_g[i];
       const int q0 = P.at_ptr[i], q1 = P.at_ptr[i + 1];
       double g = 0.0;
-      for (int qb = q0; qb < q1; qb += 32) {
+      if (fx && !P.at_val) {
+        // unit incidence: g_i = 2^-F sum_j s_fx[j], summed exactly in fixed point
+        // (the total stays below 2^62), then rounded once
+        unsigned long long acc = 0ull;
+        for (int q = q0 + lane; q < q1; q += 32) acc += Wk.s_fx[P.at_idx[q]];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        g = __dmul_rn(__ull2double_rn(acc), Wk.inv_fx_scale);
+      }
+      for (int qb = q0; qb < q1 && !(fx && !P.at_val); qb += 32) {
         const int q = qb + lane;
         double term = 0.0;
         if (q < q1) {
@@ -277,11 +313,11 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
       pr = __dmul_rn(P.r[j], sj);
     }
   }
-  const double bcy = block_sum(cy, sh);
-  const double bpr = block_sum(pr, sh);
+  double unused = 0.0;
+  block_sum3(cy, pr, unused, sh);
   if (threadIdx.x == 0) {
-    Wk.cypart[blockIdx.x] = bcy;
-    Wk.Ppart[blockIdx.x] = bpr;
+    Wk.cypart[blockIdx.x] = cy;
+    Wk.Ppart[blockIdx.x] = pr;
     __threadfence();
     const unsigned prev = atomicAdd(&st->ticket, 1u);
     last = (prev == gridDim.x - 1);
@@ -296,9 +332,7 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
     cys += __ldcg(Wk.cypart + b);
     Ps += __ldcg(Wk.Ppart + b);
   }
-  zs = block_sum(zs, sh);
-  cys = block_sum(cys, sh);
-  Ps = block_sum(Ps, sh);
+  block_sum3(zs, cys, Ps, sh);
   if (threadIdx.x != 0) return;
   st->z_sum = full ? zs : CUDART_NAN;
   st->dual_iter = full ? cys + zs : CUDART_NAN;
