@@ -67,38 +67,80 @@ __global__ void k_b_margins(Problem P, BatchMaps B, const double* __restrict__ y
 // product sales in binary64 for the reductions.
 __global__ void k_b_dual(Problem P, Work Wk) {
   const BatchMaps& B = Wk.bm;
-  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
-  if (gid < P.m) {
-    const InstState& I = B.inst[B.res_inst[gid]];
-    if (!I.converged) {
-      double g = 0.0;
-      for (int q = P.at_ptr[gid]; q < P.at_ptr[gid + 1]; ++q) {
-        const double a = P.at_val ? P.at_val[q] : 1.0;
-        g = __dadd_rn(g, __dmul_rn(a, __dmul_rn(__ull2double_rn(Wk.s_fx[P.at_idx[q]]), Wk.inv_fx_scale)));
+  // First blocks: one warp per resource (the lanes fetch its products' sales
+  // together; unit incidence: the exact fixed-point sum, rounded once; else
+  // lane 0 adds the binary64 terms in ascending product order). Then one
+  // thread per product.
+  constexpr int kWarps = kThreads / 32;
+  const int rblocks = (P.m + kWarps - 1) / kWarps;
+  if ((int)blockIdx.x < rblocks) {
+    const int i = blockIdx.x * kWarps + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (i >= P.m) return;
+    const InstState& I = B.inst[B.res_inst[i]];
+    if (I.converged) return;  // uniform over the warp
+    const int q0 = P.at_ptr[i], q1 = P.at_ptr[i + 1];
+    double g = 0.0;
+    if (!P.at_val) {
+      unsigned long long acc = 0ull;
+      for (int q = q0 + lane; q < q1; q += 32) acc += Wk.s_fx[P.at_idx[q]];
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      g = __dmul_rn(__ull2double_rn(acc), Wk.inv_fx_scale);
+    } else {
+      for (int qb = q0; qb < q1; qb += 32) {
+        const int q = qb + lane;
+        const double term = q < q1 ? __dmul_rn(P.at_val[q], __dmul_rn(__ull2double_rn(Wk.s_fx[P.at_idx[q]]),
+                                                                       Wk.inv_fx_scale))
+                                   : 0.0;
+        const int cnt = q1 - qb < 32 ? q1 - qb : 32;
+        for (int k = 0; k < cnt; ++k) {
+          const double t = __shfl_sync(0xffffffffu, term, k);
+          if (lane == 0) g = __dadd_rn(g, t);
+        }
       }
-      const double shrink = __dsub_rn(1.0, __dmul_rn(I.tau, I.mu));
-      const double yo = Wk.y[gid], c = P.c[gid];
-      const double yn = __dsub_rn(__dmul_rn(shrink, yo), __dmul_rn(I.tau, __dsub_rn(c, g)));
-      Wk.y[gid] = yn > 0.0 ? yn : 0.0;
-      Wk.g[gid] = g;
-      Wk.sum_y[gid] = __dadd_rn(Wk.sum_y[gid], yo);
-      Wk.sum_g[gid] = __dadd_rn(Wk.sum_g[gid], g);
-      B.cy_res[gid] = yo != 0.0 ? __dmul_rn(c, yo) : 0.0;
     }
+    if (lane != 0) return;
+    const double shrink = __dsub_rn(1.0, __dmul_rn(I.tau, I.mu));
+    const double yo = Wk.y[i], c = P.c[i];
+    const double yn = __dsub_rn(__dmul_rn(shrink, yo), __dmul_rn(I.tau, __dsub_rn(c, g)));
+    Wk.y[i] = yn > 0.0 ? yn : 0.0;
+    Wk.g[i] = g;
+    Wk.sum_y[i] = __dadd_rn(Wk.sum_y[i], yo);
+    Wk.sum_g[i] = __dadd_rn(Wk.sum_g[i], g);
+    B.cy_res[i] = yo != 0.0 ? __dmul_rn(c, yo) : 0.0;
+    return;
   }
-  if (gid < P.n && !B.inst[B.prod_inst[gid]].converged)
-    Wk.s[gid] = __dmul_rn(__ull2double_rn(Wk.s_fx[gid]), Wk.inv_fx_scale);
+  const int j = (blockIdx.x - rblocks) * blockDim.x + threadIdx.x;
+  if (j < P.n && !B.inst[B.prod_inst[j]].converged)
+    Wk.s[j] = __dmul_rn(__ull2double_rn(Wk.s_fx[j]), Wk.inv_fx_scale);
 }
 
 // One block per instance: sum z_l, c^T y, r^T s of the iteration; counters.
-__global__ void __launch_bounds__(kThreads) k_b_finish(Problem P, Work Wk) {
+constexpr int kFinThreads = 1024;
+
+// sum of z_seg over [l0, l1) by the block: four interleaved accumulators per
+// thread (a fixed order), so the dependent binary64 adds are a quarter as deep
+__device__ double seg_sum(const double* __restrict__ z, long long l0, long long l1) {
+  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  const long long st = blockDim.x;
+  long long l = l0 + threadIdx.x;
+  for (; l + 3 * st < l1; l += 4 * st) {
+    a0 += z[l];
+    a1 += z[l + st];
+    a2 += z[l + 2 * st];
+    a3 += z[l + 3 * st];
+  }
+  for (; l < l1; l += st) a0 += z[l];
+  return (a0 + a1) + (a2 + a3);
+}
+
+__global__ void __launch_bounds__(kFinThreads) k_b_finish(Problem P, Work Wk) {
   __shared__ double sh[32];
   const BatchMaps& B = Wk.bm;
   const int b = blockIdx.x;
   InstState& I = B.inst[b];
   if (I.converged) return;
   double zs = 0.0, cys = 0.0, Ps = 0.0;
-  for (long long l = B.seg_off[b] + threadIdx.x; l < B.seg_off[b + 1]; l += blockDim.x) zs += B.z_seg[l];
+  zs = seg_sum(B.z_seg, B.seg_off[b], B.seg_off[b + 1]);
   for (int i = B.res_ptr[b] + threadIdx.x; i < B.res_ptr[b + 1]; i += blockDim.x) cys += B.cy_res[i];
   for (int j = B.prod_ptr[b] + threadIdx.x; j < B.prod_ptr[b + 1]; j += blockDim.x)
     Ps += __dmul_rn(P.r[j], Wk.s[j]);
@@ -117,7 +159,7 @@ __global__ void __launch_bounds__(kThreads) k_b_finish(Problem P, Work Wk) {
 
 // One block per instance: KKT residual of the epoch averages and the restart
 // test, as for a single instance.
-__global__ void __launch_bounds__(kThreads) k_b_eval_finish(Problem P, Work Wk, RunConfig cfg) {
+__global__ void __launch_bounds__(kFinThreads) k_b_eval_finish(Problem P, Work Wk, RunConfig cfg) {
   __shared__ double sh[32];
   __shared__ int restart, progress;
   const BatchMaps& B = Wk.bm;
@@ -134,7 +176,7 @@ __global__ void __launch_bounds__(kThreads) k_b_eval_finish(Problem P, Work Wk, 
     if (o > 0.0) over2 += __dmul_rn(o, o);
     c2 += __dmul_rn(c, c);
   }
-  for (long long l = B.seg_off[b] + threadIdx.x; l < B.seg_off[b + 1]; l += blockDim.x) zs += B.z_seg[l];
+  zs = seg_sum(B.z_seg, B.seg_off[b], B.seg_off[b + 1]);
   cy = bsum(cy, sh);
   over2 = bsum(over2, sh);
   c2 = bsum(c2, sh);
@@ -190,8 +232,8 @@ cudaError_t launch_batch_iteration(const Problem& P, const Work& Wk, const RunCo
   if (e != cudaSuccess) return e;
   e = launch_reduce_products(P, Wk.plan, zparts, Wk.part, Wk.s_fx, Wk.st, s);
   if (e != cudaSuccess) return e;
-  k_b_dual<<<blocks_for(P.m > P.n ? P.m : P.n), kThreads, 0, s>>>(P, Wk);
-  k_b_finish<<<Wk.bm.count, kThreads, 0, s>>>(P, Wk);
+  k_b_dual<<<(P.m + kThreads / 32 - 1) / (kThreads / 32) + blocks_for(P.n), kThreads, 0, s>>>(P, Wk);
+  k_b_finish<<<Wk.bm.count, kFinThreads, 0, s>>>(P, Wk);
   return cudaGetLastError();
 }
 
@@ -201,7 +243,7 @@ cudaError_t launch_batch_eval(const Problem& P, const Work& Wk, const RunConfig&
   int zparts = 0;
   cudaError_t e = launch_segment_pass(P, Wk, cfg, Wk.marg_eval, false, s, &zparts);
   if (e != cudaSuccess) return e;
-  k_b_eval_finish<<<Wk.bm.count, kThreads, 0, s>>>(P, Wk, cfg);
+  k_b_eval_finish<<<Wk.bm.count, kFinThreads, 0, s>>>(P, Wk, cfg);
   return cudaGetLastError();
 }
 
