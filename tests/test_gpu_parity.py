@@ -283,6 +283,39 @@ def test_invalid_instances_are_rejected(mut, status, needle):
     assert ei.value.status == status and needle in str(ei.value)
 
 
+def test_first_failing_nonzero_is_reported():
+    """The per-nonzero checks run on the device; the message names the first
+    failing nonzero in CSR order, as a host loop would, whatever fails later."""
+    from paper_2602_22421_gb300 import SpfomError
+
+    def two_faults(I):
+        I.v[7] = -1.0                    # an earlier nonzero: bad attraction
+        I.seg_prod[30] = I.n + 5         # a later one: id out of range
+    with pytest.raises(SpfomError) as ei:
+        Solver(_bad(two_faults))
+    assert ei.value.status == 1 and "v[7]" in str(ei.value)
+
+    def id_first(I):
+        I.seg_prod[2] = -3
+        I.v[9] = 0.0
+    with pytest.raises(SpfomError) as ei:
+        Solver(_bad(id_first))
+    assert ei.value.status == 1 and "seg_prod[2]" in str(ei.value)
+
+
+def test_binary32_range_is_checked_for_precision_32():
+    """Precision 32 keeps binary32 images of v and v - w: an attraction below
+    binary32's normal range is unsupported there (ENOTSUP) and fine in
+    precision 64."""
+    from paper_2602_22421_gb300 import SpfomError
+    inst = _bad(lambda I: I.v.__setitem__(5, 1e-40))
+    with pytest.raises(SpfomError) as ei:
+        Solver(inst, precision=32)
+    assert ei.value.status == 7 and "precision 32" in str(ei.value) and "at 5 " in str(ei.value)
+    with Solver(inst) as s:
+        assert s.step(3)["iters"] == 3
+
+
 def test_large_consideration_set_is_unsupported():
     from paper_2602_22421_gb300 import SpfomError
     inst = make_instance(n=40, m=5, L=10, kmin=33, kmax=33, seed=3)
