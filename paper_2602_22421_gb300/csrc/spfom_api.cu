@@ -687,6 +687,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   SPFOM_TRY(dalloc(ctx, &W.zpart_eval, (size_t)std::max(W.seg_blocks, W.zparts_eval)));
   SPFOM_TRY(dalloc(ctx, &W.cypart, (size_t)W.vec_blocks));
   SPFOM_TRY(dalloc(ctx, &W.Ppart, (size_t)W.vec_blocks));
+  SPFOM_TRY(dalloc(ctx, &W.zmpart, (size_t)W.vec_blocks));
   W.x_cur = nullptr;
   if (ctx->p.batch_frac < 1.0) SPFOM_TRY(dalloc(ctx, &W.x_cur, (size_t)nnz));
   W.xsum = nullptr;

@@ -171,6 +171,7 @@ struct Work {
   double* zpart_eval;  // per-block partial sums of z (evaluation)
   double* cypart;      // [vec_blocks]
   double* Ppart;       // [vec_blocks]
+  double* zmpart;      // [vec_blocks] partial sums of m_j s_j (the iterate's sum of z, fast path)
   double* x_cur;       // [nnz] current responses (sampling only)
   DevState* st;
   int seg_blocks;      // blocks of the general segment kernel

@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
   __shared__ double sh[96];
   __shared__ bool last;
   const double tau = st->tau, shrink = __dsub_rn(1.0, __dmul_rn(st->tau, st->mu));
-  double cy = 0.0, pr = 0.0;
+  double cy = 0.0, pr = 0.0, zm = 0.0;
   const bool fx = Wk.fast && full;
   // The first blocks take one resource per warp: the lanes fetch the
   // resource's products and their sales together (one round of dependent
@@ -309,15 +309,16 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
       if (fx) {
         sj = __dmul_rn(__ull2double_rn(Wk.s_fx[j]), Wk.inv_fx_scale);
         Wk.s[j] = sj;
+        zm = __dmul_rn(Wk.marg[j], sj);  // sum_l z_l = sum_j m_j s_j (z_l = sum_j m_j x_lj)
       }
       pr = __dmul_rn(P.r[j], sj);
     }
   }
-  double unused = 0.0;
-  block_sum3(cy, pr, unused, sh);
+  block_sum3(cy, pr, zm, sh);
   if (threadIdx.x == 0) {
     Wk.cypart[blockIdx.x] = cy;
     Wk.Ppart[blockIdx.x] = pr;
+    Wk.zmpart[blockIdx.x] = zm;
     __threadfence();
     const unsigned prev = atomicAdd(&st->ticket, 1u);
     last = (prev == gridDim.x - 1);
@@ -327,7 +328,11 @@ __global__ void __launch_bounds__(kVecThreads) k_dual_step(Problem P, Work Wk, R
   // Last block: fold the partial sums (strided over the block, then a tree).
   __threadfence();
   double zs = 0.0, cys = 0.0, Ps = 0.0;
-  for (int b = threadIdx.x; b < zparts; b += blockDim.x) zs += __ldcg(Wk.zpart + b);
+  if (fx) {  // the segment kernel left z to this step
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) zs += __ldcg(Wk.zmpart + b);
+  } else {
+    for (int b = threadIdx.x; b < zparts; b += blockDim.x) zs += __ldcg(Wk.zpart + b);
+  }
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
     cys += __ldcg(Wk.cypart + b);
     Ps += __ldcg(Wk.Ppart + b);

@@ -89,8 +89,8 @@ struct SegOrder {
 // layout (slot valid iff lane + p W < lim = K) and T = 32 for the slot-major
 // layout (slot valid iff p < lim = the chunk's slot rows and its id >= 0).
 // rp: the segment's carried Dinkelbach ratio (or null); zs: where to write its
-// value (or null: added to zacc).
-template <int W, int P, bool SL>
+// value (or null: added to zacc). ZV: form the value at all (see below).
+template <int W, int P, bool SL, bool ZV>
 __device__ __forceinline__ void seg_solve(const FastArgs& A, const double* __restrict__ mg,
                                           const int* __restrict__ sp, const double* __restrict__ vv,
                                           const double* __restrict__ vtv, int lim, double lam, double vt0, float* rp,
@@ -188,21 +188,25 @@ __device__ __forceinline__ void seg_solve(const FastArgs& A, const double* __res
     }
     S = prev;
   }
-  // binary64 values of the chosen assortment.
+  // binary64 values of the chosen assortment. The segment's value z = q N* is
+  // formed only where it is asked for (evaluation passes, per-segment values of
+  // a batch): an iterate pass with product sums leaves sum_l z_l to the dual
+  // step, which forms it as sum_j m_j s_j (z_l = sum_j m_j x_lj), and skips N*.
+  constexpr bool Z = ZV;  // the launch chose it: no product sums, or per-segment values asked for
   double Nl = 0.0, Dl = 0.0;
 #pragma unroll
   for (int p = 0; p < P; ++p)
     if ((S >> p) & 1u) {
       Dl += vtv[p * T];
-      Nl = fma(mg[jv[p]], vv[p * T], Nl);
+      if (Z) Nl = fma(mg[jv[p]], vv[p * T], Nl);
     }
 #pragma unroll
   for (int o = W >> 1; o > 0; o >>= 1) {
-    Nl += __shfl_xor_sync(gmask, Nl, o, W);
+    if (Z) Nl += __shfl_xor_sync(gmask, Nl, o, W);
     Dl += __shfl_xor_sync(gmask, Dl, o, W);
   }
   const double q = quotient(lam, vt0 + Dl);
-  if (lane == 0) {
+  if (Z && lane == 0) {
     if (zs) *zs = q * Nl;
     else zacc += q * Nl;
   }
@@ -256,14 +260,14 @@ struct SlWalk {
 };
 
 // One segment l of the CSR layout.
-template <int W, int P>
+template <int W, int P, bool ZV = true>
 __device__ __forceinline__ void fast_segment(const FastArgs& A, const double* __restrict__ mg, long long l, int lane,
                                              unsigned gmask, unsigned long long* sums, int base, double& zacc,
                                              int& fallbacks) {
   const Problem& Pr = A.P;
   const long long b = Pr.seg_ptr[l];
   const int K = (int)(Pr.seg_ptr[l + 1] - b);
-  seg_solve<W, P, false>(A, mg, Pr.seg_prod + b + lane, Pr.v + b + lane, Pr.vt + b + lane, K, Pr.lam[l], Pr.vt0[l],
+  seg_solve<W, P, false, ZV>(A, mg, Pr.seg_prod + b + lane, Pr.v + b + lane, Pr.vt + b + lane, K, Pr.lam[l], Pr.vt0[l],
                          A.rprev ? A.rprev + l : nullptr, A.z_seg ? A.z_seg + l : nullptr, lane, gmask, sums, base,
                          zacc, fallbacks);
 }
@@ -273,7 +277,7 @@ __device__ __forceinline__ void fast_segment(const FastArgs& A, const double* __
 // gather of a segment's margins reads shared memory instead of L2.
 // SL = 1 (tiling 3): the slot-major copy, one warp per chunk of 32 / W
 // positions, every slot row one contiguous load of the warp.
-template <int W, int P, int SC, int MS = 0, int SL = 0>
+template <int W, int P, int SC, int MS = 0, int SL = 0, bool ZV = (SC == 0)>
 __global__ void __launch_bounds__(MS ? kMsThreads : kFastThreads, MS ? 1 : 2) k_seg_fast(FastArgs A) {
   extern __shared__ unsigned long long acc[];  // [n] product sales (fixed point) when SC == 1; MS: + [n] margins
   __shared__ double sh[32];
@@ -304,7 +308,7 @@ __global__ void __launch_bounds__(MS ? kMsThreads : kFastThreads, MS ? 1 : 2) k_
       const long long o = wk.o0 + wl;
       const int rows = (int)((wk.o1 - wk.o0) >> 5);
       const long long pos = wk.c * (32 / W) + wl / W;
-      seg_solve<W, P, true>(A, mg, A.sl.prod + o, A.sl.v + o, A.sl.vt + o, rows, __ldcg(A.sl.lam + pos),
+      seg_solve<W, P, true, ZV>(A, mg, A.sl.prod + o, A.sl.v + o, A.sl.vt + o, rows, __ldcg(A.sl.lam + pos),
                             __ldcg(A.sl.vt0 + pos), A.sl.rprev ? A.sl.rprev + pos : nullptr, nullptr, lane, gmask,
                             sums, 0, zacc, fallbacks);
     }
@@ -314,7 +318,7 @@ __global__ void __launch_bounds__(MS ? kMsThreads : kFastThreads, MS ? 1 : 2) k_
       const long long l = ord.next();
       if (l >= Pr.L) continue;
       if (A.seg_inst && A.inst_conv[A.seg_inst[l]]) continue;  // batch: instance already converged
-      fast_segment<W, P>(A, mg, l, lane, gmask, sums, 0, zacc, fallbacks);
+      fast_segment<W, P, ZV>(A, mg, l, lane, gmask, sums, 0, zacc, fallbacks);
     }
   }
   const double tot = block_sum_d(zacc, sh);
@@ -419,10 +423,7 @@ __device__ __forceinline__ void f32_solve(const F32Args& A, const float* __restr
   }
   if (rp && lane == 0) *rp = R;
   const float q = lam / (vt0 + Dsel);
-  if (lane == 0) {
-    if (zs) *zs = (double)(q * Nsel);
-    else zacc += q * Nsel;
-  }
+  if (lane == 0 && zs) *zs = (double)(q * Nsel);  // the sum of z comes from the dual step (sum_j m_j s_j)
   if (SC != 0) {
     for (unsigned msk = sel; msk; msk &= msk - 1) {  // this lane's chosen slots
       const int k = (__ffs(msk) - 1) * T;
@@ -727,17 +728,25 @@ void set_order(long long L, int W, int grid, bool batch, long long* a, long long
   *d = (long long)((__int128)nwarps * pa % nch);
 }
 
+template <int SC, bool ZV>
+cudaError_t launch_fast_wz(const FastArgs& A, int W, int grid, int smem, cudaStream_t s) {
+  switch (W) {  // 8 products per lane
+    case 1: k_seg_fast<1, 8, SC, 0, 0, ZV><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 2: k_seg_fast<2, 8, SC, 0, 0, ZV><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 4: k_seg_fast<4, 8, SC, 0, 0, ZV><<<grid, kFastThreads, smem, s>>>(A); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+// Segment values are formed by evaluation passes and for the per-segment values
+// of a batch; an iterate pass of a single instance leaves them to the dual step.
 template <int SC>
 cudaError_t launch_fast_w(const FastArgs& A0, int W, int grid, int smem, cudaStream_t s) {
   FastArgs A = A0;
   set_order(A0.P.L, W, grid, A0.seg_inst != nullptr, &A.perm_a, &A.perm_d);
-  switch (W) {  // 8 products per lane
-    case 1: k_seg_fast<1, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
-    case 2: k_seg_fast<2, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
-    case 4: k_seg_fast<4, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
-    default: return cudaErrorInvalidValue;
-  }
-  return cudaGetLastError();
+  if constexpr (SC == 0) return launch_fast_wz<0, true>(A, W, grid, smem, s);
+  else return A.z_seg ? launch_fast_wz<SC, true>(A, W, grid, smem, s) : launch_fast_wz<SC, false>(A, W, grid, smem, s);
 }
 
 template <int SC>
@@ -781,14 +790,19 @@ cudaError_t launch_f32_p8(const F32Args& A0, int W8, int grid, int smem, cudaStr
 
 // Margins in shared memory (precision-64 tiling 2, precision-32 tiling 7):
 // one block of kMsThreads per SM, shared-memory sums only.
-cudaError_t launch_fast_ms(const FastArgs& A, int W8, int grid, int smem, cudaStream_t s) {
+template <bool ZV>
+cudaError_t launch_fast_msz(const FastArgs& A, int W8, int grid, int smem, cudaStream_t s) {
   switch (W8) {
-    case 1: k_seg_fast<1, 8, 1, 1><<<grid, kMsThreads, smem, s>>>(A); break;
-    case 2: k_seg_fast<2, 8, 1, 1><<<grid, kMsThreads, smem, s>>>(A); break;
-    case 4: k_seg_fast<4, 8, 1, 1><<<grid, kMsThreads, smem, s>>>(A); break;
+    case 1: k_seg_fast<1, 8, 1, 1, 0, ZV><<<grid, kMsThreads, smem, s>>>(A); break;
+    case 2: k_seg_fast<2, 8, 1, 1, 0, ZV><<<grid, kMsThreads, smem, s>>>(A); break;
+    case 4: k_seg_fast<4, 8, 1, 1, 0, ZV><<<grid, kMsThreads, smem, s>>>(A); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_fast_ms(const FastArgs& A, int W8, int grid, int smem, cudaStream_t s) {
+  return A.z_seg ? launch_fast_msz<true>(A, W8, grid, smem, s) : launch_fast_msz<false>(A, W8, grid, smem, s);
 }
 
 cudaError_t launch_f32_ms(const F32Args& A, int W8, int grid, int smem, cudaStream_t s) {
@@ -876,6 +890,19 @@ int blocks_per_sm(K kernel, int smem, int threads = kFastThreads) {
   return nb;
 }
 
+// The shared-memory limit of the variants that form segment values (a batch's
+// per-segment values), which occupancy() and ms_blocks() do not query.
+bool zv_attributes(int W8, int smem, int ms_smem) {
+  bool ok = true;
+  auto set = [&](auto k, int bytes) {
+    if (bytes > 0) ok &= cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+  };
+  if (W8 == 1) { set(k_seg_fast<1, 8, 1, 0, 0, true>, smem); set(k_seg_fast<1, 8, 1, 1, 0, true>, ms_smem); }
+  if (W8 == 2) { set(k_seg_fast<2, 8, 1, 0, 0, true>, smem); set(k_seg_fast<2, 8, 1, 1, 0, true>, ms_smem); }
+  if (W8 == 4) { set(k_seg_fast<4, 8, 1, 0, 0, true>, smem); set(k_seg_fast<4, 8, 1, 1, 0, true>, ms_smem); }
+  return ok;
+}
+
 // Blocks per SM of the margins-in-shared kernels (binary64 or binary32).
 int ms_blocks(int W8, int smem, bool f32) {
   if (W8 == 1) return f32 ? blocks_per_sm(k_seg_f32<1, 8, 1, 1>, smem, kMsThreads)
@@ -947,6 +974,7 @@ bool fast_plan(int n, int kmax, int sms, FastPlan* plan) {
     q.smem = sc == 1 ? smem : 0;
     plan->sl_attr = W8 == 1 ? sl_attributes<1>(q) : (W8 == 2 ? sl_attributes<2>(q) : sl_attributes<4>(q));
   }
+  if (!zv_attributes(W8, sc == 1 ? smem : 0, plan->ms_ok ? plan->ms_smem64 : 0)) return false;
   plan->W16 = kmax <= 16 ? 1 : 2;
   plan->W = W;
   plan->W8 = W8;
