@@ -114,7 +114,8 @@ __global__ void k_b_dual(Problem P, Work Wk) {
     Wk.s[j] = __dmul_rn(__ull2double_rn(Wk.s_fx[j]), Wk.inv_fx_scale);
 }
 
-// One block per instance: sum z_l, c^T y, r^T s of the iteration; counters.
+// One block per instance: sum z_l (= sum_j m_j s_j), c^T y, r^T s of the
+// iteration; counters.
 constexpr int kFinThreads = 1024;
 
 // sum of z_seg over [l0, l1) by the block: four interleaved accumulators per
@@ -140,10 +141,11 @@ __global__ void __launch_bounds__(kFinThreads) k_b_finish(Problem P, Work Wk) {
   InstState& I = B.inst[b];
   if (I.converged) return;
   double zs = 0.0, cys = 0.0, Ps = 0.0;
-  zs = seg_sum(B.z_seg, B.seg_off[b], B.seg_off[b + 1]);
   for (int i = B.res_ptr[b] + threadIdx.x; i < B.res_ptr[b + 1]; i += blockDim.x) cys += B.cy_res[i];
-  for (int j = B.prod_ptr[b] + threadIdx.x; j < B.prod_ptr[b + 1]; j += blockDim.x)
+  for (int j = B.prod_ptr[b] + threadIdx.x; j < B.prod_ptr[b + 1]; j += blockDim.x) {
     Ps += __dmul_rn(P.r[j], Wk.s[j]);
+    zs += __dmul_rn(Wk.marg[j], Wk.s[j]);  // sum_l z_l = sum_j m_j s_j over the instance
+  }
   zs = bsum(zs, sh);
   cys = bsum(cys, sh);
   Ps = bsum(Ps, sh);

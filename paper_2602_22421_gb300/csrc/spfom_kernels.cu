@@ -510,7 +510,9 @@ cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfi
                                 bool iterate, cudaStream_t s, int* zparts_out) {
   const int* seg_inst = Wk.batch ? Wk.bm.seg_inst : nullptr;
   const int* conv = Wk.batch ? Wk.bm.conv : nullptr;
-  double* z_seg = Wk.batch ? Wk.bm.z_seg : nullptr;
+  // per-segment values: evaluation passes of a batch (an iterate pass takes the
+  // sum of z per instance from the products, sum_j m_j s_j)
+  double* z_seg = (Wk.batch && !iterate) ? Wk.bm.z_seg : nullptr;
   if (Wk.v2 && (!iterate || !(cfg.f32 && Wk.v32))) {
     // double-float precision-64 kernel (also the evaluation pass of precision 32)
     const bool it = iterate;

@@ -354,7 +354,8 @@ __global__ void __launch_bounds__(kFastThreads, 2) k_seg_fast_bchunk(FastArgs A)
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += blockDim.x) acc[i] = 0ull;
     __syncthreads();
-    for (long long l = l0 + threadIdx.x / W; l < l1; l += gpb) fast_segment<W, P>(A, A.marg, l, lane, gmask, acc, pb, zacc, fallbacks);
+    for (long long l = l0 + threadIdx.x / W; l < l1; l += gpb)
+      fast_segment<W, P, false>(A, A.marg, l, lane, gmask, acc, pb, zacc, fallbacks);  // an iterate pass: no values
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += blockDim.x)
       if (acc[i]) atomicAdd(A.s_fx + pb + i, acc[i]);
