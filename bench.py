@@ -149,6 +149,17 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
+def code_digest(path):
+    """SHA-256 of a source file's code: line comments and blank lines dropped,
+    so that a capture stays valid across comment-only edits."""
+    lines = []
+    for line in open(path, encoding="utf-8"):
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            lines.append(code)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def kernel_traffic(kernel, tiling, src, nnz):
     """DRAM bytes per launch of `kernel` in `tiling` from the committed ncu
     summary, if it was taken on the current kernel source; scaled by nonzeros."""
@@ -158,8 +169,7 @@ def kernel_traffic(kernel, tiling, src, nnz):
         d = json.load(f).get(f"{kernel}/tiling{tiling}")
     if not d:
         return None, None
-    sha = hashlib.sha256(open(os.path.join(CSRC, src), "rb").read()).hexdigest()
-    if d.get("kernel_source_sha256") != sha:
+    if d.get("kernel_code_sha256") != code_digest(os.path.join(CSRC, src)):
         return None, "kernel changed since the ncu capture"
     return d["dram_bytes_per_launch"] * nnz / d["nnz"], d.get("capture")
 

@@ -13,10 +13,12 @@
 // assortment is S* = {j : a_j > R* b_j} where R* = N(S*)/D(S*),
 // N(S) = sum_S a_j, D(S) = vt_0 + sum_S b_j (the greedy order of Lemma 1:
 // item j enters exactly when its key a_j / b_j exceeds the optimal rate).
-// Dinkelbach's iteration R <- N(S(R))/D(S(R)), S(R) = {a_j > R b_j}, started at
-// R = 0, shrinks S monotonically to such a fixed point, and every fixed point
-// is optimal: for any T, N(T) - R D(T) <= N(S) - R D(S) = 0. It runs in
-// binary32 on binary32 images of the inputs. The decision is certified when
+// Dinkelbach's iteration R <- N(S(R))/D(S(R)), S(R) = {a_j > R b_j}, reaches
+// such a fixed point from any start (after one step R <= R*; from there R
+// rises and S shrinks), and every fixed point is optimal: for any T,
+// N(T) - R D(T) <= N(S) - R D(S) = 0. It runs in binary32 on binary32 images
+// of the inputs, started from the segment's ratio of the previous iteration
+// (the margins move little between iterations). The decision is certified when
 // every candidate clears the threshold by a relative margin
 // |a_j - R b_j| > 2^-16 (a_j + R b_j); the binary32 rounding of a_j, b_j, N, D
 // and R is below 5e-6 relative for consideration sets of up to 32 products,
@@ -24,19 +26,24 @@
 // certified (a near-tie, or an input outside binary32's normal range) repeat
 // the iteration in binary64.
 //
-// Values, in binary64: D* = vt_0 + sum_{S*} vt_j, N* = sum_{S*} m_j v_j,
-// q = lambda / D*, z = q N*, and the sales x_j = q v_j of the chosen products.
+// Values, in binary64: D* = vt_0 + sum_{S*} vt_j, q = lambda / D* and the
+// sales x_j = q v_j of the chosen products; N* = sum_{S*} m_j v_j and
+// z = q N* only where segment values are asked for (evaluation passes, a
+// batch's per-segment values): an iterate pass leaves sum_l z_l to the dual
+// step, which forms it as sum_j m_j s_j.
 //
-// Layout: W lanes per segment, P = 4 products per lane (lane r holds products
-// r, r + W, r + 2W, r + 3W of the segment's CSR slice, so each group reads its
-// slice with contiguous loads), and the group's binary64 reductions cost
-// log2(W) shuffle steps shared by 32/W segments per warp instruction.
+// Layout: W lanes per segment, P = 8 products per lane (lane r holds products
+// r, r + W, r + 2W, ... of the segment's set: contiguous loads from the CSR
+// slice, or one 32-entry row per slot in the slot-major copy), and the group's
+// binary64 reductions cost log2(W) shuffle steps shared by 32/W segments per
+// warp instruction. The margins are read from global memory, or (MS) from a
+// copy in shared memory.
 //
 // Sales aggregate: each block sums x_j per product in shared memory as
 // unsigned 64-bit fixed point (x * 2^F rounded; F fixed per instance so that
 // the arrival mass fits in 62 bits), which makes the sum exact and
 // independent of order, and writes its n partial sums out; k_reduce_products
-// folds them into the product sales. No contended global atomics.
+// folds them into the product sales. Wider instances add into global sums.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
