@@ -131,8 +131,9 @@ constexpr size_t kSlack = 4;  // elements of zeroed slack after arrays that bulk
 
 bool is_finite(double x) { return std::isfinite(x); }
 
-// Host checks of an instance. items = false leaves the per-nonzero checks
-// (ids, repeats, v, w) to the device pass of spfom_load_instance.
+// Host checks of an instance. items = false leaves the per-segment and
+// per-nonzero checks (offsets, lambda, v0, ids, repeats, v, w) and the largest
+// set to the device pass of spfom_load_instance (*kmax_out is then not set).
 spfom_status validate(spfom_ctx* ctx, const spfom_instance* I, int* kmax_out, bool items = true) {
   if (!I) return fail(ctx, SPFOM_EINVAL, "instance is NULL");
   if (I->n < 0 || I->m < 0 || I->L < 0) return fail(ctx, SPFOM_EINVAL, "negative size");
@@ -159,13 +160,12 @@ spfom_status validate(spfom_ctx* ctx, const spfom_instance* I, int* kmax_out, bo
   std::fill(stamp.begin(), stamp.end(), -1);
   std::vector<long long> stampl((size_t)I->n + 1, -1);
   int kmax = 0;
-  for (long long l = 0; l < I->L; ++l) {
+  for (long long l = 0; l < (items ? I->L : 0); ++l) {
     long long b = I->seg_ptr[l], e = I->seg_ptr[l + 1];
     if (e < b) return fail(ctx, SPFOM_EINVAL, "seg_ptr not monotone at %lld", l);
     if (e - b > kmax) kmax = (int)(e - b > 1 << 30 ? 1 << 30 : e - b);
     if (!(I->lam[l] >= 0.0) || !is_finite(I->lam[l])) return fail(ctx, SPFOM_EINVAL, "lam[%lld] must be >= 0", l);
     if (!(I->v0[l] > 0.0) || !is_finite(I->v0[l])) return fail(ctx, SPFOM_EINVAL, "v0[%lld] must be > 0", l);
-    if (!items) continue;
     for (long long p = b; p < e; ++p) {
       int j = I->seg_prod[p];
       if (j < 0 || j >= I->n) return fail(ctx, SPFOM_EINVAL, "seg_prod[%lld] = %d out of range", p, j);
@@ -443,19 +443,12 @@ void spfom_destroy(spfom_ctx* ctx) {
 
 spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   if (!ctx) return SPFOM_EINVAL;
-  int kmax = 0;
-  spfom_status s = validate(ctx, I, &kmax, false);  // the per-nonzero checks run on the device below
+  int kmax = 0;  // from the device pass below
+  spfom_status s = validate(ctx, I, &kmax, false);  // the per-segment and per-nonzero checks run on the device
   if (s != SPFOM_OK) return s;
-  if (kmax > 32) return fail(ctx, SPFOM_ENOTSUP, "consideration set of %d products (at most 32 supported)", kmax);
   if (I->L > 0 && (I->seg_ptr[I->L] > 0) && (!I->seg_prod || !I->v))
     return fail(ctx, SPFOM_EINVAL, "missing segment arrays");
-  if (ctx->p.precision == 32) {
-    // binary32 copies must stay normal numbers (zero allowed for lambda; v and v - w: on the device)
-    auto in32 = [](double x, bool zero_ok) { return (zero_ok && x == 0.0) || (x >= 1.1754943508222875e-38 && x <= 3.4028234663852886e+38); };
-    for (long long l = 0; l < I->L; ++l)
-      if (!in32(I->lam[l], true) || !in32(I->v0[l], false))
-        return fail(ctx, SPFOM_ENOTSUP, "precision 32: lambda or v0 of segment %lld outside binary32's range", l);
-  }
+  if (I->L > 0 && I->seg_ptr[I->L] < 0) return fail(ctx, SPFOM_EINVAL, "seg_ptr not monotone at %lld", I->L - 1);
   SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
   free_instance(ctx);
   const int n = I->n, m = I->m;
@@ -505,26 +498,40 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   P.at_ptr = d_atptr; P.at_idx = d_atidx; P.at_val = d_atval;
   P.seg_ptr = d_segptr; P.seg_prod = d_prod; P.v = d_v; P.vt = d_vt; P.lam = d_lam; P.vt0 = d_vt0;
   {
-    // per-nonzero checks on the device: the smallest failing position and what failed
+    // per-segment and per-nonzero checks on the device: the first failure in
+    // the order of a host loop over segments, and the largest set
     unsigned long long* d_keys = nullptr;
-    SPFOM_TRY(dalloc(ctx, &d_keys, 2));
-    unsigned long long keys[2];
-    cudaError_t ev = spfom::launch_validate_items(P, d_w, ctx->p.precision == 32, d_keys, ctx->stream);
+    SPFOM_TRY(dalloc(ctx, &d_keys, 3));
+    unsigned long long keys[3];
+    cudaError_t ev = spfom::launch_validate_items(P, d_w, d_v0, ctx->p.precision == 32, d_keys, ctx->stream);
     if (ev == cudaSuccess) ev = cudaMemcpyAsync(keys, d_keys, sizeof keys, cudaMemcpyDeviceToHost, ctx->stream);
     if (ev == cudaSuccess) ev = cudaStreamSynchronize(ctx->stream);
     if (ev != cudaSuccess) { free_instance(ctx); return cuda_fail(ctx, ev, "instance check"); }
-    if (keys[0] != ~0ull || keys[1] != ~0ull) {
-      const bool inval = keys[0] != ~0ull;
-      const long long p = (long long)((inval ? keys[0] : keys[1]) >> 3);
-      const int code = (int)((inval ? keys[0] : keys[1]) & 7);
-      const int j = I->seg_prod[p];
-      const long long l = (long long)(std::upper_bound(I->seg_ptr, I->seg_ptr + L + 1, (int64_t)p) - I->seg_ptr) - 1;
+    if (keys[0] != ~0ull) {
+      const long long l = (long long)(keys[0] >> spfom::kCheckSegShift);
+      const int sub = (int)(keys[0] & ((1ull << spfom::kCheckSegShift) - 1));
       free_instance(ctx);
-      if (!inval) return fail(ctx, SPFOM_ENOTSUP, "precision 32: attraction at %lld outside binary32's normal range", p);
+      if (sub == spfom::kSegOrder) return fail(ctx, SPFOM_EINVAL, "seg_ptr not monotone at %lld", l);
+      if (sub == spfom::kSegLam) return fail(ctx, SPFOM_EINVAL, "lam[%lld] must be >= 0", l);
+      if (sub == spfom::kSegV0) return fail(ctx, SPFOM_EINVAL, "v0[%lld] must be > 0", l);
+      const long long p = I->seg_ptr[l] + ((sub - spfom::kSegItems) >> 3);
+      const int code = (sub - spfom::kSegItems) & 7, j = I->seg_prod[p];
       if (code == spfom::kBadId) return fail(ctx, SPFOM_EINVAL, "seg_prod[%lld] = %d out of range", p, j);
       if (code == spfom::kRepeated) return fail(ctx, SPFOM_EINVAL, "product %d repeated in segment %lld", j, l);
       if (code == spfom::kBadV) return fail(ctx, SPFOM_EINVAL, "v[%lld] must be finite and > 0", p);
       return fail(ctx, SPFOM_EINVAL, "w[%lld] must lie in [0, v]", p);
+    }
+    kmax = (int)keys[2];
+    if (kmax > 32) {
+      free_instance(ctx);
+      return fail(ctx, SPFOM_ENOTSUP, "consideration set of %d products (at most 32 supported)", kmax);
+    }
+    if (keys[1] != ~0ull) {  // precision 32: attractions first (in nonzero order), then the segments
+      const long long pos = (long long)keys[1];
+      free_instance(ctx);
+      if (pos < nnz) return fail(ctx, SPFOM_ENOTSUP, "precision 32: attraction at %lld outside binary32's normal range", pos);
+      return fail(ctx, SPFOM_ENOTSUP, "precision 32: lambda or v0 of segment %lld outside binary32's range",
+                  pos - nnz);
     }
   }
   cudaError_t e = spfom::launch_prep(P, d_w, d_v0, d_vt, d_vt0, ctx->stream);

@@ -306,12 +306,18 @@ struct RunConfig {
 };
 
 // Launchers (spfom_kernels.cu). Each returns the launch status.
-// Per-nonzero checks of a loaded instance (spfom_load_instance): keys[0] = the
-// smallest (position << 3 | code) over failed checks, keys[1] the same over
-// binary32-range failures when f32; ~0 when none failed.
-enum ItemCheck { kBadId = 1, kRepeated = 2, kBadV = 3, kBadW = 4, kBadF32 = 5 };
-cudaError_t launch_validate_items(const Problem& P, const double* w, bool f32, unsigned long long* keys,
-                                  cudaStream_t s);
+// Device checks of a loaded instance (spfom_load_instance), one thread per
+// segment. keys[0] = the smallest (l << kCheckSegShift | sub) over failed
+// checks, sub = kSegOrder (offsets decrease), kSegLam, kSegV0, or
+// kSegItems + 8 (p - seg_ptr[l]) + ItemCheck for the nonzero p: the order of
+// a host loop over segments and their nonzeros. keys[1] (f32 only) = the
+// smallest binary32-range failure: p for an attraction, nnz + l for lambda or
+// v0 of segment l. keys[2] = the largest set. ~0 when none failed.
+enum ItemCheck { kBadId = 1, kRepeated = 2, kBadV = 3, kBadW = 4 };
+enum SegCheck { kSegOrder = 0, kSegLam = 1, kSegV0 = 2, kSegItems = 3 };
+constexpr int kCheckSegShift = 36;
+cudaError_t launch_validate_items(const Problem& P, const double* w, const double* v0, bool f32,
+                                  unsigned long long* keys, cudaStream_t s);
 cudaError_t launch_prep(const Problem& P, const double* w, const double* v0, double* vt, double* vt0,
                         cudaStream_t s);
 // seg_begin / seg_end (may be null) are recorded around the segment kernel.

@@ -452,15 +452,37 @@ int vec_grid(const Problem& P) {
 
 namespace {
 
-// One thread per segment, its nonzeros in order: id in range, not repeated
-// earlier in the segment, v finite and > 0, w in [0, v]; with f32, v and v - w
-// normal binary32 numbers (v - w may be 0). Sets of <= 32 products (checked on
-// the host before the launch).
-__global__ void k_validate_items(const Problem P, const double* __restrict__ w, int f32,
-                                 unsigned long long* __restrict__ keys) {
+// One thread per segment: its offsets, lambda, v0, then its nonzeros in
+// order (id in range, not repeated earlier in the segment, v finite and > 0,
+// w in [0, v]); with f32, v and v - w (and lambda, v0) normal binary32 numbers
+// (v - w and lambda may be 0). The first failure of a segment ends its checks.
+// Nonzeros are read only inside [0, nnz) and only for the first 32 of a set.
+__device__ __forceinline__ bool in_f32(double x, bool zero_ok) {
+  return (zero_ok && x == 0.0) || (x >= 1.1754943508222875e-38 && x <= 3.4028234663852886e+38);
+}
+
+__global__ void k_validate_items(const Problem P, const double* __restrict__ w, const double* __restrict__ v0,
+                                 int f32, unsigned long long* __restrict__ keys) {
   for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < P.L;
        l += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long seg = (unsigned long long)l << kCheckSegShift;
     const long long b = P.seg_ptr[l], e = P.seg_ptr[l + 1];
+    if (e < b) {
+      atomicMin(keys, seg | kSegOrder);
+      continue;
+    }
+    if (b < 0 || e > P.nnz) continue;  // a decrease elsewhere reports it
+    atomicMax(keys + 2, (unsigned long long)(e - b));
+    const double lam = P.lam[l], v0l = v0[l];
+    if (!(lam >= 0.0 && isfinite(lam))) {
+      atomicMin(keys, seg | kSegLam);
+      continue;
+    }
+    if (!(v0l > 0.0 && isfinite(v0l))) {
+      atomicMin(keys, seg | kSegV0);
+      continue;
+    }
+    if (f32 && (!in_f32(lam, true) || !in_f32(v0l, false))) atomicMin(keys + 1, (unsigned long long)(P.nnz + l));
     for (long long p = b; p < e && p < b + 32; ++p) {
       const int j = P.seg_prod[p];
       int code = 0;
@@ -475,27 +497,25 @@ __global__ void k_validate_items(const Problem P, const double* __restrict__ w, 
       const double wp = w ? w[p] : 0.0;
       if (!code && w && !(wp >= 0.0 && wp <= v)) code = kBadW;
       if (code) {
-        atomicMin(keys, ((unsigned long long)p << 3) | (unsigned)code);
-        break;  // later nonzeros of this segment sort after this one
+        atomicMin(keys, seg | (unsigned long long)(kSegItems + 8 * (p - b) + code));
+        break;
       }
-      if (f32) {
-        const double vt = w ? __dsub_rn(v, wp) : v;
-        const bool ok_v = v >= 1.1754943508222875e-38 && v <= 3.4028234663852886e+38;
-        const bool ok_t = vt == 0.0 || (vt >= 1.1754943508222875e-38 && vt <= 3.4028234663852886e+38);
-        if (!ok_v || !ok_t) atomicMin(keys + 1, ((unsigned long long)p << 3) | (unsigned)kBadF32);
-      }
+      if (f32 && (!in_f32(v, false) || !in_f32(w ? __dsub_rn(v, wp) : v, true)))
+        atomicMin(keys + 1, (unsigned long long)p);
     }
   }
 }
 
 }  // namespace
 
-cudaError_t launch_validate_items(const Problem& P, const double* w, bool f32, unsigned long long* keys,
-                                  cudaStream_t s) {
+cudaError_t launch_validate_items(const Problem& P, const double* w, const double* v0, bool f32,
+                                  unsigned long long* keys, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(keys, 0xff, 2 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(keys + 2, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess || P.L <= 0) return e;
   const long long blocks = (P.L + 255) / 256;
-  k_validate_items<<<(unsigned)(blocks < 65535ll * 16 ? blocks : 65535ll * 16), 256, 0, s>>>(P, w, f32 ? 1 : 0, keys);
+  k_validate_items<<<(unsigned)(blocks < 65535ll * 16 ? blocks : 65535ll * 16), 256, 0, s>>>(P, w, v0, f32 ? 1 : 0,
+                                                                                               keys);
   return cudaGetLastError();
 }
 

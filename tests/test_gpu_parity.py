@@ -303,6 +303,30 @@ def test_first_failing_nonzero_is_reported():
     assert ei.value.status == 1 and "seg_prod[2]" in str(ei.value)
 
 
+def test_segment_checks_run_in_segment_order():
+    """Offsets, lambda and v0 are checked on the device too; the message names
+    the first failure of a host loop over segments (a segment's own checks
+    before its nonzeros, earlier segments first)."""
+    from paper_2602_22421_gb300 import SpfomError
+
+    def lam_then_item(I):
+        I.lam = I.lam.copy()
+        I.lam[6] = -1.0                  # segment 6
+        I.v[6 * 4 + 1] = -2.0            # a nonzero of segment 6: reported after its lambda
+        I.seg_prod[30 * 4] = -1          # a later segment
+    with pytest.raises(SpfomError) as ei:
+        Solver(_bad(lam_then_item))
+    assert ei.value.status == 1 and "lam[6]" in str(ei.value)
+
+    def order(I):
+        I.seg_ptr = I.seg_ptr.copy()
+        I.seg_ptr[12] = I.seg_ptr[11] - 1  # segment 11 ends before it starts
+        I.v0[20] = 0.0
+    with pytest.raises(SpfomError) as ei:
+        Solver(_bad(order))
+    assert ei.value.status == 1 and "not monotone at 11" in str(ei.value)
+
+
 def test_binary32_range_is_checked_for_precision_32():
     """Precision 32 keeps binary32 images of v and v - w: an attraction below
     binary32's normal range is unsupported there (ENOTSUP) and fine in
