@@ -190,10 +190,12 @@ spfom_status spfom_create(const spfom_params* p, spfom_ctx** out);
  * sizes < 0, non-finite r, c < 0, v <= 0, w < 0 or w > v, v0 <= 0, lam < 0,
  * a_val <= 0, ids out of range, a product repeated in a segment or a resource
  * repeated in a product, non-monotone offsets. ENOTSUP: a consideration set
- * larger than 32 products. The checks of the sizes, offsets and per-segment
- * values run on the host before anything is released; the per-nonzero checks
- * (ids, repeats, v, w, and binary32 range for precision 32) run on the device
- * after the upload, so a load that fails them leaves the ctx with no instance.
+ * larger than 32 products. The checks of the sizes and of the product ×
+ * resource incidence run on the host before anything is released; those of
+ * the segment offsets, lambda, v0 and the nonzeros (ids, repeats, v, w, and
+ * binary32 range for precision 32) run on the device after the upload, so a
+ * load that fails them leaves the ctx with no instance. Either way the message
+ * names the first failure of a loop over segments in order.
  * The host arrays are not kept. */
 spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* inst);
 
