@@ -559,8 +559,13 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   W.fast = false;
   W.zparts_iter = W.zparts_eval = W.seg_blocks;
   {
-    double mass = 0.0;
-    for (long long l = 0; l < L; ++l) mass += I->lam[l];
+    // only the exponent of the arrival mass matters: four interleaved sums
+    double m4[4] = {0.0, 0.0, 0.0, 0.0};
+    long long l = 0;
+    for (; l + 3 < L; l += 4)
+      for (int k = 0; k < 4; ++k) m4[k] += I->lam[l + k];
+    for (; l < L; ++l) m4[0] += I->lam[l];
+    const double mass = (m4[0] + m4[1]) + (m4[2] + m4[3]);
     int e2 = 0;
     std::frexp(mass > 1.0 ? mass : 1.0, &e2);  // mass < 2^e2
     const int F = 61 - e2;
