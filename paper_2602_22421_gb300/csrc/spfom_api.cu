@@ -522,9 +522,16 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       return fail(ctx, SPFOM_EINVAL, "w[%lld] must lie in [0, v]", p);
     }
     kmax = (int)keys[2];
-    if (kmax > 32) {
+    if (kmax > spfom::kFastMaxSet) {
       free_instance(ctx);
-      return fail(ctx, SPFOM_ENOTSUP, "consideration set of %d products (at most 32 supported)", kmax);
+      return fail(ctx, SPFOM_ENOTSUP, "consideration set of %d products (at most %d supported)", kmax,
+                  spfom::kFastMaxSet);
+    }
+    if (kmax > 32 && (ctx->p.path != 0 || ctx->p.track_xbar || ctx->p.batch_frac < 1.0 || ctx->loading_batch)) {
+      free_instance(ctx);
+      return fail(ctx, SPFOM_ENOTSUP,
+                  "consideration set of %d products: sets of more than 32 need the certified-decision path "
+                  "(path 0, batch_frac 1, a single instance, no track_xbar)", kmax);
     }
     if (keys[1] != ~0ull) {  // precision 32: attractions first (in nonzero order), then the segments
       const long long pos = (long long)keys[1];
@@ -639,7 +646,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
         bool ok = t <= 8;
         if (ok && ctx->p.precision == 32) {
           ok = (t != 2 || W.plan.tma_ok) && (t != 4 || W.plan.coop_ok) && (t != 6 || W.plan.bchunk_ok) &&
-               (t != 7 || W.plan.ms_ok) && (t != 8 || W.plan.sl_ok);
+               (t != 7 || W.plan.ms_ok) && (t != 8 || W.plan.sl_ok) && (t != 5 || kmax <= 32);
           W.plan.bchunk = t == 6 ? 1 : 0;
           W.plan.tma = t == 2 ? 1 : 0;
           W.plan.f32_p8 = t == 3 ? 1 : 0;
@@ -677,6 +684,10 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       SPFOM_TRY(dalloc(ctx, &W.seg4, (size_t)(L > 0 ? L : 1)));
       SPFOM_TRY(dalloc(ctx, &W.marg2, (size_t)(n > 0 ? n : 1)));
       SPFOM_TRY(dalloc(ctx, &W.marg2_eval, (size_t)(n > 0 ? n : 1)));
+    }
+    if (kmax > 32 && !W.fast) {
+      free_instance(ctx);
+      return fail(ctx, SPFOM_ENOTSUP, "sets of more than 32 products need the certified-decision kernel");
     }
     if (ctx->p.precision == 32) {
       if (!W.fast) {
@@ -1029,6 +1040,7 @@ spfom_status spfom_duals(spfom_ctx* ctx, int32_t averaged, double* y_out) {
 spfom_status spfom_evaluate(spfom_ctx* ctx, const double* y, double* z_out, double* dual_out) {
   if (!ctx || !y) return SPFOM_EINVAL;
   if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
+  if (ctx->W.W > 32) return fail(ctx, SPFOM_ENOTSUP, "spfom_evaluate needs sets of <= 32 products (the sorting kernel)");
   const Problem& P = ctx->P;
   for (int i = 0; i < P.m; ++i)
     if (!(y[i] >= 0.0) || !is_finite(y[i])) return fail(ctx, SPFOM_EINVAL, "y[%d] must be finite and >= 0", i);
@@ -1214,6 +1226,7 @@ spfom_status spfom_update(spfom_ctx* ctx, const double* c, const double* lam) {
 spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out) {
   if (!ctx || !y || !s_out) return SPFOM_EINVAL;
   if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
+  if (ctx->W.W > 32) return fail(ctx, SPFOM_ENOTSUP, "spfom_sales_at needs sets of <= 32 products (the sorting kernel)");
   const Problem& P = ctx->P;
   for (int i = 0; i < P.m; ++i)
     if (!(y[i] >= 0.0) || !is_finite(y[i])) return fail(ctx, SPFOM_EINVAL, "y[%d] must be finite and >= 0", i);
@@ -1256,6 +1269,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
     if (f32 && c == 8) return ctx->W.sl.nchunks > 0;
     if (f64) return c == 1 || (c == 2 && plan.ms_ok != 0) || (c == 3 && ctx->W.sl.nchunks > 0);
     if (f32 && c == 6) return plan.bchunk_ok != 0 && ctx->W.batch && ctx->W.bc_count > 0;
+    if (f32 && c == 5) return ctx->W.W <= 32;  // 16 products per lane and at most two lanes
     if (f32) return c == 4 ? (plan.coop_ok != 0 && !ctx->W.batch) : (c != 2 || (plan.tma_ok && !ctx->W.batch));
     return c <= 3 && dd && spfom::dd_variant_ok(plan, c);
   };
@@ -1375,6 +1389,7 @@ spfom_status features_into(spfom_ctx* ctx, const WarmScratch& w, float* feat) {
 extern "C" spfom_status spfom_features(spfom_ctx* ctx, float* features) {
   if (!ctx || !features) return SPFOM_EINVAL;
   if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
+  if (ctx->W.W > 32) return fail(ctx, SPFOM_ENOTSUP, "spfom_features needs sets of <= 32 products (the sorting kernel)");
   if (ctx->W.batch) return fail(ctx, SPFOM_ENOTSUP, "features are per instance; load a single instance");
   SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
   WarmScratch w{};
@@ -1389,6 +1404,7 @@ extern "C" spfom_status spfom_solve_warm(spfom_ctx* ctx, spfom_mlp* net, int64_t
                                          int32_t* mode_out) {
   if (!ctx || !net) return SPFOM_EINVAL;
   if (!ctx->loaded) return fail(ctx, SPFOM_ESTATE, "no instance loaded");
+  if (ctx->W.W > 32) return fail(ctx, SPFOM_ENOTSUP, "spfom_solve_warm needs sets of <= 32 products (the sorting kernel)");
   if (ctx->W.batch) return fail(ctx, SPFOM_ENOTSUP, "the warm start is per instance; load a single instance");
   const auto t0 = std::chrono::steady_clock::now();
   SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));

@@ -72,6 +72,10 @@ struct Problem {
 };
 
 constexpr int kFastThreads = 512;
+// Largest consideration set of the certified-decision path: 16 lanes x 8 slots
+// (binary64), 32 lanes x 4 slots (binary32 tiling 1); the other paths and
+// kernels (sorting kernel, double-float, staged, batched) take sets of <= 32.
+constexpr int kFastMaxSet = 128;
 constexpr int kFastMaxSmem = 200 * 1024;
 constexpr int kTmaThreads = 1024;
 constexpr int kMsThreads = 1024;  // block of the margins-in-shared segment kernels (one per SM)

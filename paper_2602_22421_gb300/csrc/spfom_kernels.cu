@@ -456,7 +456,8 @@ namespace {
 // order (id in range, not repeated earlier in the segment, v finite and > 0,
 // w in [0, v]); with f32, v and v - w (and lambda, v0) normal binary32 numbers
 // (v - w and lambda may be 0). The first failure of a segment ends its checks.
-// Nonzeros are read only inside [0, nnz) and only for the first 32 of a set.
+// Nonzeros are read only inside [0, nnz) and only for the first kFastMaxSet of
+// a set (a larger set is rejected by its size).
 __device__ __forceinline__ bool in_f32(double x, bool zero_ok) {
   return (zero_ok && x == 0.0) || (x >= 1.1754943508222875e-38 && x <= 3.4028234663852886e+38);
 }
@@ -472,7 +473,7 @@ __global__ void k_validate_items(const Problem P, const double* __restrict__ w, 
       continue;
     }
     if (b < 0 || e > P.nnz) continue;  // a decrease elsewhere reports it
-    atomicMax(keys + 2, (unsigned long long)(e - b));
+    atomicMax(keys + 2, (unsigned long long)(e - b));  // the largest set
     const double lam = P.lam[l], v0l = v0[l];
     if (!(lam >= 0.0 && isfinite(lam))) {
       atomicMin(keys, seg | kSegLam);
@@ -483,7 +484,7 @@ __global__ void k_validate_items(const Problem P, const double* __restrict__ w, 
       continue;
     }
     if (f32 && (!in_f32(lam, true) || !in_f32(v0l, false))) atomicMin(keys + 1, (unsigned long long)(P.nnz + l));
-    for (long long p = b; p < e && p < b + 32; ++p) {
+    for (long long p = b; p < e && p < b + kFastMaxSet; ++p) {
       const int j = P.seg_prod[p];
       int code = 0;
       if (j < 0 || j >= P.n) {

@@ -21,8 +21,9 @@
 // (the margins move little between iterations). The decision is certified when
 // every candidate clears the threshold by a relative margin
 // |a_j - R b_j| > 2^-16 (a_j + R b_j); the binary32 rounding of a_j, b_j, N, D
-// and R is below 5e-6 relative for consideration sets of up to 32 products,
-// so a certified set is the exact-arithmetic optimum S*. Segments that are not
+// and R stays below 5e-6 relative (each sum is a lane's sum of at most 8 slots
+// and a shuffle tree of at most 4 levels: depth <= 11 for sets of up to 128
+// products), so a certified set is the exact-arithmetic optimum S*. Segments that are not
 // certified (a near-tie, or an input outside binary32's normal range) repeat
 // the iteration in binary64.
 //
@@ -742,6 +743,8 @@ cudaError_t launch_fast_wz(const FastArgs& A, int W, int grid, int smem, cudaStr
     case 1: k_seg_fast<1, 8, SC, 0, 0, ZV><<<grid, kFastThreads, smem, s>>>(A); break;
     case 2: k_seg_fast<2, 8, SC, 0, 0, ZV><<<grid, kFastThreads, smem, s>>>(A); break;
     case 4: k_seg_fast<4, 8, SC, 0, 0, ZV><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 8: k_seg_fast<8, 8, SC, 0, 0, ZV><<<grid, kFastThreads, smem, s>>>(A); break;    // sets of 33..64
+    case 16: k_seg_fast<16, 8, SC, 0, 0, ZV><<<grid, kFastThreads, smem, s>>>(A); break;  // sets of 65..128
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -766,6 +769,8 @@ cudaError_t launch_f32_w(const F32Args& A0, int W, int grid, int smem, cudaStrea
     case 2: k_seg_f32<2, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     case 4: k_seg_f32<4, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     case 8: k_seg_f32<8, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 16: k_seg_f32<16, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 32: k_seg_f32<32, 4, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -791,6 +796,8 @@ cudaError_t launch_f32_p8(const F32Args& A0, int W8, int grid, int smem, cudaStr
     case 1: k_seg_f32<1, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     case 2: k_seg_f32<2, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     case 4: k_seg_f32<4, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 8: k_seg_f32<8, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
+    case 16: k_seg_f32<16, 8, SC><<<grid, kFastThreads, smem, s>>>(A); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -935,9 +942,13 @@ int occupancy(int W, int sc, int smem, bool f32) {
   SPFOM_OCC32(2)
   SPFOM_OCC32(4)
   SPFOM_OCC32(8)
+  SPFOM_OCC32(16)
+  SPFOM_OCC32(32)
   SPFOM_OCC64(1)
   SPFOM_OCC64(2)
   SPFOM_OCC64(4)
+  SPFOM_OCC64(8)
+  SPFOM_OCC64(16)
 #undef SPFOM_OCC32
 #undef SPFOM_OCC64
   return 0;
@@ -946,7 +957,7 @@ int occupancy(int W, int sc, int smem, bool f32) {
 }  // namespace
 
 bool fast_plan(int n, int kmax, int sms, FastPlan* plan) {
-  if (kmax > 32) return false;
+  if (kmax > kFastMaxSet) return false;
   int W = 1, W8 = 1;
   while (W * 4 < kmax) W <<= 1;
   while (W8 * 8 < kmax) W8 <<= 1;
@@ -960,6 +971,8 @@ bool fast_plan(int n, int kmax, int sms, FastPlan* plan) {
     cudaFuncSetAttribute(k_seg_f32<1, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_seg_f32<2, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_seg_f32<4, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_seg_f32<8, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaFuncSetAttribute(k_seg_f32<16, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_seg_f32<1, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     cudaFuncSetAttribute(k_seg_f32<2, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   }

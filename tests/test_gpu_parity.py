@@ -341,11 +341,70 @@ def test_binary32_range_is_checked_for_precision_32():
 
 
 def test_large_consideration_set_is_unsupported():
+    """Sets of more than 128 products are rejected; sets of 33..128 need the
+    certified-decision path (the sorting kernel takes at most 32)."""
     from paper_2602_22421_gb300 import SpfomError
-    inst = make_instance(n=40, m=5, L=10, kmin=33, kmax=33, seed=3)
     with pytest.raises(SpfomError) as ei:
-        Solver(inst)
+        Solver(make_instance(n=200, m=5, L=10, kmin=129, kmax=129, seed=3))
+    assert ei.value.status == 7 and "at most 128" in str(ei.value)
+    wide_sets = make_instance(n=60, m=5, L=10, kmin=33, kmax=40, seed=3)
+    with pytest.raises(SpfomError) as ei:
+        Solver(wide_sets, path=1)
     assert ei.value.status == 7
+    with Solver(wide_sets) as s:
+        assert s.step(2)["iters"] == 2
+        with pytest.raises(SpfomError) as ei:
+            s.sales_at(np.zeros(5))
+        assert ei.value.status == 7
+
+
+def paper_shaped_small():
+    """The paper's speedup-study shape (Section 4.5): every segment considers
+    all 100 products, MNL, one resource per product, at 2000 segments."""
+    from instances import paper_shaped
+    return paper_shaped(3, L=2000, n=100)
+
+
+def wide_sets_gam():
+    """GAM instance with sets of 60..100 of 120 products."""
+    return make_instance(n=120, m=60, L=3000, kmin=60, kmax=100, gam=True, tightness=0.6, seed=3, name="wide_sets")
+
+
+@pytest.mark.parametrize("make", [paper_shaped_small, wide_sets_gam], ids=["paper_shaped_mnl", "gam_60_100"])
+def test_sets_of_100_products_track_oracle(make):
+    """Sets of up to 100 products (16 lanes x 8 slots per segment): the
+    binary64 iterates track the oracle as for small sets."""
+    inst = make()
+    o = Oracle(inst)
+    run = o.run(OracleParams())
+    done = 0
+    with Solver(inst) as s:
+        assert s.stats()["fast_path"] == 1
+        for t in (1, 2, 63, 64, 65, 200):
+            while done < t:
+                run.step(1)
+                done += 1
+            st = s.step(t - st_iters(s))
+            ost = run.stats()
+            assert st["iters"] == ost["t"] == t and st["restarts"] == ost["restarts"]
+            assert nrel(s.duals(), run.y) <= ITER_RTOL, (t, nrel(s.duals(), run.y))
+            assert nrel(s.vector(5), run.s) <= ITER_RTOL
+            assert st["z_sum"] == pytest.approx(ost["z_sum"], rel=ITER_RTOL)
+            if ost["evals"]:
+                assert st["kkt"] == pytest.approx(ost["kkt"], rel=1e-5, abs=1e-12)
+
+
+def test_sets_of_100_products_binary32_solve():
+    """The binary32 bulk mode (32 lanes x 4 slots, or 16 x 8) on sets of up
+    to 100 products solves to KKT <= 1e-4 at the binary64 solve's objective."""
+    inst = wide_sets_gam()
+    with Solver(inst) as s:
+        ref = s.solve()
+    with Solver(inst, precision=32) as s:
+        assert s.autotune(8) in (1, 3)
+        st = s.solve()
+    assert ref["converged"] == 1 and st["converged"] == 1 and st["kkt"] <= 1e-4
+    assert st["dual_avg"] == pytest.approx(ref["dual_avg"], rel=1e-4)
 
 
 # -- binary32 bulk mode (precision 32) --------------------------------------
