@@ -65,6 +65,8 @@ def parse():
                     help="instances of the batched family re-solved one at a time for the plain reference "
                          "(0 = all)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm start")
+    ap.add_argument("--no-paper-shaped", action="store_true",
+                    help="skip the instance of the paper's speedup-study shape (sets of all 100 products)")
     ap.add_argument("--learned-test", type=int, default=32)
     return ap.parse_args()
 
@@ -388,7 +390,8 @@ def run_gpu(args):
         cpu = cpu_baseline(inst, args.cpu_seconds)
     legs = {}
     if rank == 0:
-        for name, skip, fn in (("huge", args.no_huge, lambda: huge_leg(args, stream, local)),
+        for name, skip, fn in (("paper_shaped", args.no_paper_shaped, lambda: paper_shaped_leg(args, stream, local)),
+                               ("huge", args.no_huge, lambda: huge_leg(args, stream, local)),
                                ("batched", args.no_batched, lambda: batched_leg(args, local)),
                                ("learned", args.no_learned, lambda: learned_leg(args, local))):
             if skip:
@@ -430,6 +433,40 @@ def roofline_of(s_prof, inst, precision, ips, steps):
             "frac": achieved / peak, "algorithmic_bytes_per_launch": alg, "launch_ms": per_launch * 1e3,
             "peak_source": f"{src} hbm_gbs", "traffic": None,
             "binary64_redo_fraction": pst["fallback_segments"] / (steps * ips * inst.L)}
+
+
+def paper_shaped_leg(args, stream, local):
+    """The shape of the paper's speedup study (Section 4.5): n = m = 100, one
+    resource per product, every segment considers all 100 products, MNL,
+    c, r, v ~ U(0,1), lambda = 1, here with 1e5 segments (1e7 nonzeros):
+    iterations/s and the segment kernel's roofline in both precisions."""
+    import torch
+    from instances import paper_shaped
+    from paper_2602_22421_gb300 import Solver
+    inst = paper_shaped(3, L=100_000, n=100)
+    out = {"workload": f"paper-shaped: n=m={inst.n}, A=I, L={inst.L}, |C_l|={inst.n} (all products), MNL, "
+                       "c, r, v ~ U(0,1), lambda = 1", "nnz": inst.nnz}
+    ips = args.iters_per_step
+    for precision in (64, 32):
+        s = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, precision=precision)
+        tiling = s.autotune(16)
+        s.step(2 * ips)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(4 * ips)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        s.close()
+        sp = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, profile=1, precision=precision,
+                    tiling=tiling)
+        sp.step(ips)
+        roof = roofline_of(sp, inst, precision, ips, 2)
+        sp.close()
+        out[f"f{precision}"] = {"value": 4 * ips / (ms * 1e-3), "unit": "iters/s", "tiling": tiling,
+                                "ms_per_iter": ms / (4 * ips), "roofline": roof}
+    return out
 
 
 def huge_leg(args, stream, local):

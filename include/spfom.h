@@ -190,7 +190,10 @@ spfom_status spfom_create(const spfom_params* p, spfom_ctx** out);
  * sizes < 0, non-finite r, c < 0, v <= 0, w < 0 or w > v, v0 <= 0, lam < 0,
  * a_val <= 0, ids out of range, a product repeated in a segment or a resource
  * repeated in a product, non-monotone offsets. ENOTSUP: a consideration set
- * larger than 32 products. The checks of the sizes and of the product ×
+ * larger than 128 products, or larger than 32 unless the ctx runs the
+ * certified-decision path (path 0, batch_frac 1, no track_xbar); with such
+ * sets spfom_sales_at, spfom_evaluate, spfom_recover and the warm-start calls
+ * return ENOTSUP. The checks of the sizes and of the product ×
  * resource incidence run on the host before anything is released; those of
  * the segment offsets, lambda, v0 and the nonzeros (ids, repeats, v, w, and
  * binary32 range for precision 32) run on the device after the upload, so a
