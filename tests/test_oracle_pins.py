@@ -148,7 +148,8 @@ def test_sblp_equals_cblp_and_strong_duality(make):
 def test_consumption_is_dual_gradient(make):
     """The dual function is piecewise linear with gradient c - A s(y)
     (Danskin); finite differences of Dual recover g, and the Lagrangian
-    identity sum_l z_l = P - y^T g holds."""
+    identity sum_l z_l = P - y^T g holds, i.e. sum_l z_l = sum_j m_j s_j (the
+    form in which the GPU's dual step takes the iteration's sum of z)."""
     inst = make()
     o = Oracle(inst)
     A = dense_A(inst)
@@ -157,6 +158,7 @@ def test_consumption_is_dual_gradient(make):
         np.testing.assert_allclose(sw["g"], A @ sw["s"], rtol=1e-12, atol=1e-12)
         assert sw["P"] == pytest.approx(float(inst.r @ sw["s"]), rel=1e-12)
         assert sw["zsum"] == pytest.approx(sw["P"] - float(y @ sw["g"]), rel=1e-10, abs=1e-9)
+        assert sw["zsum"] == pytest.approx(float(o.margins(y) @ sw["s"]), rel=1e-10, abs=1e-9)
         D0 = o.dual(y)
         h = 1e-6 * max(1.0, float(np.mean(y)))
         for i in range(inst.m):
