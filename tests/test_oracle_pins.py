@@ -288,3 +288,39 @@ def test_sampled_run_keeps_stale_responses():
     np.testing.assert_allclose(run.s, s, rtol=1e-12, atol=1e-12)
     np.testing.assert_allclose(run.g, dense_A(inst) @ s, rtol=1e-12, atol=1e-12)
     assert K.min() >= 3
+
+
+# -- checker: every workload shape --------------------------------------------
+def _wide_sets():
+    return make_instance(n=60, m=10, L=200, kmin=33, kmax=40, gam=True, tightness=0.6, seed=8, name="wide_sets")
+
+
+def _paper_shaped_small():
+    from instances import paper_shaped
+    return paper_shaped(3, L=100, n=100)
+
+
+@pytest.mark.parametrize("make", [tiny_mnl, small_gam, lambda: with_zero_vt(small_gam()), _wide_sets,
+                                  _paper_shaped_small],
+                         ids=["tiny_mnl", "small_gam", "zero_vt", "wide_sets", "paper_shaped"])
+def test_checker_holds_along_the_run(make):
+    """Along a run on every workload shape: the duals and their averages stay
+    >= 0, and the Lagrangian bound holds at the epoch average, since the
+    averaged response is a convex combination of assortment points:
+    Dual(y) >= Pbar + y^T (c - gbar) for every y >= 0 (weak duality)."""
+    inst = make()
+    o = Oracle(inst)
+    run = o.run(Params())
+    ys = dual_points(inst, 3)
+    done = 0
+    for t in (1, 10, 64, 130, 200):
+        run.step(t - done)
+        done = t
+        st = run.stats()
+        assert (run.y >= 0).all() and (run.ybar >= 0).all()
+        if st["count"] == 0:
+            continue
+        pbar = st["sum_P"] / st["count"]
+        for y in ys + [run.y, run.ybar]:
+            d = o.dual(y)
+            assert d >= pbar + float(y @ (inst.c - run.gbar)) - 1e-9 * (1.0 + abs(d)), (t, d)
