@@ -90,6 +90,8 @@ def lib(omp: bool = False):
         h.orc_state_init.argtypes = [P(_Inst), P(_Params), P(_State)]
         h.orc_run.argtypes = [P(_Inst), P(_Params), P(_State), C.c_int64]
         h.orc_run.restype = C.c_int
+        h.orc_evaluate.argtypes = [P(_Inst), P(_Params), P(_State)]
+        h.orc_evaluate.restype = None
         h.orc_recover.argtypes = [P(_Inst), _f64p, _f64p, _i32p]
         h.orc_recover.restype = None
         _libs[omp] = h
@@ -112,7 +114,7 @@ class Params:
     restart_beta: float = 0.2
     restart_artificial: float = 0.36
     restart_tau_decay: float = 1.0
-    restart_tau_balance: float = 0.0
+    restart_tau_balance: float = 0.5
     kkt_tol: float = 1e-4
 
     def _c(self) -> _Params:
@@ -227,6 +229,20 @@ class OracleRun:
         if rc != 0:
             raise RuntimeError("oracle run failed")
         return self.stats()
+
+    def evaluate(self) -> dict:
+        """One KKT evaluation and restart test on the current epoch sums (what
+        ``step`` runs every ``eval_every`` iterations); returns the stats."""
+        self.orc._lib.orc_evaluate(C.byref(self.orc._c), C.byref(self._pc), C.byref(self._st))
+        return self.stats()
+
+    def set_state(self, **kw) -> None:
+        """Overwrite scalar fields of the run state (sum_P, count, t, mu_cur,
+        tau_used, kkt_anchor, ...); the arrays are the numpy views above."""
+        for k, v in kw.items():
+            if k in ("y", "sum_y", "sum_g", "s", "g", "x_cur", "sum_x") or not hasattr(self._st, k):
+                raise KeyError(k)
+            setattr(self._st, k, v)
 
     def stats(self) -> dict:
         st = self._st

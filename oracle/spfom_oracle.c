@@ -34,8 +34,12 @@
  *       golden-section tolerance shrinks (Lemma 1);
  *   orc_run dual step + averaging     -- convergence to the LP optimum on tiny
  *       instances; y >= 0; y stays 0 when capacities do not bind;
- *   orc_run KKT residual and restart  -- parity unpinned beyond the
- *       convergence test: the paper defines neither.
+ *   orc_evaluate (KKT residual and restart rules; the paper defines neither,
+ *       so the definition below is the solver's own) -- pinned by a
+ *       hand-worked three-segment instance whose dual function is known in
+ *       closed form: the residuals, the objective pair, every restart
+ *       trigger (progress, epoch length at its boundary), the mu halving, the
+ *       tau decay and both bounds of the tau-balance clamp.
  *   orc_recover (Lemma recover, Section 4.4) -- the recovered assortment
  *       probabilities reproduce the sales through the closed-form choice
  *       probabilities, sum to one, and turn the SBLP optimum (HiGHS) into a
@@ -399,7 +403,7 @@ void orc_state_init(const orc_instance* I, const orc_params* P, orc_state* S) {
  * multiplied by restart_tau_decay (a restarted subgradient schedule); a restart
  * forced by the epoch length (no progress) also multiplies tau by
  * clamp(sqrt(pinf / gap), b, 1 / b) when restart_tau_balance = b > 0. */
-static void evaluate(const orc_instance* I, const orc_params* P, orc_state* S) {
+void orc_evaluate(const orc_instance* I, const orc_params* P, orc_state* S) {
   int32_t m = I->m;
   double* ybar = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
   double cnt = (double)S->count;
@@ -539,7 +543,7 @@ int orc_run(const orc_instance* I, const orc_params* P, orc_state* S, int64_t it
     S->sum_P += Pv;
     S->count += 1;
     S->t = t;
-    if (P->eval_every > 0 && t % P->eval_every == 0) evaluate(I, P, S);
+    if (P->eval_every > 0 && t % P->eval_every == 0) orc_evaluate(I, P, S);
   }
   free(marg);
   free(yprev);
