@@ -69,8 +69,8 @@ typedef struct {
   double restart_beta;       /* 0.2: restart when KKT <= beta * KKT at the last restart */
   double restart_artificial; /* 0.36: or when the epoch holds this fraction of all iterations */
   double restart_tau_decay;  /* 1.0: tau <- tau * decay at each restart */
-  double restart_tau_balance;/* 0 (default): off. b in (0, 1]: at a restart forced by the epoch-
-                                length rule (the KKT did not drop by restart_beta), also
+  double restart_tau_balance;/* 0.5 (default); 0: off. b in (0, 1]: at a restart forced by the
+                                epoch-length rule (the KKT did not drop by restart_beta), also
                                 tau <- tau * clamp(sqrt(pinf / gap), b, 1 / b): a constant step
                                 leaves an O(tau) duality gap on instances with few segments, and
                                 this balances the gap against the infeasibility (solver addition) */
@@ -342,9 +342,10 @@ const char* spfom_status_string(spfom_status s);
  * allocates nothing: its scratch is a set of fixed arrays inside the library
  * (SPFOM_NOALLOC_MAX_PRODUCTS doubles of sales plus 8 KiB), which every GPU
  * that loads the library keeps until the process exits.
- *  - The first call on a device (with that device current) looks up the
- *    scratch arrays' device addresses; make that first call before capturing
- *    any CUDA stream on that device.
+ *  - The first call in a CUDA context (per device and context, with that
+ *    context current; a context made after cudaDeviceReset counts as new)
+ *    looks up the scratch arrays' device addresses with cudaGetSymbolAddress;
+ *    make that first call before capturing any CUDA stream on that device.
  *  - Work is enqueued on `stream` (NULL: the legacy default stream) and the
  *    call returns without waiting for it.
  *  - All calls share the scratch arrays, and each leaves its results there;
@@ -352,8 +353,13 @@ const char* spfom_status_string(spfom_status s);
  *    overlaps on the GPU (other streams, other host threads) race on the
  *    arrays and give wrong results: serialise them.
  *  - Limits: n <= SPFOM_NOALLOC_MAX_PRODUCTS and max_set_size <= 32, else
- *    EINVAL (nothing launched). A segment larger than max_set_size is left
- *    out and *z_sum is set to NaN.
+ *    EINVAL (nothing launched). seg_prod and v may be NULL only when
+ *    max_set_size is 0 (every segment empty). A segment with more than
+ *    max_set_size products is not solved, and then every entry of sales and
+ *    *z_sum is NaN (the results would be incomplete).
+ *  - An error already pending in the calling thread's CUDA state (from
+ *    earlier work) makes the call return ECUDA without launching, and is left
+ *    in place for its owner.
  *  - No input validation beyond sizes: ids must lie in [0, n), v > 0,
  *    0 <= w <= v, v0 > 0, lam >= 0, as for spfom_load_instance.
  * Outputs: sales [n] (device), z_sum [1] (device). ECUDA if the scratch

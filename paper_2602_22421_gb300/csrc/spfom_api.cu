@@ -370,6 +370,7 @@ void spfom_default_params(spfom_params* p) {
   p->restart_beta = 0.2;
   p->restart_artificial = 0.36;
   p->restart_tau_decay = 1.0;
+  p->restart_tau_balance = 0.5;
   p->kkt_tol = 1e-4;
   p->max_iters = 100000;
   p->device = 0;

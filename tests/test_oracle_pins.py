@@ -170,26 +170,35 @@ def test_consumption_is_dual_gradient(make):
 # -- a4..a6: the run --------------------------------------------------------
 def test_run_converges_to_lp_optimum_tiny():
     """Projected dual ascent (Algorithm 2, full batch) with averaging and
-    restarts (step halved at each restart) drives the dual bound at the
-    averaged duals to the HiGHS optimum from above and the KKT residual down.
-    With 40 segments the dual is very non-smooth, so the averaged primal's
-    infeasibility decays slowly; KKT <= 1e-4 is required on the many-segment
-    instance below."""
+    restarts drives the dual bound at the averaged duals to the HiGHS optimum
+    from above and the KKT residual to 1e-4 on the tiny capacitated MNL
+    instance. With 40 segments the dual function is very non-smooth and a
+    constant step leaves an O(tau) duality gap, so this instance's schedule
+    halves the step at every restart (restart_tau_decay = 0.5, a restarted
+    subgradient schedule); it converges at iteration 4544. The default
+    schedule (tau balanced at epoch-length restarts) converges too, later."""
     inst = tiny_mnl(0)
     opt, _ = sblp_highs(inst)
     o = Oracle(inst)
-    run = o.run(Params(eval_every=64, restart_tau_decay=0.5, kkt_tol=1e-4))
-    ys, kkts = [], []
-    for _ in range(60):
+    run = o.run(Params(eval_every=64, restart_tau_decay=0.5, restart_tau_balance=0.0, kkt_tol=1e-4))
+    ys = []
+    for _ in range(80):
         st = run.step(64)
         ys.append(run.y.copy())
-        kkts.append(st["kkt"])
         if st["converged"]:
             break
+    assert st["converged"] == 1 and st["kkt"] <= 1e-4, st
+    assert st["t"] <= 80 * 64
     assert all(np.all(y >= 0) for y in ys)
-    assert st["kkt"] <= 1e-3 and st["kkt"] < kkts[0] / 5
     assert opt * (1 - 1e-12) <= st["dual_avg"] <= opt * (1 + 1e-4)
     assert o.dual(run.ybar) >= opt * (1 - 1e-12)
+    default = o.run(Params())  # restart_tau_balance = 0.5
+    for _ in range(300):
+        st = default.step(64)
+        if st["converged"]:
+            break
+    assert st["converged"] == 1 and st["kkt"] <= 1e-4, st
+    assert opt * (1 - 1e-12) <= st["dual_avg"] <= opt * (1 + 3e-4)
 
 
 @pytest.mark.slow
@@ -216,7 +225,7 @@ def test_balanced_restarts_reach_the_optimum_where_a_constant_step_stalls():
     inst = batch_base(4, 10)
     opt, _ = sblp_highs(inst)
     o = Oracle(inst)
-    const = o.run(Params())
+    const = o.run(Params(restart_tau_balance=0.0))
     for _ in range(60):
         st = const.step(64)
     assert st["converged"] == 0 and st["gap"] > 3 * st["pinf"]
