@@ -33,7 +33,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f != "gb300_probe.cu"] + \
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + \
         [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)] + [__file__]
     return any(os.path.getmtime(d) > t for d in deps)
 
@@ -64,15 +64,6 @@ def build(force: bool = False, verbose: bool = False) -> str:
     subprocess.check_call([exe, *ARCH, "-shared", "-o", tmp, *objs])
     os.replace(tmp, LIB)
     return LIB
-
-
-def build_probe() -> str:
-    """Compile the standalone GB300 throughput microbenchmark (csrc/gb300_probe.cu)
-    into _build/gb300_probe and return its path."""
-    os.makedirs(BUILD, exist_ok=True)
-    out = os.path.join(BUILD, "gb300_probe")
-    subprocess.check_call([nvcc(), *ARCH, "-O3", "-o", out, os.path.join(CSRC, "gb300_probe.cu")])
-    return out
 
 
 if __name__ == "__main__":
