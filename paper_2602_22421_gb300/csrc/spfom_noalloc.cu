@@ -12,8 +12,9 @@
 //   g_sales  SPFOM_NOALLOC_MAX_PRODUCTS binary64 sums (1 MiB),
 //   g_zpart  kMaxBlocks per-block sums of segment values (8 KiB),
 //   g_error  one flag.
-// The address of each array is looked up once per device with
-// cudaGetSymbolAddress, on the first call made with that device current.
+// The address of each array is looked up with cudaGetSymbolAddress on the
+// first call made in a CUDA context (per device and context: a context made
+// after cudaDeviceReset gets its own lookup), with that context current.
 // Every call shares the arrays and leaves them holding its last contents;
 // each call clears what it accumulates before use. Calls whose work overlaps
 // on the GPU (different streams, or different threads on one device) race on
@@ -23,9 +24,11 @@
 // lanes per segment, binary64 throughout, exact sort and prefix scan, with
 // vt = v - w and vt0 = v0 + sum w formed in registers instead of read from
 // the ctx's preprocessed arrays.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "../../include/spfom.h"
@@ -34,7 +37,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kMaxBlocks = 1024;
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_sales[SPFOM_NOALLOC_MAX_PRODUCTS];
 static __device__ __align__(256) double g_zpart[kMaxBlocks];
@@ -46,27 +48,64 @@ struct Scratch {
   int* error;
 };
 
-std::mutex g_setup_mutex;
-bool g_ready[kMaxDevices];
-Scratch g_scratch[kMaxDevices];
+constexpr int kMaxContexts = 64;
 
-// Device addresses of the static arrays on the current device (set up once).
-cudaError_t scratch_for_current_device(Scratch* out) {
+struct ScratchEntry {
+  int device;
+  CUcontext ctx;
+  Scratch s;
+};
+
+std::mutex g_setup_mutex;
+ScratchEntry g_cache[kMaxContexts];
+int g_cached = 0;
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+// cuCtxGetCurrent through the runtime's driver entry-point query (the library
+// does not link the driver library directly).
+CtxGetCurrentFn ctx_get_current() {
+  static std::once_flag once;
+  static CtxGetCurrentFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  });
+  return fn;
+}
+
+// Device addresses of the static arrays in the current context: looked up on
+// the first call in each (device, context) and kept. A symbol's address
+// belongs to one context, so a context created later on the same device (for
+// instance after cudaDeviceReset) gets its own lookup.
+cudaError_t scratch_for_current_context(Scratch* out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get) return cudaErrorDeviceUninitialized;
   std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_ready[dev]) {
-    Scratch s{};
-    e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.sales), g_sales);
-    if (e == cudaSuccess) e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.zpart), g_zpart);
-    if (e == cudaSuccess) e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.error), g_error);
-    if (e != cudaSuccess) return e;
-    g_scratch[dev] = s;
-    g_ready[dev] = true;
-  }
-  *out = g_scratch[dev];
+  CUcontext ctx = nullptr;
+  if (get(&ctx) == CUDA_SUCCESS && ctx)  // no context yet: the lookup below makes the primary one current
+    for (int k = 0; k < g_cached; ++k)
+      if (g_cache[k].device == dev && g_cache[k].ctx == ctx) {
+        *out = g_cache[k].s;
+        return cudaSuccess;
+      }
+  Scratch s{};
+  e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.sales), g_sales);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.zpart), g_zpart);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.error), g_error);
+  if (e != cudaSuccess) return e;
+  if (get(&ctx) != CUDA_SUCCESS || !ctx) return cudaErrorDeviceUninitialized;
+  // A full table (more than kMaxContexts contexts in one process) overwrites a
+  // slot; a context that loses its slot is looked up again on its next call.
+  const int slot = g_cached < kMaxContexts ? g_cached++ : (int)(reinterpret_cast<uintptr_t>(ctx) % kMaxContexts);
+  g_cache[slot] = ScratchEntry{dev, ctx, s};
+  *out = s;
   return cudaSuccess;
 }
 
@@ -100,7 +139,7 @@ __global__ void __launch_bounds__(kThreads) k_na_segments(spfom_device_segments 
   for (long long l = blockIdx.x * gpb + threadIdx.x / W; l < D.L; l += ngroups) {
     const long long b = D.seg_ptr[l];
     const int K = (int)(D.seg_ptr[l + 1] - b);
-    if (K > W) {  // larger than the stated max_set_size: flag it, leave the segment out
+    if (K > D.max_set_size) {  // larger than the stated max_set_size: flag it, leave the segment out
       if (lane == 0) s.error[0] = 1;
       continue;
     }
@@ -171,15 +210,19 @@ __global__ void __launch_bounds__(kThreads) k_na_segments(spfom_device_segments 
   if (threadIdx.x == 0) s.zpart[blockIdx.x] = tot;
 }
 
+// Copies the sales out (every entry NaN when a segment exceeded max_set_size:
+// the results are then incomplete, and a caller that reads only the sales
+// sees it too) and folds the per-block values into *z_out (NaN likewise).
 __global__ void k_na_finish(int n, int nblocks, Scratch s, double* __restrict__ sales_out, double* z_out) {
   __shared__ double sh[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) sales_out[i] = s.sales[i];
+  const bool bad = s.error[0] != 0;
+  if (i < n) sales_out[i] = bad ? CUDART_NAN : s.sales[i];
   if (blockIdx.x != 0) return;
   double z = 0.0;
   for (int b = threadIdx.x; b < nblocks; b += blockDim.x) z += s.zpart[b];
   z = na_block_sum(z, sh);
-  if (threadIdx.x == 0) z_out[0] = s.error[0] ? CUDART_NAN : z;
+  if (threadIdx.x == 0) z_out[0] = bad ? CUDART_NAN : z;
 }
 
 }  // namespace
@@ -190,11 +233,16 @@ extern "C" spfom_status spfom_sales_noalloc(const spfom_device_segments* seg, co
   if (seg->n < 0 || seg->n > SPFOM_NOALLOC_MAX_PRODUCTS || seg->L < 0 || seg->max_set_size < 0 ||
       seg->max_set_size > 32)
     return SPFOM_EINVAL;
+  // seg_prod and v are read only for segments of at most max_set_size products,
+  // so with max_set_size == 0 (every segment must be empty) they may be NULL.
   if (!seg->seg_ptr || (seg->n > 0 && (!margins || !sales)) ||
       (seg->L > 0 && (!seg->lam || !seg->v0 || (seg->max_set_size > 0 && (!seg->seg_prod || !seg->v)))))
     return SPFOM_EINVAL;
+  // An error already pending on this thread belongs to earlier work: leave it
+  // for its owner instead of reporting (and clearing) it as this call's.
+  if (cudaPeekAtLastError() != cudaSuccess) return SPFOM_ECUDA;
   Scratch s{};
-  if (scratch_for_current_device(&s) != cudaSuccess) return SPFOM_ECUDA;
+  if (scratch_for_current_context(&s) != cudaSuccess) return SPFOM_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   int W = 1;
   while (W < seg->max_set_size) W <<= 1;
