@@ -515,8 +515,17 @@ def huge_leg(args, stream, local):
                                       "kkt": st["kkt"], "dual_obj": st["dual_avg"],
                                       "final_iter_precision": st["iter_precision"]}
     sv.close()
-    # the binary64 time to 1e-4 at the measured iteration rate (same iteration count as the binary32 solve)
-    out["f64"]["time_to_kkt_1e-4_at_f32_iterations_s"] = st["iters"] * out["f64"]["ms_per_iter"] * 1e-3
+    # the plain binary64 solve to 1e-4, measured the same way
+    sd = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=1e-4, max_iters=20000, precision=64,
+                tiling=out["f64"]["tiling"])
+    w0 = time.perf_counter()
+    sd_st = sd.solve()
+    out["f64"]["time_to_kkt_1e-4"] = {"seconds_wall": time.perf_counter() - w0, "seconds_device": sd_st["seconds"],
+                                      "iterations": sd_st["iters"], "converged": bool(sd_st["converged"]),
+                                      "kkt": sd_st["kkt"], "dual_obj": sd_st["dual_avg"]}
+    sd.close()
+    out["f32"]["time_to_kkt_1e-4"]["speedup_vs_f64"] = sd_st["seconds"] / st["seconds"] if st["seconds"] > 0 else None
+    out["f32"]["time_to_kkt_1e-4"]["objective_rel_diff_vs_f64"] = abs(st["dual_avg"] / sd_st["dual_avg"] - 1.0)
     # the oracle on one host core: two full iterations, and its time to 1e-4 extrapolated with the
     # GPU solve's iteration count (same iterates)
     if not args.no_cpu_baseline:

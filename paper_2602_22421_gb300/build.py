@@ -17,7 +17,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspfom.so")
 SOURCES = ["spfom_kernels.cu", "spfom_segments_fast.cu", "spfom_segments_tma.cu", "spfom_batch.cu",
            "spfom_api.cu", "spfom_noalloc.cu", "spfom_mlp.cu", "spfom_warm.cu",
-           "spfom_segments_dd.cu", "spfom_segments_coop.cu", "spfom_segments_bchunk.cu", "spfom_sliced.cu"]
+           "spfom_segments_dd.cu", "spfom_segments_coop.cu", "spfom_segments_bchunk.cu", "spfom_sliced.cu",
+           "spfom_segments_rows.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing"]
 

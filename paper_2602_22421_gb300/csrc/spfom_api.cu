@@ -233,6 +233,51 @@ spfom_status build_sliced(spfom_ctx* ctx) {
   return SPFOM_OK;
 }
 
+// The row-exact copy of the loaded single instance (precision-64 tiling 4),
+// built on first use like the slot-major copy: positions, chunk offsets and
+// classes on the host, the items and per-position values gathered on the device.
+spfom_status build_rows(spfom_ctx* ctx) {
+  Work& W = ctx->W;
+  if (W.rx.nchunks > 0 || !W.fast || !W.plan.rows_ok) return SPFOM_OK;
+  const Problem& P = ctx->P;
+  std::vector<long long> seg_ptr((size_t)P.L + 1);
+  SPFOM_CUDA(ctx, cudaMemcpyAsync(seg_ptr.data(), P.seg_ptr, sizeof(long long) * seg_ptr.size(),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+  SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::vector<long long> perm, off;
+  spfom::SlView rx{};
+  const long long nch = spfom::rows_layout(seg_ptr.data(), P.L, &perm, &off, rx.cls_c, rx.cls_pos);
+  const size_t entries = (size_t)std::max(off[(size_t)nch], 1ll), npos = std::max<size_t>(perm.size(), 1);
+  long long* d_perm = nullptr;
+#define SPFOM_TRYS(x) do { spfom_status s_ = (x); if (s_ != SPFOM_OK) return s_; } while (0)
+  SPFOM_TRYS(upload(ctx, &rx.off, off.data(), off.size()));
+  if (!perm.empty()) SPFOM_TRYS(upload(ctx, &d_perm, perm.data(), perm.size()));
+  SPFOM_TRYS(dalloc(ctx, &rx.prod, entries));
+  SPFOM_TRYS(dalloc(ctx, &rx.v, entries));
+  SPFOM_TRYS(dalloc(ctx, &rx.vt, entries));
+  SPFOM_TRYS(dalloc(ctx, &rx.lam, npos));
+  SPFOM_TRYS(dalloc(ctx, &rx.vt0, npos));
+  SPFOM_TRYS(dalloc(ctx, &rx.rprev, npos));
+  SPFOM_TRYS(dalloc(ctx, &rx.redo, npos));
+  SPFOM_TRYS(dalloc(ctx, &rx.redo_ctl, 2));
+#undef SPFOM_TRYS
+  SPFOM_CUDA(ctx, cudaMemsetAsync(rx.rprev, 0, sizeof(float) * npos, ctx->stream));
+  SPFOM_CUDA(ctx, cudaMemsetAsync(rx.redo_ctl, 0, 2 * sizeof(unsigned), ctx->stream));
+  rx.mixed = 1;
+  rx.nchunks = nch;
+  W.rx = rx;
+  W.rx_perm = d_perm;
+  cudaError_t e = spfom::launch_rows_items(P, W.rx, W.rx_perm, ctx->stream);
+  if (e == cudaSuccess) e = spfom::launch_rows_segments(P, W.rx, W.rx_perm, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the host vectors go out of scope
+  if (e != cudaSuccess) {
+    W.rx = spfom::SlView{};
+    W.rx_perm = nullptr;
+    return cuda_fail(ctx, e, "row-exact copy");
+  }
+  return SPFOM_OK;
+}
+
 spfom_status init_state(spfom_ctx* ctx, const double* y0) {
   Work& W = ctx->W;
   const Problem& P = ctx->P;
@@ -623,6 +668,10 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
         W.ntiles = nt;
       }
       const bool dd = ctx->p.path == 2 && spfom::dd_setup(&plan, ctx->sms);
+      // row-exact copy for the precision-64 tiling 4 (single instances, path 0)
+      if (!(ctx->p.path == 0 && !ctx->loading_batch && L > 0 && ctx->p.precision == 64 &&
+            spfom::rows_plan(n, ctx->sms, &plan)))
+        plan.rows_ok = 0;
       W.plan = plan;
       W.fx_scale = std::ldexp(1.0, F);
       W.fx_bits = F;
@@ -633,6 +682,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       if (plan.bchunk_ok) W.zparts_iter = std::max(W.zparts_iter, plan.bchunk_grid);
       if (plan.bchunk64_ok) W.zparts_iter = std::max(W.zparts_iter, plan.bchunk64_grid);
       if (plan.ms_ok) W.zparts_iter = std::max(W.zparts_iter, std::max(plan.ms_grid, plan.ms_grid32));
+      if (plan.rows_ok) W.zparts_iter = std::max(W.zparts_iter, plan.rows_grid);
       W.zparts_eval = plan.grid_eval;
       if (dd)
         for (int v = 1; v <= 3; ++v) {
@@ -659,12 +709,13 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
           // double-float kernel: its tilings 1..3; binary64-sum kernel: 1 = margins read
           // from global memory, 2 = margins in shared memory, 3 = slot-major copy
           ok = dd ? spfom::dd_variant_ok(W.plan, t) != 0
-                  : (t == 1 || (t == 2 && W.plan.ms_ok) || (t == 3 && W.plan.sl_ok));
+                  : (t == 1 || (t == 2 && W.plan.ms_ok) || (t == 3 && W.plan.sl_ok) || (t == 4 && W.plan.rows_ok));
           if (dd) {
             W.plan.dd_variant = t;
           } else {
             W.plan.fast_ms = t == 2 ? 1 : 0;
             W.plan.fast_sl = t == 3 ? 1 : 0;
+            W.plan.fast_rows = t == 4 ? 1 : 0;
           }
         }
         if (!ok) {
@@ -675,6 +726,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       if (plan.scatter == 1)
         SPFOM_TRY(dalloc(ctx, &W.part, (size_t)W.zparts_iter * (size_t)(n > 0 ? n : 1)));
       SPFOM_TRY(dalloc(ctx, &W.s_fx, (size_t)n));
+      if (W.plan.rows_ok) SPFOM_TRY(dalloc(ctx, &W.marg32c, (size_t)(n > 0 ? n : 1)));
       SPFOM_TRY(dalloc(ctx, &W.rprev, (size_t)(L > 0 ? L : 1)));
       SPFOM_CUDA(ctx, cudaMemsetAsync(W.rprev, 0, sizeof(float) * (size_t)(L > 0 ? L : 1), ctx->stream));
     }
@@ -726,6 +778,8 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   }
   W.sl = spfom::SlView{};
   W.sl_perm = nullptr;
+  W.rx = spfom::SlView{};
+  W.rx_perm = nullptr;
 #undef SPFOM_TRY
   ctx->P = P;
   if (W.v2) {
@@ -738,6 +792,10 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   }
   if (W.fast && (W.plan.fast_sl || W.plan.f32_sl)) {  // a requested slot-major tiling
     const spfom_status st = build_sliced(ctx);
+    if (st != SPFOM_OK) { free_instance(ctx); return st; }
+  }
+  if (W.fast && W.plan.fast_rows) {  // the requested row-exact tiling
+    const spfom_status st = build_rows(ctx);
     if (st != SPFOM_OK) { free_instance(ctx); return st; }
   }
   // step size: tau, or tau0 * mean(r) / mean(c) (sums in index order)
@@ -1199,6 +1257,10 @@ spfom_status spfom_update(spfom_ctx* ctx, const double* c, const double* lam) {
       cudaError_t e = spfom::launch_slice_segments(P, ctx->W, ctx->W.plan.W8, ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "slot-major copy");
     }
+    if (ctx->W.rx.nchunks > 0) {  // lambda of the row-exact copy
+      cudaError_t e = spfom::launch_rows_segments(P, ctx->W.rx, ctx->W.rx_perm, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "row-exact copy");
+    }
   }
   // step sizes follow the new capacities: tau0 * mean(r) / mean(c), per instance in a batch
   if (c && !(ctx->p.tau > 0.0)) {
@@ -1259,7 +1321,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
                               : (plan.bchunk ? 6
                                              : (plan.f32_p16 ? 5
                                                              : (plan.coop ? 4 : (plan.tma ? 2 : (plan.f32_p8 ? 3 : 1))))))
-               : (dd ? plan.dd_variant : (plan.fast_sl ? 3 : (plan.fast_ms ? 2 : 1)));
+               : (dd ? plan.dd_variant : (plan.fast_rows ? 4 : (plan.fast_sl ? 3 : (plan.fast_ms ? 2 : 1))));
   };
   // The staged kernels (2, 4) load whole tiles even when a batch has frozen
   // (converged) members, which the plain-load kernels skip; their early timing
@@ -1268,7 +1330,9 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   auto available = [&](int c) {
     if (f32 && c == 7) return plan.ms_ok != 0;
     if (f32 && c == 8) return ctx->W.sl.nchunks > 0;
-    if (f64) return c == 1 || (c == 2 && plan.ms_ok != 0) || (c == 3 && ctx->W.sl.nchunks > 0);
+    if (f64)
+      return c == 1 || (c == 2 && plan.ms_ok != 0) || (c == 3 && ctx->W.sl.nchunks > 0) ||
+             (c == 4 && ctx->W.rx.nchunks > 0);
     if (f32 && c == 6) return plan.bchunk_ok != 0 && ctx->W.batch && ctx->W.bc_count > 0;
     if (f32 && c == 5) return ctx->W.W <= 32;  // 16 products per lane and at most two lanes
     if (f32) return c == 4 ? (plan.coop_ok != 0 && !ctx->W.batch) : (c != 2 || (plan.tma_ok && !ctx->W.batch));
@@ -1288,15 +1352,20 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
     } else {
       plan.fast_ms = c == 2 ? 1 : 0;
       plan.fast_sl = c == 3 ? 1 : 0;
+      plan.fast_rows = c == 4 ? 1 : 0;
     }
   };
-  if (!f32 && !dd && !(f64 && (plan.ms_ok || plan.sl_ok))) {
+  if (!f32 && !dd && !(f64 && (plan.ms_ok || plan.sl_ok || plan.rows_ok))) {
     if (choice_out) *choice_out = 1;
     return SPFOM_OK;
   }
   SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
   if ((f32 || f64) && plan.sl_ok) {  // the slot-major candidates need their copy
     const spfom_status sb = build_sliced(ctx);
+    if (sb != SPFOM_OK) return sb;
+  }
+  if (f64 && plan.rows_ok) {  // and the row-exact candidate its own
+    const spfom_status sb = build_rows(ctx);
     if (sb != SPFOM_OK) return sb;
   }
   std::vector<double> y0((size_t)ctx->P.m);

@@ -77,6 +77,11 @@ constexpr int kFastThreads = 512;
 // kernels (sorting kernel, double-float, staged, batched) take sets of <= 32.
 constexpr int kFastMaxSet = 128;
 constexpr int kFastMaxSmem = 200 * 1024;
+#ifndef SPFOM_ROWS_MAX
+#define SPFOM_ROWS_MAX 8
+#endif
+constexpr int kRowsMax = SPFOM_ROWS_MAX;  // slot rows per lane of the row-exact tiling (sets of <= kRowsMax on one lane)
+constexpr int kRowsClasses = 5;  // its lane classes: 16, 8, 4, 2, 1 lanes per segment
 constexpr int kTmaThreads = 1024;
 constexpr int kMsThreads = 1024;  // block of the margins-in-shared segment kernels (one per SM)
 constexpr int kTmaMaxSmem = 226 * 1024;
@@ -121,6 +126,11 @@ struct FastPlan {
   int sl_ok;          // 1 when the load builds the slot-major copy (single instance, path 0)
   int pipe;           // 1: the binary64 pass runs k_seg_fast_pipe (warp-specialised TMA pipeline)
   int pipe_smem, pipe_acc_bytes, pipe_grid;
+  int fast_rows;      // 1: the binary64 pass runs k_seg_rows on the row-exact copy (tiling 4)
+  int rows_ok;        // 1 when tiling 4 is available (single instance, path 0)
+  int rows_ms;        // 1: k_seg_rows keeps the binary32 margin images in shared memory (12 n bytes)
+  int rows_grid, rows_smem;
+  int rows_redo_grid;  // blocks of k_rows_redo (the SM count)
 };
 
 // Slot-major copy of the consideration sets (the sliced tilings): positions
@@ -143,6 +153,17 @@ struct SlView {
   float* vt0_32;
   float* rprev;     // [nchunks * C] carried Dinkelbach ratio per position
   long long nchunks;
+  // Row-exact copy (precision-64 tiling 4, spfom_segments_rows.cu): the lanes
+  // per segment follow the set size (W = the smallest power of two with
+  // W kRowsMax >= the set size), so the chunks fall into kRowsClasses classes
+  // in order of decreasing size: class k (W = 16 >> k) holds chunks cls_c[k] ..
+  // cls_c[k+1] - 1 of 32 / W positions each, its positions start at
+  // cls_pos[k], and every chunk has exactly ceil(largest set / W) slot rows.
+  int mixed;
+  long long cls_c[6];
+  long long cls_pos[6];
+  long long* redo;     // [cls_pos[kRowsClasses]] positions whose binary32 decision was not certified
+  unsigned* redo_ctl;  // [0] entries in redo, [1] blocks done (k_rows_redo's last block clears both)
 };
 
 // Work buffers of one ctx.
@@ -204,6 +225,9 @@ struct Work {
   BatchMaps bm;
   SlView sl;              // slot-major copy (sliced tilings), nchunks = 0 when absent
   long long* sl_perm;     // [nchunks * C] segment at each position, -1 past L
+  SlView rx;              // row-exact copy (precision-64 tiling 4), nchunks = 0 when absent
+  long long* rx_perm;     // [rx.cls_pos[kRowsClasses]] segment at each position, -1 past L
+  float* marg32c;         // [n] binary32 margin images for tiling 4 (NaN: positive, outside binary32's range)
 };
 
 struct FastArgs {
@@ -233,6 +257,9 @@ struct FastArgs {
   const int* bc_inst;
   const int* bc_prod_ptr;
   SlView sl;  // slot-major copy (sliced tilings)
+  // row-exact tiling (k_seg_rows)
+  const float* marg32c;  // [n] binary32 margin images (NaN: positive, outside binary32's normal range)
+  SlView rx;             // row-exact copy
 };
 
 // Arguments of k_seg_dd (spfom_segments_dd.cu): double-float images, and the
@@ -388,5 +415,16 @@ long long sliced_layout(const long long* seg_ptr, long long L, int W8, std::vect
                         std::vector<long long>* off);
 cudaError_t launch_slice_items(const Problem& P, const Work& Wk, int W8, cudaStream_t s);
 cudaError_t launch_slice_segments(const Problem& P, const Work& Wk, int W8, cudaStream_t s);
+// row-exact copy (spfom_sliced.cu): host layout (positions, chunk offsets and
+// classes; returns the chunk count), the gather of the items and of lambda / vt_0
+long long rows_layout(const long long* seg_ptr, long long L, std::vector<long long>* perm,
+                      std::vector<long long>* off, long long cls_c[6], long long cls_pos[6]);
+cudaError_t launch_rows_items(const Problem& P, const SlView& S, const long long* perm, cudaStream_t s);
+cudaError_t launch_rows_segments(const Problem& P, const SlView& S, const long long* perm, cudaStream_t s);
+// row-exact segment kernel (spfom_segments_rows.cu)
+bool rows_plan(int n, int sms, FastPlan* plan);
+cudaError_t launch_seg_rows(const FastArgs& A, const FastPlan& plan, cudaStream_t s);
+// the binary64 redo of the segments the row-exact kernel did not certify (after it, into s_fx)
+cudaError_t launch_rows_redo(const FastArgs& A, int sms, cudaStream_t s);
 
 }  // namespace spfom

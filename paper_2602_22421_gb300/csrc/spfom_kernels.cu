@@ -115,7 +115,8 @@ __global__ void k_prep_segments(long long L, const long long* __restrict__ seg_p
 __global__ void k_margins(Problem P, const double* __restrict__ y, const double* __restrict__ sum_y, int avg,
                           double* __restrict__ marg, double* __restrict__ s_clear,
                           unsigned long long* __restrict__ sfx_clear, const DevState* st,
-                          float* __restrict__ marg32 = nullptr, float2* __restrict__ marg2 = nullptr) {
+                          float* __restrict__ marg32 = nullptr, float2* __restrict__ marg2 = nullptr,
+                          float* __restrict__ marg32c = nullptr) {
   if (st && st->converged) return;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= P.n) return;
@@ -130,6 +131,12 @@ __global__ void k_margins(Problem P, const double* __restrict__ y, const double*
   const double m = __dsub_rn(P.r[j], acc);
   marg[j] = m;
   if (marg32) marg32[j] = __double2float_rn(m);
+  // images for the row-exact kernel's certified decision: a positive margin
+  // outside binary32's normal range becomes NaN (that segment is redone in binary64)
+  if (marg32c) {
+    const float f = __double2float_rn(m);
+    marg32c[j] = m > 0.0 ? ((f >= 1.17549435e-38f && f <= 3.40282347e38f) ? f : __int_as_float(0x7fc00000)) : 0.f;
+  }
   // pairs for the double-float kernel: only positive margins enter its decision
   if (marg2) marg2[j] = m > 0.0 ? split_pair(m) : make_float2(m < 0.0 ? -1.f : 0.f, 0.f);
   if (s_clear) s_clear[j] = 0.0;
@@ -527,6 +534,11 @@ cudaError_t launch_prep(const Problem& P, const double* w, const double* v0, dou
   return cudaGetLastError();
 }
 
+// The iterate pass of a single instance runs the row-exact kernel (precision-64 tiling 4).
+bool rows_active(const Work& Wk, const RunConfig& cfg, bool sampled) {
+  return Wk.fast && !sampled && !cfg.f32 && !Wk.batch && Wk.plan.fast_rows && Wk.rx.nchunks > 0 && Wk.marg32c;
+}
+
 cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfig& cfg, const double* marg,
                                 bool iterate, cudaStream_t s, int* zparts_out) {
   const int* seg_inst = Wk.batch ? Wk.bm.seg_inst : nullptr;
@@ -575,6 +587,12 @@ cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfi
     *zparts_out = Wk.plan.pipe_grid;
     return launch_seg_fast_pipe(A, Wk.plan, s);
   }
+  if (iterate && rows_active(Wk, cfg, false)) {
+    A.marg32c = Wk.marg32c;
+    A.rx = Wk.rx;
+    *zparts_out = Wk.plan.rows_grid;
+    return launch_seg_rows(A, Wk.plan, s);
+  }
   if (Wk.plan.bchunk64_ok && A.bc_count > 0) *zparts_out = Wk.plan.bchunk64_grid;
   else if ((Wk.plan.fast_sl && Wk.sl.nchunks > 0) || Wk.plan.fast_ms) *zparts_out = Wk.plan.ms_ok ? Wk.plan.ms_grid : Wk.plan.grid;
   else *zparts_out = Wk.plan.grid;
@@ -591,7 +609,8 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
   const int gn = (P.n + kVecThreads - 1) / kVecThreads > 0 ? (P.n + kVecThreads - 1) / kVecThreads : 1;
   k_margins<<<gn, kVecThreads, 0, s>>>(P, Wk.y, nullptr, 0, Wk.marg, (sampled || fast) ? nullptr : Wk.s,
                                        fast ? Wk.s_fx : nullptr, Wk.st, f32 ? Wk.marg32 : nullptr,
-                                       (fast && !f32) ? Wk.marg2 : nullptr);
+                                       (fast && !f32) ? Wk.marg2 : nullptr,
+                                       (fast && !f32 && Wk.plan.fast_rows) ? Wk.marg32c : nullptr);
   if (seg_begin) cudaEventRecord(seg_begin, s);
   cudaError_t e;
   int zparts = Wk.seg_blocks;
@@ -605,6 +624,12 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
   if (e != cudaSuccess) return e;
   if (fast) {
     e = launch_reduce_products(P, Wk.plan, zparts, Wk.part, Wk.s_fx, Wk.st, s);
+    if (e != cudaSuccess) return e;
+  }
+  if (rows_active(Wk, cfg, sampled)) {  // the segments the row-exact kernel left for binary64
+    FastArgs A{P, Wk.marg, nullptr, nullptr, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, Wk.s_fx};
+    A.rx = Wk.rx;
+    e = launch_rows_redo(A, Wk.plan.rows_redo_grid, s);
     if (e != cudaSuccess) return e;
   }
   k_dual_step<<<gv, kVecThreads, 0, s>>>(P, Wk, cfg, sampled ? 0 : 1, zparts);
@@ -748,7 +773,7 @@ cudaError_t launch_recover(const Problem& P, const Work& Wk, const double* x, do
 int kernel_launches_per_iteration(const Work& Wk, const RunConfig& cfg) {
   if (Wk.batch) return batch_launches_per_iteration(Wk);
   if (!(Wk.fast && cfg.batch_frac >= 1.0)) return 3;
-  return Wk.plan.scatter == 1 ? 4 : 3;
+  return (Wk.plan.scatter == 1 ? 4 : 3) + (rows_active(Wk, cfg, false) ? 1 : 0);
 }
 
 namespace {

@@ -1,0 +1,477 @@
+// Row-exact segment kernel for the precision-64 iteration (tiling 4).
+//
+// The same certified decision as k_seg_fast (Section 4.1 inner problem, GAM
+// form: the optimal assortment is S* = {j : m_j v_j > R* vt_j} at the optimal
+// rate R*, found by Dinkelbach's iteration in binary32 and certified, with a
+// binary64 redo for uncertified segments; see spfom_segments_fast.cu), laid
+// out so that no lane issues work for a slot it does not hold:
+//
+//  * one lane per segment for sets of up to 12 products (32 segments per warp,
+//    no shuffles), 2 lanes for up to 24, 4 for up to 48, 8 for up to 96 and 16
+//    for up to 128 (kRowsMax = 12 slot rows per lane at most);
+//  * the row-exact copy (spfom_sliced.cu) sorts the segments by set size, so a
+//    chunk's segments have (nearly) equal sizes, and gives each chunk exactly
+//    ceil(largest set / W) slot rows of 32 entries; the kernel is instantiated
+//    per (W, rows), and its fully unrolled slot loops hold the binary32 images
+//    a_j = m_j v_j, b_j = vt_j of just those rows in registers;
+//  * the certificate is tested once, at the converged ratio; a segment that
+//    does not pass it is not solved in the chunk loop but listed, and the
+//    kernel's last block to finish solves the listed segments in binary64
+//    (about 1e-4 of the segments), so the chunk loop carries no binary64
+//    decision code;
+//  * the binary64 work is D* = vt_0 + sum_{S*} vt_j over the chosen slots and
+//    the quotient q = lambda / D*, whose warp instructions now serve 32 (or
+//    32 / W) segments; the chosen slots' ids, v and vt are read again (L1/L2)
+//    for D* and for the sales x_j = q v_j, rounded once to unsigned 64-bit
+//    fixed point (from the 106-bit product of the significands; when the
+//    rounding position lies in its upper half, as for every workload here,
+//    the upper 64 bits decide the rounding exactly) and added per product
+//    (shared memory, or global atomics for instances with more products than
+//    shared memory holds).
+//
+// The margins enter the decision as binary32 images prepared with them
+// (k_margins): round to nearest for positive margins in binary32's normal
+// range, NaN for positive margins outside it (the segment is then not
+// certified and redone in binary64 from the binary64 margins), 0 otherwise.
+//
+// Error budget of the certificate (|a_j - R b_j| > 2^-16 (a_j + R b_j)): the
+// images carry at most 2^-23 relative error (v and vt truncated, m rounded),
+// a lane sums at most 12 slots in two interleaved partial sums (depth <= 7)
+// and a group adds at most 4 shuffle levels, so N, D and R stay within about
+// 2e-6 of their exact values, below the 1.5e-5 margin: a certified set is the
+// exact-arithmetic optimum.
+#include <cuda_runtime.h>
+
+#include "spfom_device.cuh"
+#include "spfom_internal.h"
+
+namespace spfom {
+
+namespace {
+
+#ifndef SPFOM_ROWS_THREADS
+#define SPFOM_ROWS_THREADS 512
+#endif
+#ifndef SPFOM_ROWS_MINB
+#define SPFOM_ROWS_MINB 2
+#endif
+#ifndef SPFOM_ROWS_MS_THREADS
+#define SPFOM_ROWS_MS_THREADS 1024
+#endif
+constexpr int kRowsThreads = SPFOM_ROWS_THREADS;     // block of the kernel without shared margins
+constexpr int kRowsMinBlocks = SPFOM_ROWS_MINB;      // its blocks per SM (register budget)
+constexpr int kRowsMsThreads = SPFOM_ROWS_MS_THREADS;  // block of the shared-margins kernel (one per SM)
+
+// round(x 2^G) for binary64 x >= 0 with x 2^G < 2^62 (integer operations only).
+__device__ __forceinline__ long long fx_of(double x, int G) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int e = (int)(u >> 52);
+  const unsigned long long m = (u & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const int sh = 1075 - G - e;  // x 2^G = m 2^-sh
+  if (e == 0 || sh > 63) return 0;
+  if (sh <= 0) return (long long)(m << -sh);
+  return (long long)((m + (1ull << (sh - 1))) >> sh);
+}
+
+// round(q v 2^F) for positive normal binary64 q, v (q v 2^F < 2^62), with q's
+// significand mq and biased exponent eq decoded once per segment. The product
+// of the 53-bit significands is P = hi 2^64 + lo and the result is
+// round(P / 2^sh). For sh >= 65 the rounding bit lies in hi and lo < 2^64
+// cannot move floor((hi 2^64 + lo + 2^(sh-1)) / 2^sh) = floor((hi + 2^(sh-65)) /
+// 2^(sh-64) + lo / 2^sh), so hi alone gives the exact rounding.
+__device__ __forceinline__ unsigned long long fixed_q(unsigned long long mq, int eq, double v, int F) {
+  const unsigned long long uv = (unsigned long long)__double_as_longlong(v);
+  const unsigned long long mv = (uv & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const int sh = 2150 - F - eq - (int)(uv >> 52);
+  const unsigned long long hi = __umul64hi(mq, mv);
+  if (sh >= 65) return sh > 126 ? 0ull : (hi + (1ull << (sh - 65))) >> (sh - 64);
+  if (sh < 43) return 0ull;  // cannot occur below 2^62
+  unsigned long long lo = mq * mv, h = hi;
+  if (sh <= 64) {
+    const unsigned long long half = 1ull << (sh - 1);
+    lo += half;
+    h += (lo < half) ? 1ull : 0ull;
+  }
+  return sh < 64 ? (h << (64 - sh)) | (lo >> sh) : h;
+}
+
+// Chunk and group of a position of the row-exact copy.
+struct RowsPos {
+  long long c, e;  // chunk, entry of the group's lane 0 in row 0
+  int W, rows;
+};
+__device__ __forceinline__ RowsPos rows_pos(const SlView& S, long long pos) {
+  int k = 0;
+  while (k < kRowsClasses - 1 && pos >= S.cls_pos[k + 1]) ++k;
+  RowsPos r;
+  r.W = 16 >> k;
+  const long long rel = pos - S.cls_pos[k], C = 32 / r.W;
+  r.c = S.cls_c[k] + rel / C;
+  const long long o = S.off[r.c];
+  r.rows = (int)((S.off[r.c + 1] - o) >> 5);
+  r.e = o + (rel % C) * r.W;
+  return r;
+}
+
+// One Dinkelbach pass over a lane's R slots at ratio Rr: the set {a_j > Rr b_j}
+// of the candidates, with the sums of a and b over it (two interleaved partial
+// sums each); CERT also tests every candidate against the certificate margin.
+template <int R, bool CERT>
+__device__ __forceinline__ unsigned dk_pass(const float (&af)[R], const float (&bf)[R], unsigned cand, float Rr,
+                                            float& N, float& D, bool& cert) {
+  unsigned s = 0;
+  float N0 = 0.f, N1 = 0.f, D0 = 0.f, D1 = 0.f;
+#pragma unroll
+  for (int p = 0; p < R; ++p) {
+    const float a = af[p], c = Rr * bf[p];
+    const bool in = ((cand >> p) & 1u) && a > c;
+    s |= in ? 1u << p : 0u;
+    const float ai = in ? a : 0.f, bi = in ? bf[p] : 0.f;
+    if (p & 1) {
+      N1 += ai;
+      D1 += bi;
+    } else {
+      N0 += ai;
+      D0 += bi;
+    }
+    if (CERT) cert &= !((cand >> p) & 1u) || fabsf(a - c) > kCertDelta * (a + c);
+  }
+  N = N0 + N1;
+  D = D0 + D1;
+  return s;
+}
+
+// One segment (W = 1) or one lane of a W-lane segment group, R slot rows.
+// sp / vv / vtv point at this lane's entry of row 0 (row stride 32 entries).
+// Returns false when the binary32 decision is not certified: nothing is
+// added, and the caller lists the segment for the binary64 redo.
+template <int W, int R>
+__device__ __forceinline__ bool rows_segment(const FastArgs& A, const float* __restrict__ mg,
+                                             const int* __restrict__ sp, const double* __restrict__ vv,
+                                             const double* __restrict__ vtv, const SlView& S, long long pos,
+                                             unsigned gmask, unsigned long long* sums) {
+  float af[R], bf[R];
+  unsigned cand = 0;
+  bool ok = true;
+#pragma unroll
+  for (int p = 0; p < R; ++p) {
+    const int j = sp[32 * p];  // -1: padding (v = vt = 0)
+    const double v = vv[32 * p], vt = vtv[32 * p];
+    af[p] = 0.f;
+    bf[p] = 0.f;
+    if (j >= 0) {
+      const float m = mg[j];
+      if (m > 0.f) {
+        cand |= 1u << p;
+        af[p] = m * f32_trunc(v, ok);
+        bf[p] = f32_trunc(vt, ok);
+      } else if (m != m) {
+        ok = false;  // positive margin outside binary32's range: decide in binary64
+      }
+    }
+  }
+  const double vt0 = S.vt0[pos];
+  const float vt0f = f32_trunc(vt0, ok);
+  float* rp = S.rprev + pos;
+  // Dinkelbach from the carried ratio (the margins move little between
+  // iterations, so the second pass confirms almost every set)
+  float Rr = *rp, Dsel = 0.f;
+  unsigned sel = 0xffffffffu;
+  bool conv = false;
+#pragma unroll 1
+  for (int it = 0; it < R * W + 3; ++it) {
+    float N, D;
+    bool unused = true;
+    const unsigned s = dk_pass<R, false>(af, bf, cand, Rr, N, D, unused);
+    if (W == 1 ? s == sel : __all_sync(gmask, s == sel)) {
+      conv = true;
+      break;
+    }
+#pragma unroll
+    for (int o = W >> 1; o > 0; o >>= 1) {
+      N += __shfl_xor_sync(gmask, N, o, W);
+      D += __shfl_xor_sync(gmask, D, o, W);
+    }
+    Rr = __fdividef(N, vt0f + D);
+    sel = s;
+    Dsel = D;
+  }
+  // certificate at the final ratio
+  bool cert = true;
+  {
+    float N, D;
+    dk_pass<R, true>(af, bf, cand, Rr, N, D, cert);
+  }
+  bool good = ok && conv && cert;
+  if (W == 1 ? !good : !__all_sync(gmask, good)) return false;
+  if ((gmask & -gmask) == (1u << (threadIdx.x & 31))) *rp = Rr;  // the group's first lane
+  // D* = vt_0 + sum of the chosen vt, each rounded to the segment's unit 2^-G
+  // and summed exactly as integers: G puts D* just below 2^61 (from the binary32
+  // sum of the chosen images, within 1e-5 of D*), so each term's rounding is
+  // below 2^-62 of D*, finer than a binary64 sum's. The chosen slots' vt are
+  // read again (L1 or L2) by predicated loads that are all in flight together;
+  // the rounding of the sum to binary64 and the quotient are the segment's
+  // only binary64 operations.
+  const int G = 59 - (int)((__float_as_uint(vt0f + Dsel) >> 23) & 0xFFu) + 127;  // D* < 2^(61 - G)
+  long long Dfx = (W == 1 || (gmask & -gmask) == (1u << (threadIdx.x & 31))) ? fx_of(vt0, G) : 0ll;
+#pragma unroll
+  for (int p = 0; p < R; ++p)
+    if ((sel >> p) & 1u) Dfx += fx_of(vtv[32 * p], G);
+#pragma unroll
+  for (int o = W >> 1; o > 0; o >>= 1) Dfx += __shfl_xor_sync(gmask, Dfx, o, W);
+  // Dfx 2^-G: the exponent of the (positive, normal) binary64 image drops by G
+  const double Dstar = __longlong_as_double(__double_as_longlong(__ll2double_rn(Dfx)) - ((long long)G << 52));
+  const double q = quotient(S.lam[pos], Dstar);
+  const unsigned long long uq = (unsigned long long)__double_as_longlong(q);
+  const unsigned long long mq = (uq & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const int eq = (int)(uq >> 52);
+  const bool qpos = (uq >> 52) != 0ull;  // q > 0 (q is never negative)
+  // sales, four slots at a time: their ids and values are loaded before any of their atomics
+#pragma unroll
+  for (int p0 = 0; p0 < R; p0 += 4) {
+    int jc[4];
+    double vc[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      jc[u] = 0;
+      vc[u] = 0.0;
+      if (p0 + u < R && ((sel >> (p0 + u)) & 1u)) {
+        jc[u] = sp[32 * (p0 + u)];
+        vc[u] = vv[32 * (p0 + u)];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (p0 + u < R && qpos && ((sel >> (p0 + u)) & 1u)) atomicAdd(sums + jc[u], fixed_q(mq, eq, vc[u], A.fx_bits));
+  }
+  return true;
+}
+
+template <int W, int R>
+__device__ __forceinline__ void rows_chunk(const FastArgs& A, const float* mg, long long e, long long pos,
+                                           unsigned gmask, unsigned long long* sums) {
+  const SlView& S = A.rx;
+  const bool done = rows_segment<W, R>(A, mg, S.prod + e, S.v + e, S.vt + e, S, pos, gmask, sums);
+  if (!done && (gmask & -gmask) == (1u << (threadIdx.x & 31))) S.redo[atomicAdd(S.redo_ctl, 1u)] = pos;
+}
+
+// rows is exactly ceil(largest set / W): 1..kRowsMax for W = 1, above
+// kRowsMax / 2 for W >= 2 (and at most ceil(kFastMaxSet / 16) for W = 16).
+template <int W>
+__host__ __device__ constexpr int rows_lo() { return W == 1 ? 1 : kRowsMax / 2 + 1; }
+template <int W>
+__host__ __device__ constexpr int rows_hi() { return W == 16 ? (kFastMaxSet + 15) / 16 : kRowsMax; }
+
+template <int W, int R>
+__device__ __forceinline__ void rows_dispatch_r(const FastArgs& A, const float* mg, int rows, long long e,
+                                                long long pos, unsigned gmask, unsigned long long* sums) {
+  if (rows == R) {
+    rows_chunk<W, R>(A, mg, e, pos, gmask, sums);
+  } else if constexpr (R > rows_lo<W>()) {
+    rows_dispatch_r<W, R - 1>(A, mg, rows, e, pos, gmask, sums);
+  }  // rows 0 (empty sets) and counts the layout does not produce: nothing to do
+}
+
+template <int W>
+__device__ __forceinline__ void rows_dispatch(const FastArgs& A, const float* mg, int rows, long long e, long long pos,
+                                              unsigned gmask, unsigned long long* sums) {
+  rows_dispatch_r<W, rows_hi<W>()>(A, mg, rows, e, pos, gmask, sums);
+}
+
+// Binary64 solve of one listed segment by one full warp: lanes r < W hold
+// the slots r, r + W, ... of the segment (as in the chunk loop) in registers
+// (all loads in flight together), the decision is Dinkelbach's iteration in
+// binary64 from the binary64 margins, and the sales go to the global product
+// sums; the segment's carried ratio is refreshed.
+__device__ void rows_redo_segment(const FastArgs& A, long long pos, int& fallbacks) {
+  const SlView& S = A.rx;
+  const RowsPos rp = rows_pos(S, pos);
+  const int lane = threadIdx.x & 31;
+  const bool in = lane < rp.W;
+  int jv[kRowsMax];
+  double av[kRowsMax], tv[kRowsMax];
+  unsigned cand = 0;
+#pragma unroll
+  for (int p = 0; p < kRowsMax; ++p) {
+    jv[p] = -1;
+    av[p] = tv[p] = 0.0;
+    if (in && p < rp.rows) {
+      const long long k = rp.e + lane + 32ll * p;
+      jv[p] = S.prod[k];
+      tv[p] = S.vt[k];
+      av[p] = S.v[k];
+    }
+  }
+#pragma unroll
+  for (int p = 0; p < kRowsMax; ++p)
+    if (jv[p] >= 0) {
+      const double m = A.marg[jv[p]];
+      if (m > 0.0) {
+        cand |= 1u << p;
+        av[p] *= m;
+      }
+    }
+  const double vt0 = S.vt0[pos];
+  double Rd = 0.0;
+  unsigned prev = 0xffffffffu;
+  for (int it = 0; it < kRowsMax * 16 + 2; ++it) {
+    unsigned s = 0;
+    double N = 0.0, D = 0.0;
+#pragma unroll
+    for (int p = 0; p < kRowsMax; ++p)
+      if (((cand >> p) & 1u) && av[p] > Rd * tv[p]) {
+        s |= 1u << p;
+        N += av[p];
+        D += tv[p];
+      }
+    if (__all_sync(0xffffffffu, s == prev)) break;
+    for (int o = 16; o > 0; o >>= 1) {
+      N += __shfl_xor_sync(0xffffffffu, N, o);
+      D += __shfl_xor_sync(0xffffffffu, D, o);
+    }
+    Rd = N / (vt0 + D);
+    prev = s;
+  }
+  double Dl = 0.0;
+#pragma unroll
+  for (int p = 0; p < kRowsMax; ++p)
+    if ((prev >> p) & 1u) Dl += tv[p];
+  for (int o = 16; o > 0; o >>= 1) Dl += __shfl_xor_sync(0xffffffffu, Dl, o);
+  const double q = quotient(S.lam[pos], vt0 + Dl);
+#pragma unroll
+  for (int p = 0; p < kRowsMax; ++p)
+    if ((prev >> p) & 1u) atomicAdd(A.s_fx + jv[p], fixed_product(q, S.v[rp.e + lane + 32ll * p], A.fx_bits));
+  if (lane == 0) {
+    S.rprev[pos] = (float)Rd;
+    ++fallbacks;
+  }
+}
+
+// The segments the chunk loop listed: one warp per segment; the last block to
+// finish clears the list for the next pass.
+__global__ void __launch_bounds__(256) k_rows_redo(FastArgs A) {
+  __shared__ int last;
+  if (A.st && A.st->converged) return;
+  const SlView& S = A.rx;
+  const unsigned cnt = *(volatile unsigned*)S.redo_ctl;
+  int fallbacks = 0;
+  const unsigned gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), nw = gridDim.x * (blockDim.x >> 5);
+  for (unsigned i = gw; i < cnt; i += nw) rows_redo_segment(A, S.redo[i], fallbacks);
+  if (fallbacks && A.fallbacks) atomicAdd(A.fallbacks, (unsigned long long)fallbacks);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(S.redo_ctl + 1, 1u) == gridDim.x - 1;
+    if (last) {
+      S.redo_ctl[0] = 0u;
+      S.redo_ctl[1] = 0u;
+    }
+  }
+}
+
+// SC = 1: product sums in shared memory, per-block partial sums out
+// (k_reduce_products folds them); MS = 1 also copies the binary32 margin
+// images into shared memory (one 1024-thread block per SM). SC = 2: global
+// atomics into the product sums, margin images read from global memory.
+template <int SC, int MS>
+__global__ void __launch_bounds__(MS ? kRowsMsThreads : kRowsThreads, MS ? 1 : kRowsMinBlocks) k_seg_rows(FastArgs A) {
+  extern __shared__ unsigned long long acc[];  // SC == 1: [n] fixed-point sums; MS: + [n] binary32 margins
+  if (A.st && A.st->converged) return;
+  const int n = A.P.n;
+  const float* mg = A.marg32c;
+  if (SC == 1) {
+    float* smg = reinterpret_cast<float*>(acc + n);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      acc[j] = 0ull;
+      if (MS) smg[j] = A.marg32c[j];
+    }
+    if (MS) mg = smg;
+    __syncthreads();
+  }
+  unsigned long long* sums = SC == 1 ? acc : A.s_fx;
+  const SlView& S = A.rx;
+  const int wl = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < S.nchunks; c += nw) {
+    const long long o = S.off[c];
+    const int rows = (int)((S.off[c + 1] - o) >> 5);
+    int k = 0;
+    while (k < kRowsClasses - 1 && c >= S.cls_c[k + 1]) ++k;  // warp-uniform
+    const int W = 16 >> k;
+    const long long pos = S.cls_pos[k] + (c - S.cls_c[k]) * (32 / W) + wl / W;
+    const long long e = o + wl;
+    const unsigned gmask = W == 1 ? (1u << wl) : (((1u << W) - 1u) << (wl & ~(W - 1)));
+    switch (W) {
+      case 1: rows_dispatch<1>(A, mg, rows, e, pos, gmask, sums); break;
+      case 2: rows_dispatch<2>(A, mg, rows, e, pos, gmask, sums); break;
+      case 4: rows_dispatch<4>(A, mg, rows, e, pos, gmask, sums); break;
+      case 8: rows_dispatch<8>(A, mg, rows, e, pos, gmask, sums); break;
+      default: rows_dispatch<16>(A, mg, rows, e, pos, gmask, sums); break;
+    }
+  }
+  // an iterate pass forms no segment values: the dual step takes sum_l z_l as sum_j m_j s_j
+  if (threadIdx.x == 0) A.zpart[blockIdx.x] = 0.0;
+  if (SC == 1) {
+    __syncthreads();
+    unsigned long long* dst = A.part + (size_t)blockIdx.x * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) dst[j] = acc[j];
+  }
+}
+
+template <class K>
+int rows_blocks(K kernel, int smem, int threads) {
+  int nb = 0;
+  if (smem > 0 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) return 0;
+  return nb;
+}
+
+}  // namespace
+
+bool rows_plan(int n, int sms, FastPlan* plan) {
+  plan->rows_ok = 0;
+  plan->rows_redo_grid = sms;
+  const long long sums = 8ll * n, ms = 12ll * n;
+  if (ms <= kTmaMaxSmem) {  // sums and binary32 margins in shared memory, one 1024-thread block per SM
+    const int nb = rows_blocks(k_seg_rows<1, 1>, (int)ms, kRowsMsThreads);
+    if (nb >= 1) {
+      plan->rows_ok = 1;
+      plan->rows_ms = 1;
+      plan->rows_smem = (int)ms;
+      plan->rows_grid = nb * sms;
+      return true;
+    }
+  }
+  if (sums <= kFastMaxSmem) {
+    const int nb = rows_blocks(k_seg_rows<1, 0>, (int)sums, kRowsThreads);
+    if (nb >= 1) {
+      plan->rows_ok = 1;
+      plan->rows_ms = 0;
+      plan->rows_smem = (int)sums;
+      plan->rows_grid = nb * sms;
+      return true;
+    }
+  }
+  const int nb = rows_blocks(k_seg_rows<2, 0>, 0, kRowsThreads);
+  if (nb < 1) return false;
+  plan->rows_ok = 1;
+  plan->rows_ms = 0;
+  plan->rows_smem = 0;
+  plan->rows_grid = nb * sms;
+  return true;
+}
+
+cudaError_t launch_seg_rows(const FastArgs& A, const FastPlan& pl, cudaStream_t s) {
+  if (pl.rows_ms) k_seg_rows<1, 1><<<pl.rows_grid, kRowsMsThreads, pl.rows_smem, s>>>(A);
+  else if (pl.rows_smem > 0) k_seg_rows<1, 0><<<pl.rows_grid, kRowsThreads, pl.rows_smem, s>>>(A);
+  else k_seg_rows<2, 0><<<pl.rows_grid, kRowsThreads, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_redo(const FastArgs& A, int sms, cudaStream_t s) {
+  k_rows_redo<<<sms > 0 ? sms : 1, 256, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+}  // namespace spfom

@@ -72,7 +72,79 @@ __global__ void k_slice_segments(const Problem P, const float* __restrict__ lam3
   }
 }
 
+// Row-exact copy: one warp per chunk, the chunk's lanes per segment W from
+// its class; entry 32 p + wl of chunk c is product (wl mod W) + p W of the
+// chunk's (wl / W)-th segment.
+__device__ __forceinline__ int rows_class(const SlView& S, long long c) {
+  int k = 0;
+  while (k < kRowsClasses - 1 && c >= S.cls_c[k + 1]) ++k;
+  return k;
+}
+
+__global__ void k_rows_items(const Problem P, SlView S, const long long* __restrict__ perm) {
+  const int wl = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < S.nchunks; c += nw) {
+    const int k = rows_class(S, c), W = 16 >> k;
+    const long long o = S.off[c];
+    const int rows = (int)((S.off[c + 1] - o) >> 5);
+    const long long l = perm[S.cls_pos[k] + (c - S.cls_c[k]) * (32 / W) + wl / W];  // -1 past L
+    long long b = 0;
+    int K = 0;
+    if (l >= 0) {
+      b = P.seg_ptr[l];
+      K = (int)(P.seg_ptr[l + 1] - b);
+    }
+    const int r = wl & (W - 1);
+    for (int p = 0; p < rows; ++p) {
+      const int kk = r + p * W;
+      const long long e = o + 32ll * p + wl;
+      const bool in = kk < K;
+      S.prod[e] = in ? P.seg_prod[b + kk] : -1;
+      S.v[e] = in ? P.v[b + kk] : 0.0;
+      S.vt[e] = in ? P.vt[b + kk] : 0.0;
+    }
+  }
+}
+
 }  // namespace
+
+long long rows_layout(const long long* seg_ptr, long long L, std::vector<long long>* perm,
+                      std::vector<long long>* off, long long cls_c[6], long long cls_pos[6]) {
+  // counting sort by set size (<= kFastMaxSet), descending; equal sizes keep segment order
+  const int KM = kFastMaxSet;
+  std::vector<long long> cnt((size_t)KM + 2, 0);
+  for (long long l = 0; l < L; ++l) ++cnt[(size_t)(KM - (seg_ptr[l + 1] - seg_ptr[l]))];
+  std::vector<long long> sorted((size_t)L), start((size_t)KM + 2, 0);
+  for (int k = 1; k <= KM + 1; ++k) start[(size_t)k] = start[(size_t)k - 1] + cnt[(size_t)k - 1];
+  for (long long l = 0; l < L; ++l) sorted[(size_t)start[(size_t)(KM - (seg_ptr[l + 1] - seg_ptr[l]))]++] = l;
+  auto size = [&](long long i) { return seg_ptr[sorted[(size_t)i] + 1] - seg_ptr[sorted[(size_t)i]]; };
+  auto lanes = [](long long K) {
+    int W = 1;
+    while (W * kRowsMax < K) W <<= 1;
+    return W;
+  };
+  perm->clear();
+  off->assign(1, 0);
+  long long i = 0, nch = 0;
+  for (int k = 0; k < kRowsClasses; ++k) {  // classes W = 16, 8, 4, 2, 1 in order of decreasing set size
+    const int W = 16 >> k, C = 32 / W;
+    cls_c[k] = nch;
+    cls_pos[k] = (long long)perm->size();
+    while (i < L && lanes(size(i)) == W) {
+      const long long K0 = size(i);  // the chunk's largest set
+      for (int g = 0; g < C; ++g) {
+        const bool in = i < L && lanes(size(i)) == W;
+        perm->push_back(in ? sorted[(size_t)i++] : -1);
+      }
+      off->push_back(off->back() + 32 * ((K0 + W - 1) / W));
+      ++nch;
+    }
+  }
+  cls_c[kRowsClasses] = nch;
+  cls_pos[kRowsClasses] = (long long)perm->size();
+  return nch;
+}
 
 long long sliced_layout(const long long* seg_ptr, long long L, int W8, std::vector<long long>* perm,
                         std::vector<long long>* off) {
@@ -107,6 +179,22 @@ cudaError_t launch_slice_segments(const Problem& P, const Work& Wk, int W8, cuda
   const long long blocks = (npos + 255) / 256;
   k_slice_segments<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(P, Wk.lam32, Wk.vt0_32,
                                                                                            Wk.sl, Wk.sl_perm, npos);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_items(const Problem& P, const SlView& S, const long long* perm, cudaStream_t s) {
+  if (S.nchunks <= 0) return cudaSuccess;
+  const long long blocks = (S.nchunks + 7) / 8;  // 8 warps per block
+  k_rows_items<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(P, S, perm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_segments(const Problem& P, const SlView& S, const long long* perm, cudaStream_t s) {
+  const long long npos = S.cls_pos[kRowsClasses];
+  if (S.nchunks <= 0 || npos <= 0) return cudaSuccess;
+  const long long blocks = (npos + 255) / 256;
+  k_slice_segments<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(P, nullptr, nullptr, S,
+                                                                                           perm, npos);
   return cudaGetLastError();
 }
 

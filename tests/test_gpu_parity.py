@@ -68,9 +68,9 @@ CASES = {"tiny_mnl": lambda: tiny_mnl(0), "small_gam": small_gam, "edge": edge_i
          "wide": wide}
 
 
-@pytest.mark.parametrize("path,tiling", [(0, 0), (0, 2), (0, 3), (1, 0), (2, 1), (2, 2), (2, 3)],
-                         ids=["certified", "certified_shared_margins", "certified_slot_major", "general",
-                              "double_float_t1", "double_float_t2", "double_float_t3"])
+@pytest.mark.parametrize("path,tiling", [(0, 0), (0, 2), (0, 3), (0, 4), (1, 0), (2, 1), (2, 2), (2, 3)],
+                         ids=["certified", "certified_shared_margins", "certified_slot_major", "certified_row_exact",
+                              "general", "double_float_t1", "double_float_t2", "double_float_t3"])
 @pytest.mark.parametrize("name", list(CASES))
 def test_iterates_track_oracle_200(name, path, tiling):
     if (path, tiling) == (0, 2) and name == "wide":
@@ -401,15 +401,17 @@ def wide_sets_gam():
     return make_instance(n=120, m=60, L=3000, kmin=60, kmax=100, gam=True, tightness=0.6, seed=3, name="wide_sets")
 
 
+@pytest.mark.parametrize("tiling", [0, 4], ids=["lanes_16x8", "row_exact"])
 @pytest.mark.parametrize("make", [paper_shaped_small, wide_sets_gam], ids=["paper_shaped_mnl", "gam_60_100"])
-def test_sets_of_100_products_track_oracle(make):
-    """Sets of up to 100 products (16 lanes x 8 slots per segment): the
-    binary64 iterates track the oracle as for small sets."""
+def test_sets_of_100_products_track_oracle(make, tiling):
+    """Sets of up to 100 products (16 lanes x 8 slots per segment, or 8 lanes
+    x <= 13 exact rows in the row-exact tiling): the binary64 iterates track
+    the oracle as for small sets."""
     inst = make()
     o = Oracle(inst)
     run = o.run(OracleParams())
     done = 0
-    with Solver(inst) as s:
+    with Solver(inst, tiling=tiling) as s:
         assert s.stats()["fast_path"] == 1
         for t in (1, 2, 63, 64, 65, 200):
             while done < t:
@@ -423,6 +425,28 @@ def test_sets_of_100_products_track_oracle(make):
             assert st["z_sum"] == pytest.approx(ost["z_sum"], rel=ITER_RTOL)
             if ost["evals"]:
                 assert st["kkt"] == pytest.approx(ost["kkt"], rel=1e-5, abs=1e-12)
+
+
+def test_row_exact_tiling_mixes_every_lane_class():
+    """One instance whose sets span 0..128 products, so the row-exact copy holds
+    all four lane classes (1, 2, 4, 8 lanes per segment), partial chunks at each
+    class boundary and empty sets: 200 iterations track the oracle."""
+    inst = make_instance(n=400, m=40, L=3001, kmin=0, kmax=128, gam=True, tightness=0.6, seed=21,
+                         name="all_classes")
+    o = Oracle(inst)
+    run = o.run(OracleParams())
+    done = 0
+    with Solver(inst, tiling=4) as s:
+        for t in (1, 64, 65, 200):
+            while done < t:
+                run.step(1)
+                done += 1
+            st = s.step(t - st_iters(s))
+            ost = run.stats()
+            assert st["iters"] == ost["t"] == t and st["restarts"] == ost["restarts"]
+            assert nrel(s.duals(), run.y) <= ITER_RTOL, (t, nrel(s.duals(), run.y))
+            assert nrel(s.vector(5), run.s) <= ITER_RTOL
+            assert st["z_sum"] == pytest.approx(ost["z_sum"], rel=ITER_RTOL)
 
 
 def test_sets_of_100_products_binary32_solve():
