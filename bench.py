@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm start")
     ap.add_argument("--no-paper-shaped", action="store_true",
                     help="skip the instance of the paper's speedup-study shape (sets of all 100 products)")
-    ap.add_argument("--learned-test", type=int, default=32)
+    ap.add_argument("--learned-test", type=int, default=128)
     return ap.parse_args()
 
 
@@ -559,7 +559,7 @@ def batched_leg(args, local):
         insts = list(pool.map(batch_base, [4] * count, range(count)))
     gen_s = time.perf_counter() - t0
     rho = period_rates(4, count, args.periods)
-    prm = dict(restart_tau_balance=0.5, max_iters=20000)
+    prm = dict(restart_tau_balance=0.5, max_iters=40000)
     summary, path, per = PR.run_batched(insts, rho, periods=args.periods, precision=32, **prm)
     batched_s = sum(r["seconds"] for r in summary["records"])
     if args.seq_sample and args.seq_sample < count:

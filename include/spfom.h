@@ -69,7 +69,7 @@ typedef struct {
   double restart_beta;       /* 0.2: restart when KKT <= beta * KKT at the last restart */
   double restart_artificial; /* 0.36: or when the epoch holds this fraction of all iterations */
   double restart_tau_decay;  /* 1.0: tau <- tau * decay at each restart */
-  double restart_tau_balance;/* 0.5 (default); 0: off. b in (0, 1]: at a restart forced by the
+  double restart_tau_balance;/* 0 (default): off. b in (0, 1]: at a restart forced by the
                                 epoch-length rule (the KKT did not drop by restart_beta), also
                                 tau <- tau * clamp(sqrt(pinf / gap), b, 1 / b): a constant step
                                 leaves an O(tau) duality gap on instances with few segments, and
@@ -265,6 +265,18 @@ spfom_status spfom_update(spfom_ctx* ctx, const double* c, const double* lam);
  * assortment at duals y (host [m], >= 0): bid-price control of Section 5.1
  * with bid prices y. Leaves the iteration state alone. */
 spfom_status spfom_sales_at(spfom_ctx* ctx, const double* y, double* s_out);
+
+/* Testing aid (no counterpart in the paper): the number of polls after which
+ * a bounded device wait of the staged segment kernel (precision 32, tiling 2:
+ * bulk copies of segment tiles into shared memory) gives up (default
+ * 4194304). A wait that gives up records an error in the ctx's device state;
+ * spfom_step / spfom_solve then return SPFOM_ETIMEOUT and the iteration's
+ * results are invalid (the ctx stays in that state; make a new ctx). Before a
+ * block returns it still waits, with the default limit, for the copies it
+ * issued, so none is left in flight. A limit of 0 makes every such wait give
+ * up at once; tests use it to exercise that path. Drops captured graphs.
+ * EINVAL: ctx is NULL. */
+spfom_status spfom_set_wait_limit(spfom_ctx* ctx, uint32_t polls);
 
 /* Segment-to-warp tiling autotuner (no counterpart in the paper). Times each
  * candidate segment kernel of the loaded instance or batch for `iters`

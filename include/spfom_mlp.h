@@ -47,6 +47,16 @@ typedef struct spfom_mlp spfom_mlp; /* opaque; owns weights, Adam moments, works
 spfom_status spfom_mlp_create(int32_t device, uint64_t seed, spfom_mlp** out);
 void spfom_mlp_destroy(spfom_mlp* net);
 
+/* Testing aid (no counterpart in the paper): the number of polls after which
+ * the tensor-core products' bounded copy waits give up (default 4194304). A
+ * wait that gives up sets the network's error flag; the call then returns
+ * SPFOM_ETIMEOUT and its outputs are invalid. Before giving up, a block still
+ * waits, with the default limit, for the copies it issued and for its issued
+ * tensor-core operations, then frees its tensor memory, so no copy or
+ * operation is left in flight. A limit of 0 makes every such wait give up at
+ * once; tests use it to exercise that path. EINVAL: net is NULL. */
+spfom_status spfom_mlp_set_wait_limit(spfom_mlp* net, uint32_t polls);
+
 /* Copy all parameters in (host [SPFOM_MLP_PARAMS]; resets Adam's moments) or out. */
 spfom_status spfom_mlp_set_params(spfom_mlp* net, const float* params);
 spfom_status spfom_mlp_get_params(spfom_mlp* net, float* params);

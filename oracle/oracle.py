@@ -114,7 +114,7 @@ class Params:
     restart_beta: float = 0.2
     restart_artificial: float = 0.36
     restart_tau_decay: float = 1.0
-    restart_tau_balance: float = 0.5
+    restart_tau_balance: float = 0.0
     kkt_tol: float = 1e-4
 
     def _c(self) -> _Params:

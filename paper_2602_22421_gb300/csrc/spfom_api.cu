@@ -40,6 +40,7 @@ struct spfom_ctx {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> prof_ev;  // event pairs of profiled segment launches
   int sms = 0;
+  unsigned wait_limit = 1u << 22;  // polls of a bounded device wait (spfom_set_wait_limit; the kernels' default)
   unsigned long long fallback_host = 0;
   bool polishing = false;  // precision 32: binary64 iterations after the first converged evaluation
   cudaGraphExec_t period[2] = {nullptr, nullptr};  // one evaluation period, [binary64, binary32 pass]
@@ -415,7 +416,6 @@ void spfom_default_params(spfom_params* p) {
   p->restart_beta = 0.2;
   p->restart_artificial = 0.36;
   p->restart_tau_decay = 1.0;
-  p->restart_tau_balance = 0.5;
   p->kkt_tol = 1e-4;
   p->max_iters = 100000;
   p->device = 0;
@@ -814,6 +814,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
   cfg.restart_tau_balance = ctx->p.restart_tau_balance;
   cfg.kkt_tol = ctx->p.kkt_tol;
   cfg.f32 = ctx->p.precision == 32 ? 1 : 0;
+  ctx->W.wait_limit = ctx->wait_limit;
   ctx->loaded = true;
   W.batch = false;
   if (ctx->loading_batch) {
@@ -1011,12 +1012,22 @@ spfom_status spfom_solve(spfom_ctx* ctx, const double* y0, spfom_stats* out) {
     launches += st.kernel_launches;
     if (ctx->W.batch && ctx->cfg.f32 && !st.converged && !ctx->h_inst.empty()) {
       // a few members left: finish them with binary64 iterations (a binary32 run can stall
-      // above the tolerance near ties, and the frozen members cost little either way)
+      // above the tolerance near ties, and the frozen members cost little either way), and
+      // confirm the members that converged in binary32 now, with binary64 iterations that
+      // run beside the last members' instead of after them
       long long active = 0;
       for (const auto& I : ctx->h_inst) active += I.converged ? 0 : 1;
       if (active * 20 <= (long long)ctx->h_inst.size()) {
         ctx->cfg.f32 = 0;  // the binary64 period graph is kept apart from the binary32 one
         ctx->polishing = true;
+        if (ctx->p.polish && !polished) {
+          polished = true;
+          for (auto& I : ctx->h_inst) I.converged = 0;
+          SPFOM_CUDA(ctx, cudaMemcpyAsync(ctx->W.bm.inst, ctx->h_inst.data(),
+                                          sizeof(spfom::InstState) * ctx->W.bm.count, cudaMemcpyHostToDevice,
+                                          ctx->stream));
+          SPFOM_CUDA(ctx, cudaMemsetAsync(ctx->W.bm.conv, 0, sizeof(int) * ctx->W.bm.count, ctx->stream));
+        }
       }
     }
     if (st.converged && ctx->p.precision == 32 && ctx->p.polish && !polished) {
@@ -1283,6 +1294,14 @@ spfom_status spfom_update(spfom_ctx* ctx, const double* c, const double* lam) {
     }
   }
   SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return SPFOM_OK;
+}
+
+spfom_status spfom_set_wait_limit(spfom_ctx* ctx, uint32_t polls) {
+  if (!ctx) return SPFOM_EINVAL;
+  ctx->wait_limit = polls;
+  ctx->W.wait_limit = polls;
+  drop_graphs(ctx);  // captured launches carry the old limit
   return SPFOM_OK;
 }
 

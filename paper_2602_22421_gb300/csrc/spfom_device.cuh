@@ -125,8 +125,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
       : "memory");
   return done != 0u;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity) {
-  for (unsigned it = 0; it < kWaitLimit; ++it)
+// limit: polls before giving up (kWaitLimit unless a test lowers it; the waits
+// that let a failing block's own copies land always use kWaitLimit)
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned bar, unsigned parity, unsigned limit = kWaitLimit) {
+  for (unsigned it = 0; it < limit; ++it)
     if (mbar_try_wait(bar, parity)) return true;
   return false;
 }

@@ -228,6 +228,7 @@ struct Work {
   SlView rx;              // row-exact copy (precision-64 tiling 4), nchunks = 0 when absent
   long long* rx_perm;     // [rx.cls_pos[kRowsClasses]] segment at each position, -1 past L
   float* marg32c;         // [n] binary32 margin images for tiling 4 (NaN: positive, outside binary32's range)
+  unsigned wait_limit;    // polls of a bounded device wait (spfom_set_wait_limit; default 1 << 22)
 };
 
 struct FastArgs {
@@ -325,6 +326,7 @@ struct F32Args {
   const int* bc_inst;        // [bc_count] instance of each chunk
   const int* bc_prod_ptr;    // [instances + 1] product offsets
   SlView sl;                 // slot-major copy (sliced tilings)
+  unsigned wait_limit;       // polls of a staged-copy wait before it gives up (k_seg_f32_tma)
 };
 
 struct RunConfig {

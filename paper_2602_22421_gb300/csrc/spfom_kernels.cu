@@ -568,6 +568,7 @@ cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfi
               seg_inst, conv, z_seg, Wk.coop_tile_ptr, Wk.coop_ntiles, Wk.plan.coop_items, Wk.plan.coop_segs,
               Wk.rprev, 0, 0, Wk.batch ? Wk.bc_count : 0, Wk.bc_seg, Wk.bc_inst,
               Wk.batch ? Wk.bm.prod_ptr : nullptr, Wk.sl};
+    A.wait_limit = Wk.wait_limit;
     const bool bchunk = Wk.plan.bchunk && Wk.batch && Wk.bc_count > 0;
     const FastPlan& pl = Wk.plan;
     if (!bchunk && pl.f32_sl && Wk.sl.nchunks > 0) {

@@ -128,6 +128,7 @@ struct Epi {
   int ld16t;
   int zpad;                      // rows M..zpad-1 of out16t are written as zeros (K padding of later products)
   int* error;                    // set to 1 when a wait gives up
+  unsigned wait_limit;           // polls of the producer's waits before they give up
 };
 
 template <int BN>
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     int issued = pre, consumed = 0;
     for (int i = 0; i < nkt; ++i) {
       const int s = i % S::kStages;
-      if (!mbar_wait_bounded(smem_addr(&full[s]), (unsigned)(i / S::kStages) & 1u)) {
+      if (!mbar_wait_bounded(smem_addr(&full[s]), (unsigned)(i / S::kStages) & 1u, E.wait_limit)) {
         ok = 0;
         break;
       }
@@ -206,7 +207,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       // refill the stage of the previous tile once its MMAs have read it
       if (i >= 1 && i - 1 + S::kStages < nkt) {
         const int p = i - 1;
-        if (!mbar_wait_bounded(smem_addr(&empty[p % S::kStages]), (unsigned)(p / S::kStages) & 1u)) {
+        if (!mbar_wait_bounded(smem_addr(&empty[p % S::kStages]), (unsigned)(p / S::kStages) & 1u, E.wait_limit)) {
           ok = 0;
           break;
         }
@@ -476,6 +477,7 @@ using spfom::mlp::Epi;
 struct spfom_mlp {
   int device = 0;
   int* d_error = nullptr;
+  unsigned wait_limit = spfom::kWaitLimit;  // polls of the GEMM producer's waits (spfom_mlp_set_wait_limit)
   float* p = nullptr;   // master parameters
   float* g = nullptr;   // gradients
   float* m1 = nullptr;  // Adam moments
@@ -572,6 +574,7 @@ spfom_status from_cuda(cudaError_t e) {
 Epi epi(spfom_mlp* n) {
   Epi E{};
   E.error = n->d_error;
+  E.wait_limit = n->wait_limit;
   return E;
 }
 
@@ -708,6 +711,12 @@ void spfom_mlp_destroy(spfom_mlp* n) {
   for (void* q : ptrs)
     if (q) cudaFree(q);
   delete n;
+}
+
+spfom_status spfom_mlp_set_wait_limit(spfom_mlp* n, uint32_t polls) {
+  if (!n) return SPFOM_EINVAL;
+  n->wait_limit = polls;
+  return SPFOM_OK;
 }
 
 spfom_status spfom_mlp_set_params(spfom_mlp* n, const float* params) {

@@ -601,7 +601,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1) k_seg_f32_tma(F32Args A) {
   for (long long t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
     const int stg = k & 1;
     unsigned char* S = stages + stg * StageLayout::bytes;
-    const bool ok = mbar_wait_bounded(stg ? bar1 : bar0, (unsigned)((k >> 1) & 1));
+    const bool ok = mbar_wait_bounded(stg ? bar1 : bar0, (unsigned)((k >> 1) & 1), A.wait_limit);
     if (__syncthreads_or(!ok)) {
       failed = true;
       break;

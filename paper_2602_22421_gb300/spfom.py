@@ -23,8 +23,8 @@ VEC_Y, VEC_YBAR, VEC_SUM_Y, VEC_SUM_G, VEC_G, VEC_S, VEC_MARGINS = range(7)
 EXPORTS = ("spfom_default_params", "spfom_create", "spfom_load_instance", "spfom_reset", "spfom_step",
            "spfom_solve", "spfom_vector", "spfom_duals", "spfom_evaluate", "spfom_get_stats", "spfom_destroy",
            "spfom_last_error", "spfom_status_string", "spfom_sales_noalloc", "spfom_load_batch",
-           "spfom_batch_stats", "spfom_update", "spfom_sales_at", "spfom_autotune",
-           "spfom_mlp_create", "spfom_mlp_destroy", "spfom_mlp_set_params", "spfom_mlp_get_params",
+           "spfom_batch_stats", "spfom_update", "spfom_sales_at", "spfom_autotune", "spfom_set_wait_limit",
+           "spfom_mlp_create", "spfom_mlp_set_wait_limit", "spfom_mlp_destroy", "spfom_mlp_set_params", "spfom_mlp_get_params",
            "spfom_mlp_get_grads", "spfom_mlp_forward", "spfom_mlp_loss_grad", "spfom_mlp_adam",
            "spfom_mlp_train_step", "spfom_features", "spfom_solve_warm", "spfom_xbar", "spfom_recover")
 
@@ -119,7 +119,10 @@ def lib():
         h.spfom_update.argtypes = [C.c_void_p, _f64p, _f64p]
         h.spfom_sales_at.argtypes = [C.c_void_p, _f64p, _f64p]
         h.spfom_autotune.argtypes = [C.c_void_p, C.c_int32, P(C.c_int32)]
-        for f in ("spfom_load_batch", "spfom_batch_stats", "spfom_update", "spfom_sales_at", "spfom_autotune"):
+        h.spfom_set_wait_limit.argtypes = [C.c_void_p, C.c_uint32]
+        h.spfom_mlp_set_wait_limit.argtypes = [C.c_void_p, C.c_uint32]
+        for f in ("spfom_load_batch", "spfom_batch_stats", "spfom_update", "spfom_sales_at", "spfom_autotune",
+                  "spfom_set_wait_limit", "spfom_mlp_set_wait_limit"):
             getattr(h, f).restype = C.c_int
         _f32p = C.POINTER(C.c_float)
         h.spfom_mlp_create.argtypes = [C.c_int32, C.c_uint64, P(C.c_void_p)]
@@ -263,6 +266,10 @@ class Solver:
         self._check(self._lib.spfom_sales_at(self._h, _p(y, _f64p), _p(out, _f64p)))
         return out[: self.n]
 
+    def set_wait_limit(self, polls: int):
+        """Polls before a bounded device wait gives up (spfom_set_wait_limit; testing aid)."""
+        self._check(self._lib.spfom_set_wait_limit(self._h, int(polls)))
+
     def autotune(self, iters: int = 64) -> int:
         """Pick the fastest segment kernel for this instance (spfom_autotune)."""
         ch = C.c_int32(0)
@@ -377,6 +384,11 @@ class MLP:
             raise SpfomError(ESTATE, "network is closed")
         if st != OK:
             raise SpfomError(st, f"{what}: " + self._lib.spfom_status_string(st).decode())
+
+    def set_wait_limit(self, polls: int):
+        """Polls before a bounded copy wait of the tensor-core products gives up
+        (spfom_mlp_set_wait_limit; testing aid)."""
+        self._check(self._lib.spfom_mlp_set_wait_limit(self._h, int(polls)), "set_wait_limit")
 
     @staticmethod
     def _dev(t, rows, cols=None):

@@ -175,8 +175,8 @@ def test_run_converges_to_lp_optimum_tiny():
     instance. With 40 segments the dual function is very non-smooth and a
     constant step leaves an O(tau) duality gap, so this instance's schedule
     halves the step at every restart (restart_tau_decay = 0.5, a restarted
-    subgradient schedule); it converges at iteration 4544. The default
-    schedule (tau balanced at epoch-length restarts) converges too, later."""
+    subgradient schedule); it converges at iteration 4544. Balancing tau at
+    epoch-length restarts (restart_tau_balance = 0.5) converges too, later."""
     inst = tiny_mnl(0)
     opt, _ = sblp_highs(inst)
     o = Oracle(inst)
@@ -192,9 +192,9 @@ def test_run_converges_to_lp_optimum_tiny():
     assert all(np.all(y >= 0) for y in ys)
     assert opt * (1 - 1e-12) <= st["dual_avg"] <= opt * (1 + 1e-4)
     assert o.dual(run.ybar) >= opt * (1 - 1e-12)
-    default = o.run(Params())  # restart_tau_balance = 0.5
+    balanced = o.run(Params(restart_tau_balance=0.5))
     for _ in range(300):
-        st = default.step(64)
+        st = balanced.step(64)
         if st["converged"]:
             break
     assert st["converged"] == 1 and st["kkt"] <= 1e-4, st
