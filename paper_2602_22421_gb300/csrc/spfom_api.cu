@@ -234,7 +234,8 @@ spfom_status build_sliced(spfom_ctx* ctx) {
   return SPFOM_OK;
 }
 
-// The row-exact copy of the loaded single instance (precision-64 tiling 4),
+// The row-exact copy of the loaded single instance (precision-64 tiling 4:
+// binary64 v, vt, lambda, vt_0; precision-32 tiling 9: their binary32 copies),
 // built on first use like the slot-major copy: positions, chunk offsets and
 // classes on the host, the items and per-position values gathered on the device.
 spfom_status build_rows(spfom_ctx* ctx) {
@@ -254,10 +255,17 @@ spfom_status build_rows(spfom_ctx* ctx) {
   SPFOM_TRYS(upload(ctx, &rx.off, off.data(), off.size()));
   if (!perm.empty()) SPFOM_TRYS(upload(ctx, &d_perm, perm.data(), perm.size()));
   SPFOM_TRYS(dalloc(ctx, &rx.prod, entries));
-  SPFOM_TRYS(dalloc(ctx, &rx.v, entries));
-  SPFOM_TRYS(dalloc(ctx, &rx.vt, entries));
-  SPFOM_TRYS(dalloc(ctx, &rx.lam, npos));
-  SPFOM_TRYS(dalloc(ctx, &rx.vt0, npos));
+  if (W.v32) {
+    SPFOM_TRYS(dalloc(ctx, &rx.v32, entries));
+    SPFOM_TRYS(dalloc(ctx, &rx.vt32, entries));
+    SPFOM_TRYS(dalloc(ctx, &rx.lam32, npos));
+    SPFOM_TRYS(dalloc(ctx, &rx.vt0_32, npos));
+  } else {
+    SPFOM_TRYS(dalloc(ctx, &rx.v, entries));
+    SPFOM_TRYS(dalloc(ctx, &rx.vt, entries));
+    SPFOM_TRYS(dalloc(ctx, &rx.lam, npos));
+    SPFOM_TRYS(dalloc(ctx, &rx.vt0, npos));
+  }
   SPFOM_TRYS(dalloc(ctx, &rx.rprev, npos));
   SPFOM_TRYS(dalloc(ctx, &rx.redo, npos));
   SPFOM_TRYS(dalloc(ctx, &rx.redo_ctl, 2));
@@ -268,8 +276,8 @@ spfom_status build_rows(spfom_ctx* ctx) {
   rx.nchunks = nch;
   W.rx = rx;
   W.rx_perm = d_perm;
-  cudaError_t e = spfom::launch_rows_items(P, W.rx, W.rx_perm, ctx->stream);
-  if (e == cudaSuccess) e = spfom::launch_rows_segments(P, W.rx, W.rx_perm, ctx->stream);
+  cudaError_t e = spfom::launch_rows_items(P, W.rx, W.rx_perm, W.v32, W.vt32, ctx->stream);
+  if (e == cudaSuccess) e = spfom::launch_rows_segments(P, W.rx, W.rx_perm, W.lam32, W.vt0_32, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);  // the host vectors go out of scope
   if (e != cudaSuccess) {
     W.rx = spfom::SlView{};
@@ -449,7 +457,7 @@ spfom_status spfom_create(const spfom_params* p, spfom_ctx** out) {
   if (prm.precision != 64 && prm.precision != 32) return SPFOM_ENOTSUP;
   if (!(prm.batch_frac > 0.0) || !(prm.restart_beta >= 0.0) || !(prm.kkt_tol >= 0.0) || prm.tau0 < 0 ||
       prm.mu < 0 || !(prm.restart_tau_decay > 0.0) ||
-      !(prm.restart_tau_balance >= 0.0 && prm.restart_tau_balance <= 1.0) || prm.tiling < 0 || prm.tiling > 8)
+      !(prm.restart_tau_balance >= 0.0 && prm.restart_tau_balance <= 1.0) || prm.tiling < 0 || prm.tiling > 9)
     return SPFOM_EINVAL;
   spfom_ctx* ctx = new (std::nothrow) spfom_ctx;
   if (!ctx) return SPFOM_ENOMEM;
@@ -669,8 +677,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       }
       const bool dd = ctx->p.path == 2 && spfom::dd_setup(&plan, ctx->sms);
       // row-exact copy for the precision-64 tiling 4 (single instances, path 0)
-      if (!(ctx->p.path == 0 && !ctx->loading_batch && L > 0 && ctx->p.precision == 64 &&
-            spfom::rows_plan(n, ctx->sms, &plan)))
+      if (!(ctx->p.path == 0 && !ctx->loading_batch && L > 0 && spfom::rows_plan(n, ctx->sms, &plan)))
         plan.rows_ok = 0;
       W.plan = plan;
       W.fx_scale = std::ldexp(1.0, F);
@@ -694,10 +701,12 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       W.plan.sl_ok = ctx->p.path == 0 && !ctx->loading_batch && L > 0 && plan.sl_attr && plan.W8 <= 4 ? 1 : 0;
       if (ctx->p.tiling > 0) {  // a requested tiling of the active segment pass
         const int t = ctx->p.tiling;
-        bool ok = t <= 8;
+        bool ok = t <= 9;
         if (ok && ctx->p.precision == 32) {
           ok = (t != 2 || W.plan.tma_ok) && (t != 4 || W.plan.coop_ok) && (t != 6 || W.plan.bchunk_ok) &&
-               (t != 7 || W.plan.ms_ok) && (t != 8 || W.plan.sl_ok) && (t != 5 || kmax <= 32);
+               (t != 7 || W.plan.ms_ok) && (t != 8 || W.plan.sl_ok) && (t != 5 || kmax <= 32) &&
+               (t != 9 || W.plan.rows_ok);
+          W.plan.f32_rows = t == 9 ? 1 : 0;
           W.plan.bchunk = t == 6 ? 1 : 0;
           W.plan.tma = t == 2 ? 1 : 0;
           W.plan.f32_p8 = t == 3 ? 1 : 0;
@@ -708,8 +717,9 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
         } else if (ok) {
           // double-float kernel: its tilings 1..3; binary64-sum kernel: 1 = margins read
           // from global memory, 2 = margins in shared memory, 3 = slot-major copy
-          ok = dd ? spfom::dd_variant_ok(W.plan, t) != 0
-                  : (t == 1 || (t == 2 && W.plan.ms_ok) || (t == 3 && W.plan.sl_ok) || (t == 4 && W.plan.rows_ok));
+          ok = t <= 8 && (dd ? spfom::dd_variant_ok(W.plan, t) != 0
+                             : (t == 1 || (t == 2 && W.plan.ms_ok) || (t == 3 && W.plan.sl_ok) ||
+                                (t == 4 && W.plan.rows_ok)));
           if (dd) {
             W.plan.dd_variant = t;
           } else {
@@ -726,7 +736,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       if (plan.scatter == 1)
         SPFOM_TRY(dalloc(ctx, &W.part, (size_t)W.zparts_iter * (size_t)(n > 0 ? n : 1)));
       SPFOM_TRY(dalloc(ctx, &W.s_fx, (size_t)n));
-      if (W.plan.rows_ok) SPFOM_TRY(dalloc(ctx, &W.marg32c, (size_t)(n > 0 ? n : 1)));
+      if (W.plan.rows_ok && ctx->p.precision == 64) SPFOM_TRY(dalloc(ctx, &W.marg32c, (size_t)(n > 0 ? n : 1)));
       SPFOM_TRY(dalloc(ctx, &W.rprev, (size_t)(L > 0 ? L : 1)));
       SPFOM_CUDA(ctx, cudaMemsetAsync(W.rprev, 0, sizeof(float) * (size_t)(L > 0 ? L : 1), ctx->stream));
     }
@@ -794,7 +804,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
     const spfom_status st = build_sliced(ctx);
     if (st != SPFOM_OK) { free_instance(ctx); return st; }
   }
-  if (W.fast && W.plan.fast_rows) {  // the requested row-exact tiling
+  if (W.fast && (W.plan.fast_rows || W.plan.f32_rows)) {  // the requested row-exact tiling
     const spfom_status st = build_rows(ctx);
     if (st != SPFOM_OK) { free_instance(ctx); return st; }
   }
@@ -1269,7 +1279,8 @@ spfom_status spfom_update(spfom_ctx* ctx, const double* c, const double* lam) {
       if (e != cudaSuccess) return cuda_fail(ctx, e, "slot-major copy");
     }
     if (ctx->W.rx.nchunks > 0) {  // lambda of the row-exact copy
-      cudaError_t e = spfom::launch_rows_segments(P, ctx->W.rx, ctx->W.rx_perm, ctx->stream);
+      cudaError_t e = spfom::launch_rows_segments(P, ctx->W.rx, ctx->W.rx_perm, ctx->W.lam32, ctx->W.vt0_32,
+                                                  ctx->stream);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "row-exact copy");
     }
   }
@@ -1336,7 +1347,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   const bool dd = ctx->W.fast && ctx->W.v2 && !ctx->cfg.f32;
   const bool f64 = ctx->W.fast && !ctx->cfg.f32 && !dd;
   auto current = [&]() {
-    return f32 ? (plan.f32_sl ? 8 : plan.f32_ms ? 7
+    return f32 ? (plan.f32_rows ? 9 : plan.f32_sl ? 8 : plan.f32_ms ? 7
                               : (plan.bchunk ? 6
                                              : (plan.f32_p16 ? 5
                                                              : (plan.coop ? 4 : (plan.tma ? 2 : (plan.f32_p8 ? 3 : 1))))))
@@ -1349,6 +1360,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   auto available = [&](int c) {
     if (f32 && c == 7) return plan.ms_ok != 0;
     if (f32 && c == 8) return ctx->W.sl.nchunks > 0;
+    if (f32 && c == 9) return ctx->W.rx.nchunks > 0;
     if (f64)
       return c == 1 || (c == 2 && plan.ms_ok != 0) || (c == 3 && ctx->W.sl.nchunks > 0) ||
              (c == 4 && ctx->W.rx.nchunks > 0);
@@ -1366,6 +1378,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
       plan.bchunk = c == 6 ? 1 : 0;
       plan.f32_ms = c == 7 ? 1 : 0;
       plan.f32_sl = c == 8 ? 1 : 0;
+      plan.f32_rows = c == 9 ? 1 : 0;
     } else if (dd) {
       plan.dd_variant = c;
     } else {
@@ -1383,7 +1396,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
     const spfom_status sb = build_sliced(ctx);
     if (sb != SPFOM_OK) return sb;
   }
-  if (f64 && plan.rows_ok) {  // and the row-exact candidate its own
+  if ((f32 || f64) && plan.rows_ok && !ctx->W.batch) {  // and the row-exact candidate its own
     const spfom_status sb = build_rows(ctx);
     if (sb != SPFOM_OK) return sb;
   }
@@ -1396,7 +1409,7 @@ extern "C" spfom_status spfom_autotune(spfom_ctx* ctx, int32_t iters, int32_t* c
   ctx->cfg.kkt_tol = -1.0;  // no instance may converge (and stop working) while being timed
   double best = INFINITY;
   int choice = current();
-  for (int cand = 1; cand <= 8; ++cand) {
+  for (int cand = 1; cand <= 9; ++cand) {
     if (!available(cand)) continue;
     select(cand);
     drop_graphs(ctx);

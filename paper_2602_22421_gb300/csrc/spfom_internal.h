@@ -131,6 +131,7 @@ struct FastPlan {
   int rows_ms;        // 1: k_seg_rows keeps the binary32 margin images in shared memory (12 n bytes)
   int rows_grid, rows_smem;
   int rows_redo_grid;  // blocks of k_rows_redo (the SM count)
+  int f32_rows;        // 1: the binary32 pass runs k_seg_rows32 on the row-exact copy (tiling 9)
 };
 
 // Slot-major copy of the consideration sets (the sliced tilings): positions
@@ -327,6 +328,7 @@ struct F32Args {
   const int* bc_prod_ptr;    // [instances + 1] product offsets
   SlView sl;                 // slot-major copy (sliced tilings)
   unsigned wait_limit;       // polls of a staged-copy wait before it gives up (k_seg_f32_tma)
+  SlView rx;                 // row-exact copy (precision-32 tiling 9, binary32 images)
 };
 
 struct RunConfig {
@@ -421,12 +423,16 @@ cudaError_t launch_slice_segments(const Problem& P, const Work& Wk, int W8, cuda
 // classes; returns the chunk count), the gather of the items and of lambda / vt_0
 long long rows_layout(const long long* seg_ptr, long long L, std::vector<long long>* perm,
                       std::vector<long long>* off, long long cls_c[6], long long cls_pos[6]);
-cudaError_t launch_rows_items(const Problem& P, const SlView& S, const long long* perm, cudaStream_t s);
-cudaError_t launch_rows_segments(const Problem& P, const SlView& S, const long long* perm, cudaStream_t s);
+cudaError_t launch_rows_items(const Problem& P, const SlView& S, const long long* perm, const float* v32,
+                              const float* vt32, cudaStream_t s);
+cudaError_t launch_rows_segments(const Problem& P, const SlView& S, const long long* perm, const float* lam32,
+                                 const float* vt0_32, cudaStream_t s);
 // row-exact segment kernel (spfom_segments_rows.cu)
 bool rows_plan(int n, int sms, FastPlan* plan);
 cudaError_t launch_seg_rows(const FastArgs& A, const FastPlan& plan, cudaStream_t s);
 // the binary64 redo of the segments the row-exact kernel did not certify (after it, into s_fx)
 cudaError_t launch_rows_redo(const FastArgs& A, int sms, cudaStream_t s);
+// the row-exact binary32 pass (precision-32 tiling 9)
+cudaError_t launch_seg_rows32(const F32Args& A, const FastPlan& plan, cudaStream_t s);
 
 }  // namespace spfom

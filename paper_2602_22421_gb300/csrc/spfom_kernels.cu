@@ -571,6 +571,11 @@ cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfi
     A.wait_limit = Wk.wait_limit;
     const bool bchunk = Wk.plan.bchunk && Wk.batch && Wk.bc_count > 0;
     const FastPlan& pl = Wk.plan;
+    if (!bchunk && !Wk.batch && pl.f32_rows && Wk.rx.nchunks > 0 && Wk.rx.v32) {
+      A.rx = Wk.rx;
+      *zparts_out = pl.rows_grid;
+      return launch_seg_rows32(A, pl, s);
+    }
     if (!bchunk && pl.f32_sl && Wk.sl.nchunks > 0) {
       *zparts_out = pl.ms_ok ? pl.ms_grid32 : pl.grid32;
       return launch_seg_f32(A, pl, s);

@@ -42,6 +42,8 @@
 // exact-arithmetic optimum.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "spfom_device.cuh"
 #include "spfom_internal.h"
 
@@ -418,6 +420,121 @@ __global__ void __launch_bounds__(MS ? kRowsMsThreads : kRowsThreads, MS ? 1 : k
   }
 }
 
+// ---- binary32 bulk pass (precision 32, tiling 9) --------------------------
+// The same row-exact layout and Dinkelbach iteration on binary32 copies of the
+// inputs (12 B per nonzero), without certificate or binary64 redo: the bulk
+// mode's decisions are its binary32 ones, as in k_seg_f32. Every slot's id and
+// v stay in registers, so nothing is read twice: q = lambda / (vt_0 + D) from
+// the final set's binary32 sum, and each chosen product's sales are the exact
+// product q v rounded once to fixed point.
+template <int W, int R>
+__device__ __forceinline__ void rows32_segment(const F32Args& A, const float* __restrict__ mg,
+                                               const int* __restrict__ sp, const float* __restrict__ vv,
+                                               const float* __restrict__ vtv, const SlView& S, long long pos,
+                                               unsigned gmask, unsigned long long* sums) {
+  int jv[R];
+  float vf[R], af[R], bf[R];
+  unsigned cand = 0;
+#pragma unroll
+  for (int p = 0; p < R; ++p) {
+    const int j = sp[32 * p];  // -1: padding (v = vt = 0)
+    const float v = vv[32 * p], t = vtv[32 * p];
+    const float m = mg[j >= 0 ? j : 0];
+    const bool c = j >= 0 && m > 0.f;
+    jv[p] = j;
+    vf[p] = v;
+    af[p] = c ? m * v : 0.f;
+    bf[p] = c ? t : 0.f;
+    cand |= c ? 1u << p : 0u;
+  }
+  const float vt0 = S.vt0_32[pos];
+  float* rp = S.rprev + pos;
+  float Rr = *rp, Dsel = 0.f;
+  unsigned sel = 0xffffffffu;
+#pragma unroll 1
+  for (int it = 0; it < R * W + 3; ++it) {
+    float N, D;
+    bool unused = true;
+    const unsigned s = dk_pass<R, false>(af, bf, cand, Rr, N, D, unused);
+    if (W == 1 ? s == sel : __all_sync(gmask, s == sel)) break;
+#pragma unroll
+    for (int o = W >> 1; o > 0; o >>= 1) {
+      N += __shfl_xor_sync(gmask, N, o, W);
+      D += __shfl_xor_sync(gmask, D, o, W);
+    }
+    Rr = __fdividef(N, vt0 + D);
+    sel = s;
+    Dsel = D;
+  }
+  if ((gmask & -gmask) == (1u << (threadIdx.x & 31))) *rp = Rr;
+  const float q = S.lam32[pos] / (vt0 + Dsel);
+#pragma unroll
+  for (int p = 0; p < R; ++p)
+    if ((sel >> p) & 1u) atomicAdd(sums + jv[p], fixed_product32(q, vf[p], A.fx_bits));
+}
+
+template <int W, int R>
+__device__ __forceinline__ void rows32_chunk(const F32Args& A, const float* mg, long long e, long long pos,
+                                             unsigned gmask, unsigned long long* sums) {
+  const SlView& S = A.rx;
+  rows32_segment<W, R>(A, mg, S.prod + e, S.v32 + e, S.vt32 + e, S, pos, gmask, sums);
+}
+
+template <int W, int R>
+__device__ __forceinline__ void rows32_dispatch_r(const F32Args& A, const float* mg, int rows, long long e,
+                                                  long long pos, unsigned gmask, unsigned long long* sums) {
+  if (rows == R) {
+    rows32_chunk<W, R>(A, mg, e, pos, gmask, sums);
+  } else if constexpr (R > rows_lo<W>()) {
+    rows32_dispatch_r<W, R - 1>(A, mg, rows, e, pos, gmask, sums);
+  }
+}
+
+template <int SC, int MS>
+__global__ void __launch_bounds__(MS ? kRowsMsThreads : kRowsThreads, MS ? 1 : kRowsMinBlocks) k_seg_rows32(F32Args A) {
+  extern __shared__ unsigned long long acc[];  // SC == 1: [n] fixed-point sums; MS: + [n] binary32 margins
+  if (A.st->converged) return;
+  const int n = A.n;
+  const float* mg = A.marg32;
+  if (SC == 1) {
+    float* smg = reinterpret_cast<float*>(acc + n);
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      acc[j] = 0ull;
+      if (MS) smg[j] = A.marg32[j];
+    }
+    if (MS) mg = smg;
+    __syncthreads();
+  }
+  unsigned long long* sums = SC == 1 ? acc : A.s_fx;
+  const SlView& S = A.rx;
+  const int wl = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < S.nchunks; c += nw) {
+    const long long o = S.off[c];
+    const int rows = (int)((S.off[c + 1] - o) >> 5);
+    int k = 0;
+    while (k < kRowsClasses - 1 && c >= S.cls_c[k + 1]) ++k;  // warp-uniform
+    const int W = 16 >> k;
+    const long long pos = S.cls_pos[k] + (c - S.cls_c[k]) * (32 / W) + wl / W;
+    const long long e = o + wl;
+    const unsigned gmask = W == 1 ? (1u << wl) : (((1u << W) - 1u) << (wl & ~(W - 1)));
+    switch (W) {
+      case 1: rows32_dispatch_r<1, rows_hi<1>()>(A, mg, rows, e, pos, gmask, sums); break;
+      case 2: rows32_dispatch_r<2, rows_hi<2>()>(A, mg, rows, e, pos, gmask, sums); break;
+      case 4: rows32_dispatch_r<4, rows_hi<4>()>(A, mg, rows, e, pos, gmask, sums); break;
+      case 8: rows32_dispatch_r<8, rows_hi<8>()>(A, mg, rows, e, pos, gmask, sums); break;
+      default: rows32_dispatch_r<16, rows_hi<16>()>(A, mg, rows, e, pos, gmask, sums); break;
+    }
+  }
+  // the iterate pass forms no segment values: the dual step takes sum_l z_l as sum_j m_j s_j
+  if (threadIdx.x == 0) A.zpart[blockIdx.x] = 0.0;
+  if (SC == 1) {
+    __syncthreads();
+    unsigned long long* dst = A.part + (size_t)blockIdx.x * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) dst[j] = acc[j];
+  }
+}
+
 template <class K>
 int rows_blocks(K kernel, int smem, int threads) {
   int nb = 0;
@@ -434,7 +551,8 @@ bool rows_plan(int n, int sms, FastPlan* plan) {
   plan->rows_redo_grid = sms;
   const long long sums = 8ll * n, ms = 12ll * n;
   if (ms <= kTmaMaxSmem) {  // sums and binary32 margins in shared memory, one 1024-thread block per SM
-    const int nb = rows_blocks(k_seg_rows<1, 1>, (int)ms, kRowsMsThreads);
+    const int nb = std::min(rows_blocks(k_seg_rows<1, 1>, (int)ms, kRowsMsThreads),
+                            rows_blocks(k_seg_rows32<1, 1>, (int)ms, kRowsMsThreads));
     if (nb >= 1) {
       plan->rows_ok = 1;
       plan->rows_ms = 1;
@@ -444,7 +562,8 @@ bool rows_plan(int n, int sms, FastPlan* plan) {
     }
   }
   if (sums <= kFastMaxSmem) {
-    const int nb = rows_blocks(k_seg_rows<1, 0>, (int)sums, kRowsThreads);
+    const int nb = std::min(rows_blocks(k_seg_rows<1, 0>, (int)sums, kRowsThreads),
+                            rows_blocks(k_seg_rows32<1, 0>, (int)sums, kRowsThreads));
     if (nb >= 1) {
       plan->rows_ok = 1;
       plan->rows_ms = 0;
@@ -453,7 +572,7 @@ bool rows_plan(int n, int sms, FastPlan* plan) {
       return true;
     }
   }
-  const int nb = rows_blocks(k_seg_rows<2, 0>, 0, kRowsThreads);
+  const int nb = std::min(rows_blocks(k_seg_rows<2, 0>, 0, kRowsThreads), rows_blocks(k_seg_rows32<2, 0>, 0, kRowsThreads));
   if (nb < 1) return false;
   plan->rows_ok = 1;
   plan->rows_ms = 0;
@@ -466,6 +585,13 @@ cudaError_t launch_seg_rows(const FastArgs& A, const FastPlan& pl, cudaStream_t 
   if (pl.rows_ms) k_seg_rows<1, 1><<<pl.rows_grid, kRowsMsThreads, pl.rows_smem, s>>>(A);
   else if (pl.rows_smem > 0) k_seg_rows<1, 0><<<pl.rows_grid, kRowsThreads, pl.rows_smem, s>>>(A);
   else k_seg_rows<2, 0><<<pl.rows_grid, kRowsThreads, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_seg_rows32(const F32Args& A, const FastPlan& pl, cudaStream_t s) {
+  if (pl.rows_ms) k_seg_rows32<1, 1><<<pl.rows_grid, kRowsMsThreads, pl.rows_smem, s>>>(A);
+  else if (pl.rows_smem > 0) k_seg_rows32<1, 0><<<pl.rows_grid, kRowsThreads, pl.rows_smem, s>>>(A);
+  else k_seg_rows32<2, 0><<<pl.rows_grid, kRowsThreads, 0, s>>>(A);
   return cudaGetLastError();
 }
 

@@ -81,7 +81,8 @@ __device__ __forceinline__ int rows_class(const SlView& S, long long c) {
   return k;
 }
 
-__global__ void k_rows_items(const Problem P, SlView S, const long long* __restrict__ perm) {
+__global__ void k_rows_items(const Problem P, SlView S, const long long* __restrict__ perm,
+                             const float* __restrict__ v32, const float* __restrict__ vt32) {
   const int wl = threadIdx.x & 31;
   const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long c = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < S.nchunks; c += nw) {
@@ -101,8 +102,14 @@ __global__ void k_rows_items(const Problem P, SlView S, const long long* __restr
       const long long e = o + 32ll * p + wl;
       const bool in = kk < K;
       S.prod[e] = in ? P.seg_prod[b + kk] : -1;
-      S.v[e] = in ? P.v[b + kk] : 0.0;
-      S.vt[e] = in ? P.vt[b + kk] : 0.0;
+      if (S.v) {
+        S.v[e] = in ? P.v[b + kk] : 0.0;
+        S.vt[e] = in ? P.vt[b + kk] : 0.0;
+      }
+      if (S.v32) {
+        S.v32[e] = in ? v32[b + kk] : 0.f;
+        S.vt32[e] = in ? vt32[b + kk] : 0.f;
+      }
     }
   }
 }
@@ -182,18 +189,20 @@ cudaError_t launch_slice_segments(const Problem& P, const Work& Wk, int W8, cuda
   return cudaGetLastError();
 }
 
-cudaError_t launch_rows_items(const Problem& P, const SlView& S, const long long* perm, cudaStream_t s) {
+cudaError_t launch_rows_items(const Problem& P, const SlView& S, const long long* perm, const float* v32,
+                              const float* vt32, cudaStream_t s) {
   if (S.nchunks <= 0) return cudaSuccess;
   const long long blocks = (S.nchunks + 7) / 8;  // 8 warps per block
-  k_rows_items<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(P, S, perm);
+  k_rows_items<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(P, S, perm, v32, vt32);
   return cudaGetLastError();
 }
 
-cudaError_t launch_rows_segments(const Problem& P, const SlView& S, const long long* perm, cudaStream_t s) {
+cudaError_t launch_rows_segments(const Problem& P, const SlView& S, const long long* perm, const float* lam32,
+                                 const float* vt0_32, cudaStream_t s) {
   const long long npos = S.cls_pos[kRowsClasses];
   if (S.nchunks <= 0 || npos <= 0) return cudaSuccess;
   const long long blocks = (npos + 255) / 256;
-  k_slice_segments<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(P, nullptr, nullptr, S,
+  k_slice_segments<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(P, lam32, vt0_32, S,
                                                                                            perm, npos);
   return cudaGetLastError();
 }

@@ -468,14 +468,14 @@ FP32_ERRORS = {}
 
 
 @pytest.mark.parametrize("name", ["mid_small", "wide", "edge"])
-def test_fp32_bulk_error_against_fp64_oracle(name):
+def test_fp32_bulk_error_against_fp64_oracle(name, tiling=0):
     """Binary32 segment solves with binary64 residuals: the error against the
     FP64 oracle is reported per result (FP32_ERRORS) and bounded: one iteration
     from y = 0 is within binary32 rounding; after 200 iterations the iterates
     stay close although binary32 decisions near ties may differ."""
     inst = CASES[name]()
     run = Oracle(inst).run(OracleParams())
-    with Solver(inst, precision=32) as s:
+    with Solver(inst, precision=32, tiling=tiling) as s:
         st = s.step(1)
         run.step(1)
         assert st["iter_precision"] == 32 and st["fast_path"] == 1
@@ -590,11 +590,11 @@ def test_tilings_equal_plain_loads(name, precision, plain, shared):
     assert out[plain][2]["z_sum"] == pytest.approx(out[shared][2]["z_sum"], rel=1e-6 if precision == 32 else 1e-12)
 
 
-@pytest.mark.parametrize("tiling", [1, 3, 5, 7, 8])
+@pytest.mark.parametrize("tiling", [1, 3, 5, 7, 8, 9])
 def test_fp32_tilings_solve_to_the_binary64_objective(tiling):
-    """Each plain-load binary32 tiling (4, 8 or 16 products per lane) solves
-    the mid-size instance to KKT <= 1e-4 (with binary64 polish) at the
-    binary64 solve's objective."""
+    """Each plain-load binary32 tiling (4, 8 or 16 products per lane, the
+    slot-major and the row-exact copies) solves the mid-size instance to KKT
+    <= 1e-4 (with binary64 polish) at the binary64 solve's objective."""
     inst = mid_small()
     with Solver(inst) as s:
         ref = s.solve()
@@ -602,3 +602,11 @@ def test_fp32_tilings_solve_to_the_binary64_objective(tiling):
         st = s.solve()
     assert st["converged"] == 1 and st["kkt"] <= 1e-4
     assert st["dual_avg"] == pytest.approx(ref["dual_avg"], rel=1e-4)
+
+
+@pytest.mark.parametrize("name", ["mid_small", "wide", "edge"])
+def test_fp32_row_exact_error_against_fp64_oracle(name):
+    """The row-exact binary32 pass (tiling 9) keeps the bulk mode's error bounds
+    against the FP64 oracle (one iteration within binary32 rounding, 200
+    iterations close)."""
+    test_fp32_bulk_error_against_fp64_oracle(name, tiling=9)
