@@ -162,6 +162,17 @@ def code_digest(path):
     return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
+def kernel_of(precision, path, fast_path, tiling):
+    """Name and source file of the iterate pass's segment kernel."""
+    if precision == 32:
+        return ("k_seg_rows32", "spfom_segments_rows.cu") if tiling == 9 else ("k_seg_f32", "spfom_segments_fast.cu")
+    if not fast_path:
+        return "k_segments", "spfom_kernels.cu"
+    if path == 2:
+        return "k_seg_dd", "spfom_segments_dd.cu"
+    return ("k_seg_rows", "spfom_segments_rows.cu") if tiling == 4 else ("k_seg_fast", "spfom_segments_fast.cu")
+
+
 def kernel_traffic(kernel, tiling, src, nnz):
     """DRAM bytes per launch of `kernel` in `tiling` from the committed ncu
     summary, if it was taken on the current kernel source; scaled by nonzeros."""
@@ -314,15 +325,9 @@ def run_gpu(args):
             per_launch = pst["seg_kernel_seconds"] / max(1, pst["seg_kernel_launches"])
             if precision == 32:
                 alg = BYTES_PER_NNZ_F32 * inst.nnz + BYTES_PER_SEGMENT_F32 * inst.L
-                kname, ksrc = "k_seg_f32", "spfom_segments_fast.cu"
             else:
                 alg = BYTES_PER_NNZ * inst.nnz + BYTES_PER_SEGMENT * inst.L
-                if not pst["fast_path"]:
-                    kname, ksrc = "k_segments", "spfom_kernels.cu"
-                elif path == 2:
-                    kname, ksrc = "k_seg_dd", "spfom_segments_dd.cu"
-                else:
-                    kname, ksrc = "k_seg_fast", "spfom_segments_fast.cu"
+            kname, ksrc = kernel_of(precision, path, pst["fast_path"], tiling)
             peak, src = measured_peaks()
             achieved = alg / per_launch / 1e9
             traffic, cap = kernel_traffic(kname, tiling, ksrc, inst.nnz)
@@ -365,9 +370,9 @@ def run_gpu(args):
     e2e = None
     if not args.no_e2e:
         pinned = pinned_arrays(inst)
-        # the measured tiling, except the slot-major copy (built anew by every load):
-        # then the shared-margin tiling, within about 1 % of it per iteration
-        e2e_tiling = 2 if m64["tiling"] == 3 else m64["tiling"]
+        # the measured tiling, except the slot-major and row-exact copies (each load would
+        # build them anew, a host sort of the segments by size): then the shared-margin tiling
+        e2e_tiling = 2 if m64["tiling"] in (3, 4) else m64["tiling"]
         se = Solver(None, stream=stream.cuda_stream, device=local, kkt_tol=0.0, tiling=e2e_tiling)
         ysink = np.empty(inst.m)
         se.load(pinned)
@@ -416,17 +421,16 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def roofline_of(s_prof, inst, precision, ips, steps):
+def roofline_of(s_prof, inst, precision, ips, steps, tiling=0):
     """Segment-kernel roofline of a profiled solver (the per-launch time of the
     iterate pass from its CUDA event pairs)."""
     pst = s_prof.step(steps * ips)
     per_launch = pst["seg_kernel_seconds"] / max(1, pst["seg_kernel_launches"])
     if precision == 32:
         alg = BYTES_PER_NNZ_F32 * inst.nnz + BYTES_PER_SEGMENT_F32 * inst.L
-        kname = "k_seg_f32"
     else:
         alg = BYTES_PER_NNZ * inst.nnz + BYTES_PER_SEGMENT * inst.L
-        kname = "k_seg_fast" if pst["fast_path"] else "k_segments"
+    kname = kernel_of(precision, 0, pst["fast_path"], tiling)[0]
     peak, src = measured_peaks()
     achieved = alg / per_launch / 1e9
     return {"bound": "hbm", "kernel": kname + " (iterate)", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -462,7 +466,7 @@ def paper_shaped_leg(args, stream, local):
         sp = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, profile=1, precision=precision,
                     tiling=tiling)
         sp.step(ips)
-        roof = roofline_of(sp, inst, precision, ips, 2)
+        roof = roofline_of(sp, inst, precision, ips, 2, tiling)
         sp.close()
         out[f"f{precision}"] = {"value": 4 * ips / (ms * 1e-3), "unit": "iters/s", "tiling": tiling,
                                 "ms_per_iter": ms / (4 * ips), "roofline": roof}
@@ -501,7 +505,7 @@ def huge_leg(args, stream, local):
         sp = Solver(inst, stream=stream.cuda_stream, device=local, kkt_tol=0.0, profile=1, precision=precision,
                     tiling=tiling)
         sp.step(ips)
-        roof = roofline_of(sp, inst, precision, ips, 2)
+        roof = roofline_of(sp, inst, precision, ips, 2, tiling)
         sp.close()
         out[f"f{precision}"] = {"value": args.huge_steps * ips / (ms * 1e-3), "unit": "iters/s", "tiling": tiling,
                                 "ms_per_iter": ms / (args.huge_steps * ips), "load_seconds": load_s,
