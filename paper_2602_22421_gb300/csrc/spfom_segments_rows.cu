@@ -64,15 +64,18 @@ constexpr int kRowsThreads = SPFOM_ROWS_THREADS;     // block of the kernel with
 constexpr int kRowsMinBlocks = SPFOM_ROWS_MINB;      // its blocks per SM (register budget)
 constexpr int kRowsMsThreads = SPFOM_ROWS_MS_THREADS;  // block of the shared-margins kernel (one per SM)
 
-// round(x 2^G) for binary64 x >= 0 with x 2^G < 2^62 (integer operations only).
+// round(x 2^G) for binary64 x >= 0 with x 2^G < 2^62 (integer operations only,
+// no branch: shift counts are clamped and the cases chosen by selects).
 __device__ __forceinline__ long long fx_of(double x, int G) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int e = (int)(u >> 52);
   const unsigned long long m = (u & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
   const int sh = 1075 - G - e;  // x 2^G = m 2^-sh
-  if (e == 0 || sh > 63) return 0;
-  if (sh <= 0) return (long long)(m << -sh);
-  return (long long)((m + (1ull << (sh - 1))) >> sh);
+  const int r = sh < 1 ? 1 : (sh > 63 ? 63 : sh);
+  const unsigned long long down = (m + (1ull << (r - 1))) >> r;
+  const unsigned long long up = m << (sh < 0 ? (-sh > 63 ? 63 : -sh) : 0);
+  const unsigned long long v = sh <= 0 ? up : down;
+  return (e == 0 || sh > 63) ? 0ll : (long long)v;
 }
 
 // round(q v 2^F) for positive normal binary64 q, v (q v 2^F < 2^62), with q's
@@ -115,9 +118,11 @@ __device__ __forceinline__ RowsPos rows_pos(const SlView& S, long long pos) {
   return r;
 }
 
-// One Dinkelbach pass over a lane's R slots at ratio Rr: the set {a_j > Rr b_j}
-// of the candidates, with the sums of a and b over it (two interleaved partial
-// sums each); CERT also tests every candidate against the certificate margin.
+// One Dinkelbach pass over a lane's R slots at ratio Rr: the set {a_j > Rr b_j},
+// with the sums of a and b over it (two interleaved partial sums each). Slots
+// that are not candidates hold a = b = 0 and never enter (0 > Rr 0 is false),
+// so the pass needs no candidate mask; CERT also tests every candidate
+// against the certificate margin.
 template <int R, bool CERT>
 __device__ __forceinline__ unsigned dk_pass(const float (&af)[R], const float (&bf)[R], unsigned cand, float Rr,
                                             float& N, float& D, bool& cert) {
@@ -126,15 +131,15 @@ __device__ __forceinline__ unsigned dk_pass(const float (&af)[R], const float (&
 #pragma unroll
   for (int p = 0; p < R; ++p) {
     const float a = af[p], c = Rr * bf[p];
-    const bool in = ((cand >> p) & 1u) && a > c;
-    s |= in ? 1u << p : 0u;
-    const float ai = in ? a : 0.f, bi = in ? bf[p] : 0.f;
-    if (p & 1) {
-      N1 += ai;
-      D1 += bi;
-    } else {
-      N0 += ai;
-      D0 += bi;
+    if (a > c) {
+      s |= 1u << p;
+      if (p & 1) {
+        N1 += a;
+        D1 += bf[p];
+      } else {
+        N0 += a;
+        D0 += bf[p];
+      }
     }
     if (CERT) cert &= !((cand >> p) & 1u) || fabsf(a - c) > kCertDelta * (a + c);
   }
@@ -427,6 +432,22 @@ __global__ void __launch_bounds__(MS ? kRowsMsThreads : kRowsThreads, MS ? 1 : k
 // v stay in registers, so nothing is read twice: q = lambda / (vt_0 + D) from
 // the final set's binary32 sum, and each chosen product's sales are the exact
 // product q v rounded once to fixed point.
+// round(q v 2^F) for non-negative binary32 q, v with q v 2^F < 2^62, q's
+// significand mq (24 bits) and biased exponent eq decoded once per segment:
+// the 48-bit product of the significands is exact, so the only rounding is the
+// final one (no branch: shift counts clamped, cases chosen by selects).
+__device__ __forceinline__ unsigned long long fixed32_q(unsigned mq, int eq, float v, int F) {
+  const unsigned uv = __float_as_uint(v);
+  const int ev = (int)(uv >> 23);
+  const unsigned long long prod = (unsigned long long)mq * (unsigned long long)((uv & 0x7FFFFFu) | 0x800000u);
+  const int sh = 300 - F - eq - ev;  // q v 2^F = prod / 2^sh
+  const int r = sh < 1 ? 1 : (sh > 63 ? 63 : sh);
+  const unsigned long long down = (prod + (1ull << (r - 1))) >> r;
+  const unsigned long long up = prod << (sh < 0 ? (-sh > 63 ? 63 : -sh) : 0);
+  const unsigned long long x = sh <= 0 ? up : down;
+  return (eq == 0 || ev == 0 || sh > 63) ? 0ull : x;
+}
+
 template <int W, int R>
 __device__ __forceinline__ void rows32_segment(const F32Args& A, const float* __restrict__ mg,
                                                const int* __restrict__ sp, const float* __restrict__ vv,
@@ -468,9 +489,12 @@ __device__ __forceinline__ void rows32_segment(const F32Args& A, const float* __
   }
   if ((gmask & -gmask) == (1u << (threadIdx.x & 31))) *rp = Rr;
   const float q = S.lam32[pos] / (vt0 + Dsel);
+  const unsigned uq = __float_as_uint(q);
+  const unsigned mq = (uq & 0x7FFFFFu) | 0x800000u;
+  const int eq = (int)(uq >> 23);
 #pragma unroll
   for (int p = 0; p < R; ++p)
-    if ((sel >> p) & 1u) atomicAdd(sums + jv[p], fixed_product32(q, vf[p], A.fx_bits));
+    if ((sel >> p) & 1u) atomicAdd(sums + jv[p], fixed32_q(mq, eq, vf[p], A.fx_bits));
 }
 
 template <int W, int R>
