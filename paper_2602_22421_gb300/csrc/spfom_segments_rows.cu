@@ -470,22 +470,34 @@ __device__ __forceinline__ void rows32_segment(const F32Args& A, const float* __
   }
   const float vt0 = S.vt0_32[pos];
   float* rp = S.rprev + pos;
-  float Rr = *rp, Dsel = 0.f;
-  unsigned sel = 0xffffffffu;
-#pragma unroll 1
-  for (int it = 0; it < R * W + 3; ++it) {
-    float N, D;
-    bool unused = true;
-    const unsigned s = dk_pass<R, false>(af, bf, cand, Rr, N, D, unused);
-    if (W == 1 ? s == sel : __all_sync(gmask, s == sel)) break;
+  // Dinkelbach from the carried ratio: the first two passes are straight-line
+  // code (the second confirms almost every set: the margins move little between
+  // iterations); the rare remaining segments go on in a loop
+  float N, D;
+  bool unused = true;
+  unsigned sel = dk_pass<R, false>(af, bf, cand, *rp, N, D, unused);
 #pragma unroll
-    for (int o = W >> 1; o > 0; o >>= 1) {
-      N += __shfl_xor_sync(gmask, N, o, W);
-      D += __shfl_xor_sync(gmask, D, o, W);
+  for (int o = W >> 1; o > 0; o >>= 1) {
+    N += __shfl_xor_sync(gmask, N, o, W);
+    D += __shfl_xor_sync(gmask, D, o, W);
+  }
+  float Rr = __fdividef(N, vt0 + D), Dsel = D;
+  unsigned s2 = dk_pass<R, false>(af, bf, cand, Rr, N, D, unused);
+  if (!(W == 1 ? s2 == sel : __all_sync(gmask, s2 == sel))) {
+    sel = s2;
+#pragma unroll 1
+    for (int it = 0; it < R * W + 2; ++it) {
+#pragma unroll
+      for (int o = W >> 1; o > 0; o >>= 1) {
+        N += __shfl_xor_sync(gmask, N, o, W);
+        D += __shfl_xor_sync(gmask, D, o, W);
+      }
+      Rr = __fdividef(N, vt0 + D);
+      Dsel = D;
+      const unsigned s = dk_pass<R, false>(af, bf, cand, Rr, N, D, unused);
+      if (W == 1 ? s == sel : __all_sync(gmask, s == sel)) break;
+      sel = s;
     }
-    Rr = __fdividef(N, vt0 + D);
-    sel = s;
-    Dsel = D;
   }
   if ((gmask & -gmask) == (1u << (threadIdx.x & 31))) *rp = Rr;
   const float q = S.lam32[pos] / (vt0 + Dsel);
