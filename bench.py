@@ -563,7 +563,7 @@ def batched_leg(args, local):
         insts = list(pool.map(batch_base, [4] * count, range(count)))
     gen_s = time.perf_counter() - t0
     rho = period_rates(4, count, args.periods)
-    prm = dict(restart_tau_balance=0.5, max_iters=40000)
+    prm = dict(restart_tau_balance=0.5, restart_tau_decay=0.9, max_iters=40000)
     summary, path, per = PR.run_batched(insts, rho, periods=args.periods, precision=32, **prm)
     batched_s = sum(r["seconds"] for r in summary["records"])
     if args.seq_sample and args.seq_sample < count:
