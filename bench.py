@@ -566,6 +566,11 @@ def batched_leg(args, local):
     prm = dict(restart_tau_balance=0.5, restart_tau_decay=0.9, max_iters=40000)
     summary, path, per = PR.run_batched(insts, rho, periods=args.periods, precision=32, **prm)
     batched_s = sum(r["seconds"] for r in summary["records"])
+    # the same periods with each solve phase as one launch (device-side loop over evaluation periods)
+    loop_summary, _, loop_per = PR.run_batched(insts, rho, periods=args.periods, precision=32, device_loop=1, **prm)
+    loop_s = sum(r["seconds"] for r in loop_summary["records"])
+    loop_same = all(a["iters"] == b["iters"] and a["converged"] == b["converged"]
+                    for pa, pb in zip(per, loop_per) for a, b in zip(pa, pb))
     if args.seq_sample and args.seq_sample < count:
         which = sorted(np.random.default_rng(7).choice(count, args.seq_sample, replace=False).tolist())
     else:
@@ -582,6 +587,11 @@ def batched_leg(args, local):
             "solver_params": prm,
             "instances": count, "periods": args.periods, "nnz_total": nnz_all, "generate_seconds": gen_s,
             "batched_seconds": batched_s, "batched_load_seconds": summary["load_seconds"],
+            "device_loop": {"batched_seconds": loop_s, "periods_converged":
+                            sum(r["converged"] for r in loop_summary["records"]),
+                            "same_members_iterations_as_period_by_period": loop_same,
+                            "note": "each solve phase one graph launch: a conditional WHILE node replays the "
+                                    "evaluation period until the device-side test ends the phase"},
             "autotune_choice": summary["autotune_choice"],
             "periods_converged": sum(r["converged"] for r in summary["records"]),
             "batched_iterations_per_period": [r["iters"] for r in summary["records"]],

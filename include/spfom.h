@@ -102,8 +102,17 @@ typedef struct {
                                 nonzero read and written each iteration); needs precision 64,
                                 batch_frac 1 and a single instance, and runs the general kernel */
   int32_t tiling;            /* 0 (default): tiling 1 of the active segment pass until
-                                spfom_autotune picks one; 1..8: that tiling (see spfom_autotune),
-                                ENOTSUP at load when the instance does not allow it */
+                                spfom_autotune picks one; 1..9: that tiling (see spfom_autotune;
+                                precision 32: 1..9, precision 64: 1..4 with path 0, 1..3 with
+                                path 2), ENOTSUP at load when the instance does not allow it */
+  int32_t device_loop;       /* 0 (default): spfom_solve enqueues one evaluation period (a CUDA
+                                graph) per host round trip; 1: each phase of spfom_solve is one
+                                graph launch whose conditional WHILE node replays the period on
+                                the device until a device-side test ends the phase (convergence,
+                                the iteration cap, or in a binary32 batch the switch to binary64
+                                iterations when at most 5 % of the members are left); needs
+                                graphs = 1 and eval_every > 0, and a remainder of max_iters below
+                                eval_every runs as before */
   void* stream;              /* cudaStream_t to run on; NULL (default): the ctx creates one */
 } spfom_params;
 
@@ -293,12 +302,20 @@ spfom_status spfom_set_wait_limit(spfom_ctx* ctx, uint32_t polls);
  * per SM; needs 16 n bytes of shared memory, n <= 14464),
  * 8 = a slot-major copy of the consideration sets built at load (segments
  * sorted by set size, 32-entry slot rows per warp; margins in shared memory
- * when they fit) -- batches do not try 2, 4 (the staged kernels load the
- * tiles of converged members too) and 8 (single instances only);
+ * when they fit), 9 = the row-exact copy (segments sorted by set size; lanes
+ * per segment from the set size: one lane for sets of <= 8 products, then 2,
+ * 4, 8 or 16; each chunk of a warp holds exactly as many 32-entry slot rows
+ * as its largest set needs, and the kernel is specialised per lane count and
+ * row count; binary32 margins in shared memory when 12 n bytes fit) -- batches
+ * do not try 2, 4 (the staged kernels load the tiles of converged members
+ * too), 8 and 9 (single instances only);
  * precision 64 with path 0: 1 = margins read from global memory (two
  * 512-thread blocks per SM), 2 = margins copied into shared memory (one
  * 1024-thread block per SM, n <= 14464), 3 = the slot-major copy (single
- * instances);
+ * instances), 4 = the row-exact copy as in 9 above with binary64 v and v - w
+ * (single instances; D* is summed exactly as integers, and the segments whose
+ * binary32 decision is not certified are redone in binary64 by a second small
+ * kernel after the pass);
  * precision 64 with path 2: 1 = 8 products per lane at two 512-thread blocks per
  * SM, 2 = 8 per lane at three blocks per SM, 3 = 4 per lane at three blocks
  * per SM. *choice_out (or NULL) gets the choice (1 when there is none). */

@@ -45,6 +45,8 @@ struct spfom_ctx {
   bool polishing = false;  // precision 32: binary64 iterations after the first converged evaluation
   cudaGraphExec_t period[2] = {nullptr, nullptr};  // one evaluation period, [binary64, binary32 pass]
   bool period_failed = false;                      // capture unavailable on this stream
+  cudaGraphExec_t loop[2] = {nullptr, nullptr};    // device loop over periods (params.device_loop)
+  spfom::DevLoop* d_loop = nullptr;                // its state (device, per loaded instance)
   // batch (spfom_load_batch)
   struct BatchSpec {
     int count;
@@ -89,6 +91,11 @@ void drop_graphs(spfom_ctx* ctx) {
       cudaGraphExecDestroy(g);
       g = nullptr;
     }
+  for (auto& g : ctx->loop)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
   ctx->period_failed = false;
 }
 
@@ -98,6 +105,7 @@ void free_instance(spfom_ctx* ctx) {
   ctx->bufs.clear();
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   ctx->loaded = false;
+  ctx->d_loop = nullptr;  // freed with the instance's buffers
   ctx->P = Problem{};
   Work w{};
   w.st = ctx->W.st;
@@ -911,6 +919,46 @@ cudaGraphExec_t capture_period(spfom_ctx* ctx) {
   return ok ? ex : nullptr;
 }
 
+// One graph whose conditional WHILE node replays the evaluation period (the
+// iterations and the evaluation of capture_period) followed by the test
+// kernel, which sets the node's condition on the device: a whole phase of
+// spfom_solve runs without a host round trip.
+cudaGraphExec_t capture_loop(spfom_ctx* ctx) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  if (cudaGraphCreate(&g, 0) != cudaSuccess) return nullptr;
+  bool ok = true;
+  cudaGraphConditionalHandle h{};
+  ok = cudaGraphConditionalHandleCreate(&h, g, 1u, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = h;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t node{};
+  if (ok) ok = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp) == cudaSuccess;
+  if (ok) {
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    ok = cudaStreamBeginCaptureToGraph(ctx->stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+         cudaSuccess;
+    if (ok) {
+      for (long long k = 0; k < ctx->p.eval_every && ok; ++k)
+        ok = spfom::launch_iteration(ctx->P, ctx->W, ctx->cfg, ctx->stream) == cudaSuccess;
+      if (ok) ok = spfom::launch_eval(ctx->P, ctx->W, ctx->cfg, ctx->stream) == cudaSuccess;
+      if (ok) ok = spfom::launch_loop_test(ctx->W, ctx->d_loop, h, (int)ctx->p.eval_every, ctx->stream) == cudaSuccess;
+      cudaGraph_t cap = nullptr;
+      if (cudaStreamEndCapture(ctx->stream, &cap) != cudaSuccess) ok = false;
+    }
+  }
+  if (ok && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+    ok = false;
+    ex = nullptr;
+  }
+  cudaGraphDestroy(g);
+  cudaGetLastError();
+  return ok ? ex : nullptr;
+}
+
 }  // namespace
 
 spfom_status spfom_step(spfom_ctx* ctx, int64_t iters, spfom_stats* out) {
@@ -991,6 +1039,58 @@ spfom_status spfom_step(spfom_ctx* ctx, int64_t iters, spfom_stats* out) {
   return SPFOM_OK;
 }
 
+namespace {
+
+// One phase of spfom_solve as a single launch of the device-loop graph
+// (params.device_loop): evaluation periods until the device-side test ends the
+// phase. *used stays false (and nothing runs) when the loop does not apply:
+// device_loop off, graphs off or unavailable, profiling, less than one period
+// left, or the iteration count between periods.
+spfom_status run_loop(spfom_ctx* ctx, long long left, spfom_stats* out, bool* used) {
+  *used = false;
+  const long long E = ctx->p.eval_every;
+  if (!ctx->p.device_loop || !ctx->p.graphs || E <= 0 || ctx->p.profile || left < E || ctx->host_t % E != 0 ||
+      ctx->period_failed)
+    return SPFOM_OK;
+  SPFOM_CUDA(ctx, cudaSetDevice(ctx->p.device));
+  if (!ctx->d_loop) {
+    spfom_status a = dalloc(ctx, &ctx->d_loop, 1);
+    if (a != SPFOM_OK) return a;
+  }
+  spfom::DevLoop L{};
+  L.t = ctx->host_t;
+  L.t_end = ctx->host_t + left;
+  L.batch_switch = (ctx->W.batch && ctx->cfg.f32) ? 1 : 0;
+  SPFOM_CUDA(ctx, cudaMemcpyAsync(ctx->d_loop, &L, sizeof L, cudaMemcpyHostToDevice, ctx->stream));
+  cudaGraphExec_t& ex = ctx->loop[ctx->cfg.f32 ? 1 : 0];
+  if (!ex) ex = capture_loop(ctx);
+  if (!ex) return SPFOM_OK;  // conditional graphs unavailable: the caller steps period by period
+  SPFOM_CUDA(ctx, cudaEventRecord(ctx->ev0, ctx->stream));
+  SPFOM_CUDA(ctx, cudaGraphLaunch(ex, ctx->stream));
+  SPFOM_CUDA(ctx, cudaEventRecord(ctx->ev1, ctx->stream));
+  SPFOM_CUDA(ctx, cudaMemcpyAsync(&L, ctx->d_loop, sizeof L, cudaMemcpyDeviceToHost, ctx->stream));
+  DevState st;
+  spfom_status s = read_state(ctx, &st);  // synchronises the stream
+  if (s != SPFOM_OK) return s;
+  float ms = 0.f;
+  SPFOM_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+  const long long periods = (L.t - ctx->host_t) / E;
+  ctx->host_t = ctx->W.batch ? L.t : st.t;
+  fill_stats(ctx, st, ms * 1e-3, out);
+  *used = true;
+  if (st.error)
+    return fail(ctx, SPFOM_ETIMEOUT, "a bounded device wait (bulk-copy staging) gave up; results are invalid");
+  if (out) {
+    out->kernel_launches =
+        periods * (E * spfom::kernel_launches_per_iteration(ctx->W, ctx->cfg) + spfom::kernel_launches_per_eval() + 1);
+    out->seg_kernel_seconds = 0.0;
+    out->seg_kernel_launches = 0;
+  }
+  return SPFOM_OK;
+}
+
+}  // namespace
+
 spfom_status spfom_solve(spfom_ctx* ctx, const double* y0, spfom_stats* out) {
   spfom_status s = spfom_reset(ctx, y0);
   if (s != SPFOM_OK) return s;
@@ -1006,8 +1106,13 @@ spfom_status spfom_solve(spfom_ctx* ctx, const double* y0, spfom_stats* out) {
   for (;;) {
     long long left = ctx->p.max_iters - ctx->host_t;
     if (left <= 0) break;
-    s = spfom_step(ctx, left < E ? left : E, &st);
+    bool looped = false;
+    s = run_loop(ctx, left, &st, &looped);
     if (s != SPFOM_OK) return s;
+    if (!looped) {
+      s = spfom_step(ctx, left < E ? left : E, &st);
+      if (s != SPFOM_OK) return s;
+    }
     if (st.evals > 0 && std::isfinite(st.dual_avg)) {
       if (!(st.dual_avg >= best_dual - 1e-9 * std::fabs(best_dual))) {
         best_dual = st.dual_avg;

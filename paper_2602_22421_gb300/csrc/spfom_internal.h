@@ -372,6 +372,14 @@ cudaError_t launch_features(const Problem& P, const double* s0, double* d, doubl
 cudaError_t launch_warm_duals(int m, int n, const float* o, const double* totals, double* y, cudaStream_t s);
 int kernel_launches_per_iteration(const Work& Wk, const RunConfig& cfg);
 int kernel_launches_per_eval();
+// Device-side loop of spfom_solve (params.device_loop): state of one phase and
+// the test that ends it, launched by the body of a conditional WHILE graph node.
+struct DevLoop {
+  long long t, t_end;  // iterations done, and the phase's cap (batches: counted here)
+  int batch_switch;    // binary32 batch: end the phase when at most 5 % of the members are active
+  int ended;           // why the phase ended: 1 converged, 2 cap, 3 switch
+};
+cudaError_t launch_loop_test(const Work& Wk, DevLoop* lp, cudaGraphConditionalHandle h, int E, cudaStream_t s);
 
 // spfom_segments_fast.cu
 bool fast_plan(int n, int kmax, int sms, FastPlan* plan);

@@ -808,4 +808,38 @@ cudaError_t launch_prep_f32(const Problem& P, Work& Wk, cudaStream_t s) {
 }
 int kernel_launches_per_eval() { return 3; }  // single instance and batch alike
 
+namespace {
+// End of one evaluation period inside the device loop: count the period, and
+// keep looping unless the iteration has converged (every member of a batch),
+// the phase's cap is reached, or a binary32 batch is down to its last 5 % of
+// members (the host then switches to binary64 iterations).
+__global__ void k_loop_test(const Work Wk, DevLoop* lp, cudaGraphConditionalHandle h, int E) {
+  __shared__ int active;
+  if (threadIdx.x == 0) active = 0;
+  __syncthreads();
+  int conv = 0;
+  if (Wk.batch) {
+    int a = 0;
+    for (int b = threadIdx.x; b < Wk.bm.count; b += blockDim.x) a += Wk.bm.conv[b] ? 0 : 1;
+    atomicAdd(&active, a);
+    __syncthreads();
+    conv = active == 0;
+  } else {
+    conv = Wk.st->converged;
+  }
+  if (threadIdx.x != 0) return;
+  const long long t = Wk.batch ? lp->t + E : Wk.st->t;
+  lp->t = t;
+  int ended = conv ? 1 : (t + E > lp->t_end ? 2 : 0);
+  if (!ended && lp->batch_switch && (long long)active * 20 <= (long long)Wk.bm.count) ended = 3;
+  lp->ended = ended;
+  cudaGraphSetConditional(h, ended ? 0u : 1u);
+}
+}  // namespace
+
+cudaError_t launch_loop_test(const Work& Wk, DevLoop* lp, cudaGraphConditionalHandle h, int E, cudaStream_t s) {
+  k_loop_test<<<1, 256, 0, s>>>(Wk, lp, h, E);
+  return cudaGetLastError();
+}
+
 }  // namespace spfom

@@ -45,7 +45,7 @@ class Params(C.Structure):
                 ("device", C.c_int32), ("profile", C.c_int32), ("path", C.c_int32), ("pipeline", C.c_int32),
                 ("graphs", C.c_int32),
                 ("polish", C.c_int32), ("track_xbar", C.c_int32), ("tiling", C.c_int32),
-                ("stream", C.c_void_p)]
+                ("device_loop", C.c_int32), ("stream", C.c_void_p)]
 
 
 class InstanceC(C.Structure):

@@ -185,3 +185,38 @@ def test_instance_chunked_batch_kernel_equals_plain_loads():
     np.testing.assert_array_equal(out[3][0], out[6][0])
     np.testing.assert_array_equal(out[3][1], out[6][1])
     assert [p["restarts"] for p in out[3][3]] == [p["restarts"] for p in out[6][3]]
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_device_loop_equals_period_by_period_solve(precision):
+    """params.device_loop: each phase of the solve is one graph launch whose
+    conditional node replays the evaluation period until the device-side test
+    ends it. The kernels and their order are those of the period-by-period
+    solve, so a batch (binary32 phase, switch to binary64, confirmation) and a
+    single instance reach the same iterations, restarts and duals bit for bit;
+    a cap that is not a multiple of the evaluation period finishes on the host."""
+    from paper_2602_22421_gb300 import Solver
+    from instances import batch_base
+    insts = [batch_base(4, k) for k in (0, 2, 5, 100)]
+    out = {}
+    for loop in (0, 1):
+        with Solver(None, device=0, precision=precision, device_loop=loop, restart_tau_balance=0.5) as s:
+            s.load_batch(insts)
+            st = s.solve()
+            out[loop] = (st, s.batch_stats(), s.duals(averaged=True))
+    assert out[0][0]["converged"] == out[1][0]["converged"] == 1
+    assert out[0][0]["iters"] == out[1][0]["iters"]
+    for a, b in zip(out[0][1], out[1][1]):
+        assert (a["iters"], a["restarts"], a["converged"]) == (b["iters"], b["restarts"], b["converged"])
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+    inst = mid_gam(1, L=20_000, n=1000, m=200)
+    res = {}
+    for loop in (0, 1):
+        with Solver(inst, device=0, precision=precision, device_loop=loop, max_iters=1000) as s:
+            try:
+                st = s.solve()
+            except Exception:
+                st = s.stats()
+            res[loop] = (st["iters"], st["restarts"], st["converged"], s.duals())
+    assert res[0][:3] == res[1][:3]
+    np.testing.assert_array_equal(res[0][3], res[1][3])
