@@ -440,6 +440,9 @@ bool rows_plan(int n, int sms, FastPlan* plan);
 cudaError_t launch_seg_rows(const FastArgs& A, const FastPlan& plan, cudaStream_t s);
 // the binary64 redo of the segments the row-exact kernel did not certify (after it, into s_fx)
 cudaError_t launch_rows_redo(const FastArgs& A, int sms, cudaStream_t s);
+// with per-block sums: the fold of the partial sums and the redo in one launch
+cudaError_t launch_reduce_redo(const FastArgs& A, const FastPlan& plan, int nparts, const unsigned long long* part,
+                               cudaStream_t s);
 // the row-exact binary32 pass (precision-32 tiling 9)
 cudaError_t launch_seg_rows32(const F32Args& A, const FastPlan& plan, cudaStream_t s);
 

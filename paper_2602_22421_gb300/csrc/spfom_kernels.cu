@@ -628,14 +628,16 @@ cudaError_t launch_iteration(const Problem& P, const Work& Wk, const RunConfig& 
   }
   if (seg_end) cudaEventRecord(seg_end, s);
   if (e != cudaSuccess) return e;
-  if (fast) {
-    e = launch_reduce_products(P, Wk.plan, zparts, Wk.part, Wk.s_fx, Wk.st, s);
+  const bool rows = rows_active(Wk, cfg, sampled);  // segments the row-exact kernel left for binary64
+  FastArgs R{P, Wk.marg, nullptr, nullptr, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, Wk.s_fx};
+  R.rx = Wk.rx;
+  // the row-exact kernel keeps per-block sums exactly when it has shared memory for them (rows_smem)
+  if (rows) {
+    e = Wk.plan.rows_smem > 0 ? launch_reduce_redo(R, Wk.plan, zparts, Wk.part, s)
+                              : launch_rows_redo(R, Wk.plan.rows_redo_grid, s);
     if (e != cudaSuccess) return e;
-  }
-  if (rows_active(Wk, cfg, sampled)) {  // the segments the row-exact kernel left for binary64
-    FastArgs A{P, Wk.marg, nullptr, nullptr, Wk.st, Wk.fx_scale, Wk.fallbacks, Wk.fx_bits, Wk.s_fx};
-    A.rx = Wk.rx;
-    e = launch_rows_redo(A, Wk.plan.rows_redo_grid, s);
+  } else if (fast) {
+    e = launch_reduce_products(P, Wk.plan, zparts, Wk.part, Wk.s_fx, Wk.st, s);
     if (e != cudaSuccess) return e;
   }
   k_dual_step<<<gv, kVecThreads, 0, s>>>(P, Wk, cfg, sampled ? 0 : 1, zparts);
@@ -779,7 +781,8 @@ cudaError_t launch_recover(const Problem& P, const Work& Wk, const double* x, do
 int kernel_launches_per_iteration(const Work& Wk, const RunConfig& cfg) {
   if (Wk.batch) return batch_launches_per_iteration(Wk);
   if (!(Wk.fast && cfg.batch_frac >= 1.0)) return 3;
-  return (Wk.plan.scatter == 1 ? 4 : 3) + (rows_active(Wk, cfg, false) ? 1 : 0);
+  if (rows_active(Wk, cfg, false)) return 4;  // margins, row-exact pass, fold + redo (or redo), dual step
+  return Wk.plan.scatter == 1 ? 4 : 3;
 }
 
 namespace {

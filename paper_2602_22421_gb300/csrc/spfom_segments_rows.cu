@@ -254,12 +254,25 @@ __device__ __forceinline__ bool rows_segment(const FastArgs& A, const float* __r
   return true;
 }
 
+// Uncertified segments of a block: listed in shared memory and redone by the
+// block's own warps after its chunk loop; beyond kRedoLocal per block they go
+// to the global list (redone after the pass).
+constexpr int kRedoLocal = 64;
+__shared__ long long g_redo_local[kRedoLocal];
+__shared__ int g_redo_n;
+
+__device__ void rows_redo_segment(const FastArgs& A, long long pos, unsigned long long* sums, int& fallbacks);
+
 template <int W, int R>
 __device__ __forceinline__ void rows_chunk(const FastArgs& A, const float* mg, long long e, long long pos,
                                            unsigned gmask, unsigned long long* sums) {
   const SlView& S = A.rx;
   const bool done = rows_segment<W, R>(A, mg, S.prod + e, S.v + e, S.vt + e, S, pos, gmask, sums);
-  if (!done && (gmask & -gmask) == (1u << (threadIdx.x & 31))) S.redo[atomicAdd(S.redo_ctl, 1u)] = pos;
+  if (!done && (gmask & -gmask) == (1u << (threadIdx.x & 31))) {
+    const int i = atomicAdd(&g_redo_n, 1);
+    if (i < kRedoLocal) g_redo_local[i] = pos;
+    else S.redo[atomicAdd(S.redo_ctl, 1u)] = pos;
+  }
 }
 
 // rows is exactly ceil(largest set / W): 1..kRowsMax for W = 1, above
@@ -290,7 +303,7 @@ __device__ __forceinline__ void rows_dispatch(const FastArgs& A, const float* mg
 // (all loads in flight together), the decision is Dinkelbach's iteration in
 // binary64 from the binary64 margins, and the sales go to the global product
 // sums; the segment's carried ratio is refreshed.
-__device__ void rows_redo_segment(const FastArgs& A, long long pos, int& fallbacks) {
+__device__ void rows_redo_segment(const FastArgs& A, long long pos, unsigned long long* sums, int& fallbacks) {
   const SlView& S = A.rx;
   const RowsPos rp = rows_pos(S, pos);
   const int lane = threadIdx.x & 31;
@@ -347,10 +360,47 @@ __device__ void rows_redo_segment(const FastArgs& A, long long pos, int& fallbac
   const double q = quotient(S.lam[pos], vt0 + Dl);
 #pragma unroll
   for (int p = 0; p < kRowsMax; ++p)
-    if ((prev >> p) & 1u) atomicAdd(A.s_fx + jv[p], fixed_product(q, S.v[rp.e + lane + 32ll * p], A.fx_bits));
+    if ((prev >> p) & 1u) atomicAdd(sums + jv[p], fixed_product(q, S.v[rp.e + lane + 32ll * p], A.fx_bits));
   if (lane == 0) {
     S.rprev[pos] = (float)Rd;
     ++fallbacks;
+  }
+}
+
+// With per-block product sums (SC = 1): the fold of the partial sums into the
+// global ones (rows blockIdx.y < chunks, as k_reduce_products) and the binary64
+// redo of the listed segments (the last row of blocks, one warp per segment)
+// in one launch; both add into s_fx. The last redo block to finish clears the
+// list for the next pass.
+__global__ void __launch_bounds__(256) k_reduce_redo(FastArgs A, int n, int nparts,
+                                                     const unsigned long long* __restrict__ part, int chunks) {
+  __shared__ int last;
+  if (A.st && A.st->converged) return;
+  if ((int)blockIdx.y < chunks) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const int per = (nparts + chunks - 1) / chunks;
+    const int b0 = blockIdx.y * per, b1 = min(nparts, b0 + per);
+    unsigned long long acc = 0ull;
+#pragma unroll 4
+    for (int b = b0; b < b1; ++b) acc += __ldcg(part + (size_t)b * n + j);
+    if (acc) atomicAdd(A.s_fx + j, acc);
+    return;
+  }
+  const SlView& S = A.rx;
+  const unsigned cnt = *(volatile unsigned*)S.redo_ctl;
+  int fallbacks = 0;
+  const unsigned gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), nw = gridDim.x * (blockDim.x >> 5);
+  for (unsigned i = gw; i < cnt; i += nw) rows_redo_segment(A, S.redo[i], A.s_fx, fallbacks);
+  if (fallbacks && A.fallbacks) atomicAdd(A.fallbacks, (unsigned long long)fallbacks);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    last = atomicAdd(S.redo_ctl + 1, 1u) == gridDim.x - 1;
+    if (last) {
+      S.redo_ctl[0] = 0u;
+      S.redo_ctl[1] = 0u;
+    }
   }
 }
 
@@ -363,7 +413,7 @@ __global__ void __launch_bounds__(256) k_rows_redo(FastArgs A) {
   const unsigned cnt = *(volatile unsigned*)S.redo_ctl;
   int fallbacks = 0;
   const unsigned gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), nw = gridDim.x * (blockDim.x >> 5);
-  for (unsigned i = gw; i < cnt; i += nw) rows_redo_segment(A, S.redo[i], fallbacks);
+  for (unsigned i = gw; i < cnt; i += nw) rows_redo_segment(A, S.redo[i], A.s_fx, fallbacks);
   if (fallbacks && A.fallbacks) atomicAdd(A.fallbacks, (unsigned long long)fallbacks);
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -386,6 +436,7 @@ __global__ void __launch_bounds__(MS ? kRowsMsThreads : kRowsThreads, MS ? 1 : k
   if (A.st && A.st->converged) return;
   const int n = A.P.n;
   const float* mg = A.marg32c;
+  if (threadIdx.x == 0) g_redo_n = 0;
   if (SC == 1) {
     float* smg = reinterpret_cast<float*>(acc + n);
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -393,8 +444,8 @@ __global__ void __launch_bounds__(MS ? kRowsMsThreads : kRowsThreads, MS ? 1 : k
       if (MS) smg[j] = A.marg32c[j];
     }
     if (MS) mg = smg;
-    __syncthreads();
   }
+  __syncthreads();
   unsigned long long* sums = SC == 1 ? acc : A.s_fx;
   const SlView& S = A.rx;
   const int wl = threadIdx.x & 31;
@@ -415,6 +466,14 @@ __global__ void __launch_bounds__(MS ? kRowsMsThreads : kRowsThreads, MS ? 1 : k
       case 8: rows_dispatch<8>(A, mg, rows, e, pos, gmask, sums); break;
       default: rows_dispatch<16>(A, mg, rows, e, pos, gmask, sums); break;
     }
+  }
+  // the block's uncertified segments (about 1e-4 of them), in binary64, one warp each
+  __syncthreads();
+  {
+    const int nl = g_redo_n < kRedoLocal ? g_redo_n : kRedoLocal;
+    int fallbacks = 0;
+    for (int i = threadIdx.x >> 5; i < nl; i += blockDim.x >> 5) rows_redo_segment(A, g_redo_local[i], sums, fallbacks);
+    if (fallbacks && A.fallbacks) atomicAdd(A.fallbacks, (unsigned long long)fallbacks);
   }
   // an iterate pass forms no segment values: the dual step takes sum_l z_l as sum_j m_j s_j
   if (threadIdx.x == 0) A.zpart[blockIdx.x] = 0.0;
@@ -628,6 +687,14 @@ cudaError_t launch_seg_rows32(const F32Args& A, const FastPlan& pl, cudaStream_t
   if (pl.rows_ms) k_seg_rows32<1, 1><<<pl.rows_grid, kRowsMsThreads, pl.rows_smem, s>>>(A);
   else if (pl.rows_smem > 0) k_seg_rows32<1, 0><<<pl.rows_grid, kRowsThreads, pl.rows_smem, s>>>(A);
   else k_seg_rows32<2, 0><<<pl.rows_grid, kRowsThreads, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_redo(const FastArgs& A, const FastPlan& pl, int nparts, const unsigned long long* part,
+                               cudaStream_t s) {
+  const int n = A.P.n;
+  dim3 grid(n > 0 ? (n + 255) / 256 : 1, pl.reduce_chunks + 1);
+  k_reduce_redo<<<grid, 256, 0, s>>>(A, n, nparts, part, pl.reduce_chunks);
   return cudaGetLastError();
 }
 
