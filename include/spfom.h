@@ -314,7 +314,8 @@ spfom_status spfom_set_wait_limit(spfom_ctx* ctx, uint32_t polls);
  * 1024-thread block per SM, n <= 14464), 3 = the slot-major copy (single
  * instances), 4 = the row-exact copy as in 9 above with binary64 v and v - w
  * (single instances; D* is summed exactly as integers, and the segments whose
- * binary32 decision is not certified are redone in binary64 by a second small
+ * binary32 decision is not certified are redone in binary64 by the warps of
+ * their block after its chunk loop, those beyond 64 in a block by a small
  * kernel after the pass);
  * precision 64 with path 2: 1 = 8 products per lane at two 512-thread blocks per
  * SM, 2 = 8 per lane at three blocks per SM, 3 = 4 per lane at three blocks

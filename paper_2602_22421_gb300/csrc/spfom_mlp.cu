@@ -103,6 +103,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 64 columns of the warp's 32 lanes, and the wait for them, in one statement
+// (the registers are defined when it completes)
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];\n"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
@@ -110,6 +121,19 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
+
+// Tensor store from shared memory (bulk-group completion) and its waits.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, uint32_t src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"((uint64_t)map),
+               "r"(src), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+// every committed store has read its shared-memory source (the CTA may exit;
+// the global writes complete with the grid)
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ---- the product kernel ----------------------------------------------------------
 
@@ -127,18 +151,21 @@ struct Epi {
   __nv_bfloat16* out16t;         // BF16 transposed: out16t[c * ld16t + r], or null
   int ld16t;
   int zpad;                      // rows M..zpad-1 of out16t are written as zeros (K padding of later products)
+  int staged;                    // BN = 256: out16 / out16t leave through shared memory by tensor stores
   int* error;                    // set to 1 when a wait gives up
   unsigned wait_limit;           // polls of the producer's waits before they give up
 };
 
-template <int BN>
+// ST stages in the operand ring. Row tiles of the wide product take 2, so that
+// two CTAs (2 x 256 TMEM columns) share an SM and one CTA's epilogue overlaps
+// the other's loads and MMAs; the split-K weight gradients (at most one CTA
+// per SM, 64 K tiles each) take 4.
+template <int BN, int ST>
 struct GemmShape {
   static constexpr int kA = kBM * kBK * 2;  // bytes of an A stage (16 KB)
   static constexpr int kB = BN * kBK * 2;   // bytes of a B stage
   static constexpr int kStage = kA + kB;
-  // two stages for the wide tile keep two CTAs (2 x 256 TMEM columns) per SM,
-  // so one CTA's epilogue overlaps the other's loads and MMAs
-  static constexpr int kStages = BN >= 256 ? 2 : 4;
+  static constexpr int kStages = ST;
   static constexpr int kSmem = kStages * kStage + 1024;  // + alignment slack
   static constexpr uint32_t kCols = BN < 32 ? 32 : BN;   // TMEM columns (power of two >= 32)
   static_assert(kStage % 1024 == 0, "stages must keep the 1024-byte swizzle alignment");
@@ -149,10 +176,36 @@ __device__ __forceinline__ bool bf16_positive(__nv_bfloat16 h) {
   return b != 0 && (b & 0x8000u) == 0;
 }
 
-template <int BN>
+// bias, ReLU and ReLU-backward mask of one thread's 16 accumulator columns
+__device__ __forceinline__ void epi_apply(const Epi& E, int row, int c0, int nc, float (&v)[16]) {
+  if (E.bias)
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      if (i < nc) v[i] += E.bias[c0 + i];
+  if (E.relu)
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = v[i] > 0.f ? v[i] : 0.f;
+  if (E.mask) {
+    const __nv_bfloat16* mp = E.mask + (size_t)row * E.ldmask + c0;
+    if (nc == 16 && (E.ldmask & 7) == 0 && ((uintptr_t)mp & 15) == 0) {
+      const uint4 a = __ldg(reinterpret_cast<const uint4*>(mp)), b = __ldg(reinterpret_cast<const uint4*>(mp) + 1);
+      const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int i = 0; i < 16; ++i)  // a BF16 is > 0 iff its bits, read as a signed 16-bit integer, are
+        if ((short)(uint16_t)(w[i >> 1] >> (16 * (i & 1))) <= 0) v[i] = 0.f;
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (i < nc && !bf16_positive(mp[i])) v[i] = 0.f;
+    }
+  }
+}
+
+template <int BN, int ST>
 __global__ void __launch_bounds__(kThreads, 1)
-    k_gemm_tn(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb, int K, Epi E) {
-  using S = GemmShape<BN>;
+    k_gemm_tn(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
+              const __grid_constant__ CUtensorMap tr, const __grid_constant__ CUtensorMap tt, int K, Epi E) {
+  using S = GemmShape<BN, ST>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   __shared__ __align__(8) unsigned long long full[S::kStages], empty[S::kStages], done;
@@ -234,6 +287,95 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   const int row = m0 + warp * 32 + lane;
   const bool row_ok = row < E.M;
+  static_assert(BN != 256 || S::kStages * S::kStage >= 65536, "the staged epilogue needs 64 KB of the ring");
+  if (BN == 256 && E.staged) {
+    // Staged epilogue: 64 columns at a time into one of two shared-memory
+    // buffers (the ring's, free once the MMAs are done): the row-major BF16 tile
+    // [128][64] in the 128-byte swizzle of the row-major tensor map, the
+    // transposed tile [64][128] plain (rows M..zpad-1 zero); one thread issues
+    // the tensor stores, which clip rows and columns outside the maps.
+    const int rl = warp * 32 + lane;
+#pragma unroll 1
+    for (int g = 0; g < BN / 64; ++g) {
+      unsigned char* sr = base + (g & 1) * 32768;
+      unsigned char* st = sr + 16384;
+      if (g >= 2) {
+        if (threadIdx.x == 0) bulk_wait_read1();  // the stores of group g - 2 have read this buffer
+        __syncthreads();
+      }
+      // the mask's 64 columns in flight with the accumulator load
+      uint4 mk[8];
+      const bool masked = E.mask != nullptr && row_ok;
+      if (masked) {
+        const uint4* mp = reinterpret_cast<const uint4*>(E.mask + (size_t)row * E.ldmask + g * 64);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) mk[u] = __ldg(mp + u);
+      }
+      uint32_t r[64];
+      if (have) {
+        tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * 64), r);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 64; ++i) r[i] = 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int c0 = g * 64 + q * 16;
+        float v[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = row_ok ? __uint_as_float(r[q * 16 + i]) : 0.f;
+        if (row_ok) {
+          if (E.bias)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] += E.bias[c0 + i];
+          if (E.relu)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) v[i] = v[i] > 0.f ? v[i] : 0.f;
+          if (masked) {
+            const uint32_t w[8] = {mk[2 * q].x, mk[2 * q].y, mk[2 * q].z, mk[2 * q].w,
+                                   mk[2 * q + 1].x, mk[2 * q + 1].y, mk[2 * q + 1].z, mk[2 * q + 1].w};
+#pragma unroll
+            for (int i = 0; i < 16; ++i)  // BF16 > 0 iff its bits as a signed 16-bit integer are
+              if ((short)(uint16_t)(w[i >> 1] >> (16 * (i & 1))) <= 0) v[i] = 0.f;
+          }
+        }
+        uint32_t h[8];  // BF16 pairs (column 2i in the low half)
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+          h[i] = *reinterpret_cast<const uint32_t*>(&p2);
+        }
+        if (E.out16) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int j = 2 * q + u;  // 16-byte chunk of the tile row's 128 bytes
+            *reinterpret_cast<uint4*>(sr + rl * 128 + ((j ^ (rl & 7)) << 4)) =
+                make_uint4(h[4 * u], h[4 * u + 1], h[4 * u + 2], h[4 * u + 3]);
+          }
+        }
+        if (E.out16t) {
+          uint16_t* t = reinterpret_cast<uint16_t*>(st) + q * 16 * kBM + rl;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) t[i * kBM] = (uint16_t)(h[i >> 1] >> (16 * (i & 1)));
+        }
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        if (E.out16) tma_store_2d(&tr, smem_addr(sr), g * 64, m0);
+        if (E.out16t) tma_store_2d(&tt, smem_addr(st), m0, g * 64);
+        bulk_commit();
+      }
+    }
+    if (threadIdx.x == 0) bulk_wait_read0();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+      tc_fence_after();
+      tmem_dealloc(tmem, S::kCols);
+    }
+    return;
+  }
   if (E.out16t && !row_ok && row < E.zpad)
     for (int c = 0; c < E.N; ++c) E.out16t[(size_t)c * E.ld16t + row] = __float2bfloat16_rn(0.f);
   float* out32 = E.out32 ? E.out32 + (size_t)blockIdx.y * (size_t)E.M * (size_t)E.ld32 : nullptr;
@@ -246,30 +388,39 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int i = 0; i < 16; ++i) v[i] = have ? __uint_as_float(r[i]) : 0.f;
     if (!row_ok || c0 >= E.N) continue;
     const int nc = E.N - c0 < 16 ? E.N - c0 : 16;
+    epi_apply(E, row, c0, nc, v);
+    if (out32) {
+      float* o = out32 + (size_t)row * E.ld32 + c0;
+      if (nc == 16 && (E.ld32 & 3) == 0 && ((uintptr_t)o & 15) == 0) {
 #pragma unroll
-    for (int i = 0; i < 16; ++i) {
-      if (i < nc) {
-        if (E.bias) v[i] += E.bias[c0 + i];
-        if (E.relu) v[i] = v[i] > 0.f ? v[i] : 0.f;
-        if (E.mask && !bf16_positive(E.mask[(size_t)row * E.ldmask + c0 + i])) v[i] = 0.f;
+        for (int u = 0; u < 4; ++u) reinterpret_cast<float4*>(o)[u] = make_float4(v[4 * u], v[4 * u + 1], v[4 * u + 2], v[4 * u + 3]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (i < nc) o[i] = v[i];
       }
     }
-    if (out32)
-      for (int i = 0; i < nc; ++i) out32[(size_t)row * E.ld32 + c0 + i] = v[i];
     if (E.out16) {
       if (nc == 16 && (E.ld16 & 7) == 0) {
-        __align__(16) __nv_bfloat16 h[16];
+        uint32_t h[8];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) h[i] = __float2bfloat16_rn(v[i]);
+        for (int i = 0; i < 8; ++i) {
+          const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+          h[i] = *reinterpret_cast<const uint32_t*>(&p2);
+        }
         uint4* dst = reinterpret_cast<uint4*>(E.out16 + (size_t)row * E.ld16 + c0);
-        dst[0] = reinterpret_cast<const uint4*>(h)[0];
-        dst[1] = reinterpret_cast<const uint4*>(h)[1];
+        dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
+        dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
       } else {
-        for (int i = 0; i < nc; ++i) E.out16[(size_t)row * E.ld16 + c0 + i] = __float2bfloat16_rn(v[i]);
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          if (i < nc) E.out16[(size_t)row * E.ld16 + c0 + i] = __float2bfloat16_rn(v[i]);
       }
     }
     if (E.out16t)
-      for (int i = 0; i < nc; ++i) E.out16t[(size_t)(c0 + i) * E.ld16t + row] = __float2bfloat16_rn(v[i]);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (i < nc) E.out16t[(size_t)(c0 + i) * E.ld16t + row] = __float2bfloat16_rn(v[i]);
   }
   tc_fence_before();
   __syncthreads();
@@ -283,18 +434,34 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 constexpr int kEw = 256;
 
-// x (FP32 [rows][16]) -> BF16 row-major copy [rows][64] (columns 16..63 zero,
-// the K padding of the first product) and BF16 transposed copy [16][ldt]
-// (columns rows..zpad-1 zero).
+// x (FP32 [rows][16]) -> BF16 row-major copy [rows][64] (columns 0..15; the
+// K padding 16..63 stays zero from the allocation) and BF16 transposed copy
+// [16][ldt] (columns rows..zpad-1 zero); one thread per row.
 __global__ void k_inputs(const float* __restrict__ x, long long rows, long long zpad, __nv_bfloat16* __restrict__ xb,
                          __nv_bfloat16* __restrict__ xt, long long ldt) {
-  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= zpad * kKPad) return;
-  const long long r = i / kKPad;
-  const int c = (int)(i % kKPad);
-  const __nv_bfloat16 h = (r < rows && c < kF) ? __float2bfloat16_rn(x[r * kF + c]) : __float2bfloat16_rn(0.f);
-  if (r < rows) xb[i] = h;
-  if (xt && c < kF) xt[(size_t)c * ldt + r] = h;
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= zpad) return;
+  uint32_t h[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  if (r < rows) {
+    const float* xr = x + r * kF;
+    const bool vec = ((uintptr_t)x & 15) == 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const float4 f = vec ? __ldg(reinterpret_cast<const float4*>(xr) + u)
+                           : make_float4(xr[4 * u], xr[4 * u + 1], xr[4 * u + 2], xr[4 * u + 3]);
+      const __nv_bfloat162 a = __floats2bfloat162_rn(f.x, f.y), b = __floats2bfloat162_rn(f.z, f.w);
+      h[2 * u] = *reinterpret_cast<const uint32_t*>(&a);
+      h[2 * u + 1] = *reinterpret_cast<const uint32_t*>(&b);
+    }
+    uint4* dst = reinterpret_cast<uint4*>(xb + r * kKPad);
+    dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
+    dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+  }
+  if (xt) {
+    uint16_t* t = reinterpret_cast<uint16_t*>(xt) + r;
+#pragma unroll
+    for (int c = 0; c < kF; ++c) t[(size_t)c * ldt] = (uint16_t)(h[c >> 1] >> (16 * (c & 1)));
+  }
 }
 
 // Master FP32 parameters -> BF16 operands: W1 [256][64] (columns 16..63 zero),
@@ -342,7 +509,7 @@ __global__ void k_loss(const float* __restrict__ o16, const float* __restrict__ 
     const float e = o16[(size_t)r * kOutPad] - t[r];
     e2 = (double)e * (double)e;
     const __nv_bfloat16 g = __float2bfloat16_rn(2.f * e / (float)rows);
-    for (int c = 0; c < kKPad; ++c) d16[(size_t)r * kKPad + c] = c == 0 ? g : z;
+    d16[(size_t)r * kKPad] = g;  // columns 1..63 stay zero from the allocation
     for (int c = 0; c < kOutPad; ++c) d16t[(size_t)c * ldt + r] = c == 0 ? g : z;
   } else if (r < zpad) {
     for (int c = 0; c < kOutPad; ++c) d16t[(size_t)c * ldt + r] = z;
@@ -359,15 +526,42 @@ __global__ void k_loss_finish(const double* __restrict__ partial, int nb, long l
   if (threadIdx.x == 0) loss[0] = rows > 0 ? s / (double)rows : 0.0;
 }
 
-// Bias gradient: g[c] = sum_r d[c][r] over the transposed BF16 gradient [C][ldt]
-// (one block per column, fixed order).
-__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dt, long long ldt, long long rows, float* __restrict__ g) {
+// Bias gradient g[c] = sum_r d[c][r] over the transposed BF16 gradient [C][ldt]
+// in two fixed-order passes. First: block (s, c) sums the rows
+// [s per, (s + 1) per) of column c (per and rows8 multiples of 8; the rows
+// between the valid ones and rows8 hold zeros) with 16-byte loads, FP32 within
+// a thread, binary64 across the block, into part[c * S + s].
+__global__ void k_bias_partial(const __nv_bfloat16* __restrict__ dt, long long ldt, long long rows8, long long per,
+                               float* __restrict__ part) {
   __shared__ double sh[32];
-  const int c = blockIdx.x;
+  const int c = blockIdx.y, S = gridDim.x;
+  const long long r0 = (long long)blockIdx.x * per, r1 = min(rows8, r0 + per);
+  const uint4* src = reinterpret_cast<const uint4*>(dt + (size_t)c * ldt);
+  float acc = 0.f;
+  for (long long k = r0 / 8 + threadIdx.x; k < r1 / 8; k += blockDim.x) {
+    const uint4 u = __ldg(src + k);
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+    float t = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[i]));
+      t += f.x + f.y;
+    }
+    acc += t;
+  }
+  const double tot = block_sum_d((double)acc, sh);
+  if (threadIdx.x == 0) part[(size_t)c * S + blockIdx.x] = (float)tot;
+}
+
+// Second: g[c] = the column's S partial sums, one warp per column (lane k
+// adds the partials k, k + 32, ... in order, then a fixed shuffle tree).
+__global__ void k_bias_finish(const float* __restrict__ part, int S, int C, float* __restrict__ g) {
+  const int c = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (c >= C) return;
   double s = 0.0;
-  for (long long r = threadIdx.x; r < rows; r += blockDim.x) s += (double)__bfloat162float(dt[(size_t)c * ldt + r]);
-  s = block_sum_d(s, sh);
-  if (threadIdx.x == 0) g[c] = (float)s;
+  for (int k = lane; k < S; k += 32) s += (double)part[(size_t)c * S + k];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) g[c] = (float)s;
 }
 
 // Split-K partial tiles [splits][M][N] -> g (optionally only column 0, strided).
@@ -378,7 +572,8 @@ __global__ void k_splitk_sum(const float* __restrict__ part, int splits, int M, 
   if (i >= M * cols) return;
   const int r = i / cols, c = col0_only ? 0 : i % cols;
   float s = 0.f;
-  for (int k = 0; k < splits; ++k) s += part[(size_t)k * M * N + (size_t)r * N + c];
+#pragma unroll 8
+  for (int k = 0; k < splits; ++k) s += __ldg(part + (size_t)k * M * N + (size_t)r * N + c);
   g[i] = s;
 }
 
@@ -425,6 +620,20 @@ bool make_map(CUtensorMap* map, const __nv_bfloat16* ptr, long long rows, long l
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Tensor map of the transposed BF16 output [rows][cols] (ld elements), boxes
+// of 128 columns by 64 rows, no swizzle (the staged epilogue's [64][128] tile).
+bool make_map_t(CUtensorMap* map, const __nv_bfloat16* ptr, long long rows, long long cols, long long ld) {
+  auto fn = encode_fn();
+  if (!fn || ((uintptr_t)ptr & 15) || (ld * 2) % 16) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(ld * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)kBM, 64u};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 long long round64(long long x) { return (x + 63) / 64 * 64; }
 
 }  // namespace
@@ -451,19 +660,36 @@ cudaError_t gemm_tn(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* 
   if (splits_used) *splits_used = splits;
   E.M = M;
   E.N = N;
+  // 256-wide tiles with BF16 outputs and no FP32 one: the staged epilogue
+  // (the tensor maps check the outputs' alignment; without them the plain one)
+  CUtensorMap tr = ta, tt = ta;
+  E.staged = 0;
+  if (bn == 256 && N == 256 && splits == 1 && !E.out32 && (E.out16 || E.out16t) && E.ld16t >= 0) {
+    const long long zp = E.out16t ? (E.zpad > M ? E.zpad : M) : 0;
+    bool ok = true;
+    if (E.out16) ok = make_map(&tr, E.out16, M, N, E.ld16, kBM);
+    if (ok && E.out16t) ok = zp <= E.ld16t && make_map_t(&tt, E.out16t, N, zp, E.ld16t);
+    if (ok && E.mask) ok = (E.ldmask & 7) == 0 && ((uintptr_t)E.mask & 15) == 0;
+    E.staged = ok ? 1 : 0;
+  }
   dim3 grid((M + kBM - 1) / kBM, splits);
   if (bn == 16) {
-    k_gemm_tn<16><<<grid, kThreads, GemmShape<16>::kSmem, s>>>(ta, tb, K, E);
+    k_gemm_tn<16, 4><<<grid, kThreads, GemmShape<16, 4>::kSmem, s>>>(ta, tb, tr, tt, K, E);
+  } else if (splits > 1) {
+    k_gemm_tn<256, 4><<<grid, kThreads, GemmShape<256, 4>::kSmem, s>>>(ta, tb, tr, tt, K, E);
   } else {
-    k_gemm_tn<256><<<grid, kThreads, GemmShape<256>::kSmem, s>>>(ta, tb, K, E);
+    k_gemm_tn<256, 2><<<grid, kThreads, GemmShape<256, 2>::kSmem, s>>>(ta, tb, tr, tt, K, E);
   }
   return cudaGetLastError();
 }
 
 cudaError_t gemm_setup() {
-  cudaError_t e = cudaFuncSetAttribute(k_gemm_tn<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, GemmShape<16>::kSmem);
+  cudaError_t e =
+      cudaFuncSetAttribute(k_gemm_tn<16, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, GemmShape<16, 4>::kSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_gemm_tn<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, GemmShape<256>::kSmem);
+    e = cudaFuncSetAttribute(k_gemm_tn<256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, GemmShape<256, 2>::kSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_gemm_tn<256, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, GemmShape<256, 4>::kSmem);
   return e;
 }
 
@@ -646,6 +872,22 @@ cudaError_t weight_grad(spfom_mlp* n, const __nv_bfloat16* dt, const __nv_bfloat
   return cudaGetLastError();
 }
 
+// Bias gradient of C columns of the transposed gradient dt [C][ldt] over
+// `rows` rows (zeros up to round64(rows)) into g[C]; the partial sums use
+// n->part, after the weight gradient that shares it.
+cudaError_t bias_grad(spfom_mlp* n, const __nv_bfloat16* dt, int C, long long rows, float* g, cudaStream_t s) {
+  const long long rows8 = (rows + 7) / 8 * 8;
+  long long S = (4 * 152 + C - 1) / C;            // about four blocks per SM over all columns
+  const long long smax = (rows8 + 2047) / 2048;   // at least 2048 rows (one 16-byte load per thread) each
+  if (S > smax) S = smax;
+  if (S < 1) S = 1;
+  const long long per = ((rows8 + S - 1) / S + 7) / 8 * 8;
+  S = (rows8 + per - 1) / per;
+  spfom::mlp::k_bias_partial<<<dim3((unsigned)S, (unsigned)C), 256, 0, s>>>(dt, n->cap, rows8, per, n->part);
+  spfom::mlp::k_bias_finish<<<(C * 32 + 255) / 256, 256, 0, s>>>(n->part, (int)S, C, g);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 extern "C" {
@@ -754,8 +996,7 @@ spfom_status spfom_mlp_forward(spfom_mlp* n, const float* x, int64_t rows, float
   MLP_TRY(ensure_rows(n, rows));
   MLP_TRY(refresh_weights(n, s));
   const long long zp = spfom::mlp::round64(rows);
-  spfom::mlp::k_inputs<<<spfom::mlp::blocks(zp * spfom::mlp::kKPad), spfom::mlp::kEw, 0, s>>>(x, rows, zp, n->xb,
-                                                                                              nullptr, n->cap);
+  spfom::mlp::k_inputs<<<spfom::mlp::blocks(zp), spfom::mlp::kEw, 0, s>>>(x, rows, zp, n->xb, nullptr, n->cap);
   MLP_TRY(cudaGetLastError());
   MLP_TRY(forward_rows(n, rows, false, s));
   spfom::mlp::k_take_output<<<spfom::mlp::blocks(rows), spfom::mlp::kEw, 0, s>>>(n->o16, rows, out);
@@ -773,7 +1014,7 @@ spfom_status spfom_mlp_loss_grad(spfom_mlp* n, const float* x, const float* t, i
   MLP_TRY(ensure_rows(n, rows));
   MLP_TRY(refresh_weights(n, s));
   const long long ldt = n->cap, zp = spfom::mlp::round64(rows);
-  spfom::mlp::k_inputs<<<spfom::mlp::blocks(zp * KP), spfom::mlp::kEw, 0, s>>>(x, rows, zp, n->xb, n->xt, ldt);
+  spfom::mlp::k_inputs<<<spfom::mlp::blocks(zp), spfom::mlp::kEw, 0, s>>>(x, rows, zp, n->xb, n->xt, ldt);
   MLP_TRY(cudaGetLastError());
   MLP_TRY(forward_rows(n, rows, true, s));
   const int lb = spfom::mlp::blocks(zp);
@@ -783,7 +1024,7 @@ spfom_status spfom_mlp_loss_grad(spfom_mlp* n, const float* x, const float* t, i
   float* g = n->g;
   // output layer: dw3 = h2^T dO (a [256][16] product, column 0), db3 = sum dO
   MLP_TRY(weight_grad(n, n->h2t, n->d16t, 16, rows, g + spfom::mlp::kOffW3, true, s));
-  spfom::mlp::k_bias_grad<<<1, 256, 0, s>>>(n->d16t, ldt, rows, g + spfom::mlp::kOffB3);
+  MLP_TRY(bias_grad(n, n->d16t, 1, rows, g + spfom::mlp::kOffB3, s));
   // dH2 = (dO w3^T) masked by h2 > 0
   {
     Epi E = epi(n);
@@ -798,7 +1039,7 @@ spfom_status spfom_mlp_loss_grad(spfom_mlp* n, const float* x, const float* t, i
   }
   // dW2 = dH2^T h1, db2 = sum dH2
   MLP_TRY(weight_grad(n, n->dh2t, n->h1t, H, rows, g + spfom::mlp::kOffW2, false, s));
-  spfom::mlp::k_bias_grad<<<H, 256, 0, s>>>(n->dh2t, ldt, rows, g + spfom::mlp::kOffB2);
+  MLP_TRY(bias_grad(n, n->dh2t, H, rows, g + spfom::mlp::kOffB2, s));
   // dH1 = (dH2 W2) masked by h1 > 0 (transposed copy only)
   {
     Epi E = epi(n);
@@ -811,7 +1052,7 @@ spfom_status spfom_mlp_loss_grad(spfom_mlp* n, const float* x, const float* t, i
   }
   // dW1 = dH1^T x, db1 = sum dH1
   MLP_TRY(weight_grad(n, n->dh1t, n->xt, 16, rows, g + spfom::mlp::kOffW1, false, s));
-  spfom::mlp::k_bias_grad<<<H, 256, 0, s>>>(n->dh1t, ldt, rows, g + spfom::mlp::kOffB1);
+  MLP_TRY(bias_grad(n, n->dh1t, H, rows, g + spfom::mlp::kOffB1, s));
   MLP_TRY(cudaGetLastError());
   if (loss) MLP_TRY(cudaMemcpyAsync(loss, n->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
   return check_error(n, s);
