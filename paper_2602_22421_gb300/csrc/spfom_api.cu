@@ -697,7 +697,7 @@ spfom_status spfom_load_instance(spfom_ctx* ctx, const spfom_instance* I) {
       if (plan.bchunk_ok) W.zparts_iter = std::max(W.zparts_iter, plan.bchunk_grid);
       if (plan.bchunk64_ok) W.zparts_iter = std::max(W.zparts_iter, plan.bchunk64_grid);
       if (plan.ms_ok) W.zparts_iter = std::max(W.zparts_iter, std::max(plan.ms_grid, plan.ms_grid32));
-      if (plan.rows_ok) W.zparts_iter = std::max(W.zparts_iter, plan.rows_grid);
+      if (plan.rows_ok) W.zparts_iter = std::max(W.zparts_iter, std::max(plan.rows_grid, plan.rows_grid32));
       W.zparts_eval = plan.grid_eval;
       if (dd)
         for (int v = 1; v <= 3; ++v) {

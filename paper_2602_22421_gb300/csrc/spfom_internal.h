@@ -130,6 +130,7 @@ struct FastPlan {
   int rows_ok;        // 1 when tiling 4 is available (single instance, path 0)
   int rows_ms;        // 1: k_seg_rows keeps the binary32 margin images in shared memory (12 n bytes)
   int rows_grid, rows_smem;
+  int rows_grid32;     // blocks of the binary32 row-exact kernel
   int rows_redo_grid;  // blocks of k_rows_redo (the SM count)
   int f32_rows;        // 1: the binary32 pass runs k_seg_rows32 on the row-exact copy (tiling 9)
 };

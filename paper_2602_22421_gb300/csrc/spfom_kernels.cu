@@ -573,7 +573,7 @@ cudaError_t launch_segment_pass(const Problem& P, const Work& Wk, const RunConfi
     const FastPlan& pl = Wk.plan;
     if (!bchunk && !Wk.batch && pl.f32_rows && Wk.rx.nchunks > 0 && Wk.rx.v32) {
       A.rx = Wk.rx;
-      *zparts_out = pl.rows_grid;
+      *zparts_out = pl.rows_grid32;
       return launch_seg_rows32(A, pl, s);
     }
     if (!bchunk && pl.f32_sl && Wk.sl.nchunks > 0) {

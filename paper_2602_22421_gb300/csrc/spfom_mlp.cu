@@ -103,15 +103,20 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// 64 columns of the warp's 32 lanes, and the wait for them, in one statement
-// (the registers are defined when it completes)
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&r)[64]) {
+// 32 columns of the warp's 32 lanes and the wait for them, in one statement
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%64];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
       "tcgen05.wait::ld.sync.aligned;"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr)
       : "memory");
+}
+
+// barrier 1 or 2 (barrier 0 is __syncthreads) over `threads` threads
+__device__ __forceinline__ void named_bar(uint32_t id, uint32_t threads) {
+  if (id == 1u) asm volatile("bar.sync 1, %0;" ::"r"(threads) : "memory");
+  else asm volatile("bar.sync 2, %0;" ::"r"(threads) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
@@ -201,8 +206,16 @@ __device__ __forceinline__ void epi_apply(const Epi& E, int row, int c0, int nc,
   }
 }
 
+// Threads of a CTA: the 256-wide row tiles (2 stages) run eight warps, two per
+// TMEM lane quarter, each half of them storing one half of the columns; the
+// other instantiations four.
 template <int BN, int ST>
-__global__ void __launch_bounds__(kThreads, 1)
+__host__ __device__ constexpr int gemm_threads() {
+  return BN == 256 && ST == 2 ? 2 * kThreads : kThreads;
+}
+
+template <int BN, int ST>
+__global__ void __launch_bounds__(gemm_threads<BN, ST>(), gemm_threads<BN, ST>() > kThreads ? 2 : 1)
     k_gemm_tn(const __grid_constant__ CUtensorMap ta, const __grid_constant__ CUtensorMap tb,
               const __grid_constant__ CUtensorMap tr, const __grid_constant__ CUtensorMap tt, int K, Epi E) {
   using S = GemmShape<BN, ST>;
@@ -285,89 +298,114 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
   tc_fence_after();
 
-  const int row = m0 + warp * 32 + lane;
+  constexpr int kHalves = gemm_threads<BN, ST>() / kThreads;  // column halves of the epilogue
+  const int quarter = warp & 3, half = warp >> 2;  // TMEM lanes 32 quarter.. (tile rows), columns
+  const int rl = quarter * 32 + lane;
+  const int row = m0 + rl;
   const bool row_ok = row < E.M;
+  const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);
   static_assert(BN != 256 || S::kStages * S::kStage >= 65536, "the staged epilogue needs 64 KB of the ring");
   if (BN == 256 && E.staged) {
-    // Staged epilogue: 64 columns at a time into one of two shared-memory
-    // buffers (the ring's, free once the MMAs are done): the row-major BF16 tile
-    // [128][64] in the 128-byte swizzle of the row-major tensor map, the
-    // transposed tile [64][128] plain (rows M..zpad-1 zero); one thread issues
-    // the tensor stores, which clip rows and columns outside the maps.
-    const int rl = warp * 32 + lane;
+    // Staged epilogue: 64 columns at a time into a shared-memory buffer (the
+    // ring's, free once the MMAs are done): the row-major BF16 tile [128][64] in
+    // the 128-byte swizzle of the row-major tensor map, the transposed tile
+    // [64][128] plain (rows M..zpad-1 zero); one thread per column half issues
+    // the tensor stores, which clip rows and columns outside the maps. With one
+    // half the groups alternate between two buffers; with two halves each half
+    // has its own buffer.
+    constexpr int kGroups = BN / 64 / kHalves;
+    const int lead = half * kThreads;
+    const uint32_t bar = 1u + (uint32_t)half;
 #pragma unroll 1
-    for (int g = 0; g < BN / 64; ++g) {
-      unsigned char* sr = base + (g & 1) * 32768;
+    for (int gi = 0; gi < kGroups; ++gi) {
+      const int g = half * kGroups + gi;
+      unsigned char* sr = base + (kHalves == 1 ? (gi & 1) : half) * 32768;
       unsigned char* st = sr + 16384;
-      if (g >= 2) {
-        if (threadIdx.x == 0) bulk_wait_read1();  // the stores of group g - 2 have read this buffer
-        __syncthreads();
-      }
-      // the mask's 64 columns in flight with the accumulator load
-      uint4 mk[8];
-      const bool masked = E.mask != nullptr && row_ok;
-      if (masked) {
-        const uint4* mp = reinterpret_cast<const uint4*>(E.mask + (size_t)row * E.ldmask + g * 64);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) mk[u] = __ldg(mp + u);
-      }
-      uint32_t r[64];
-      if (have) {
-        tmem_ld64(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * 64), r);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 64; ++i) r[i] = 0u;
+      if (kHalves == 1 ? gi >= 2 : gi >= 1) {
+        if (threadIdx.x == lead) {  // the stores that last read this buffer are done with it
+          if (kHalves == 1) bulk_wait_read1();
+          else bulk_wait_read0();
+        }
+        named_bar(bar, kThreads);
       }
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int c0 = g * 64 + q * 16;
-        float v[16];
+      for (int sub = 0; sub < 2; ++sub) {
+        const int cs = g * 64 + sub * 32;
+        // the mask's 32 columns in flight with the accumulator load
+        uint4 mk[4];
+        const bool masked = E.mask != nullptr && row_ok;
+        if (masked) {
+          const uint4* mp = reinterpret_cast<const uint4*>(E.mask + (size_t)row * E.ldmask + cs);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) v[i] = row_ok ? __uint_as_float(r[q * 16 + i]) : 0.f;
-        if (row_ok) {
-          if (E.bias)
+          for (int u = 0; u < 4; ++u) mk[u] = __ldg(mp + u);
+        }
+        uint32_t r[32];
+        if (have) {
+          tmem_ld32(trow + (uint32_t)cs, r);
+        } else {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] += E.bias[c0 + i];
-          if (E.relu)
+          for (int i = 0; i < 32; ++i) r[i] = 0u;
+        }
 #pragma unroll
-            for (int i = 0; i < 16; ++i) v[i] = v[i] > 0.f ? v[i] : 0.f;
-          if (masked) {
-            const uint32_t w[8] = {mk[2 * q].x, mk[2 * q].y, mk[2 * q].z, mk[2 * q].w,
-                                   mk[2 * q + 1].x, mk[2 * q + 1].y, mk[2 * q + 1].z, mk[2 * q + 1].w};
+        for (int qq = 0; qq < 2; ++qq) {
+          const int q = sub * 2 + qq;  // 16-column chunk of the group
+          const int c0 = g * 64 + q * 16;
+          float v[16];
 #pragma unroll
-            for (int i = 0; i < 16; ++i)  // BF16 > 0 iff its bits as a signed 16-bit integer are
-              if ((short)(uint16_t)(w[i >> 1] >> (16 * (i & 1))) <= 0) v[i] = 0.f;
+          for (int i = 0; i < 16; ++i) v[i] = row_ok ? __uint_as_float(r[qq * 16 + i]) : 0.f;
+          if (row_ok) {
+            if (E.bias) {
+              const float4* b4 = reinterpret_cast<const float4*>(E.bias + c0);
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const float4 b = __ldg(b4 + u);
+                v[4 * u] += b.x;
+                v[4 * u + 1] += b.y;
+                v[4 * u + 2] += b.z;
+                v[4 * u + 3] += b.w;
+              }
+            }
+            if (E.relu)
+#pragma unroll
+              for (int i = 0; i < 16; ++i) v[i] = v[i] > 0.f ? v[i] : 0.f;
+            if (masked) {
+              const uint32_t w[8] = {mk[2 * qq].x, mk[2 * qq].y, mk[2 * qq].z, mk[2 * qq].w,
+                                     mk[2 * qq + 1].x, mk[2 * qq + 1].y, mk[2 * qq + 1].z, mk[2 * qq + 1].w};
+#pragma unroll
+              for (int i = 0; i < 16; ++i)  // BF16 > 0 iff its bits as a signed 16-bit integer are
+                if ((short)(uint16_t)(w[i >> 1] >> (16 * (i & 1))) <= 0) v[i] = 0.f;
+            }
           }
-        }
-        uint32_t h[8];  // BF16 pairs (column 2i in the low half)
+          uint32_t h[8];  // BF16 pairs (column 2i in the low half)
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
-          h[i] = *reinterpret_cast<const uint32_t*>(&p2);
-        }
-        if (E.out16) {
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            const int j = 2 * q + u;  // 16-byte chunk of the tile row's 128 bytes
-            *reinterpret_cast<uint4*>(sr + rl * 128 + ((j ^ (rl & 7)) << 4)) =
-                make_uint4(h[4 * u], h[4 * u + 1], h[4 * u + 2], h[4 * u + 3]);
+          for (int i = 0; i < 8; ++i) {
+            const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+            h[i] = *reinterpret_cast<const uint32_t*>(&p2);
           }
-        }
-        if (E.out16t) {
-          uint16_t* t = reinterpret_cast<uint16_t*>(st) + q * 16 * kBM + rl;
+          if (E.out16) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) t[i * kBM] = (uint16_t)(h[i >> 1] >> (16 * (i & 1)));
+            for (int u = 0; u < 2; ++u) {
+              const int j = 2 * q + u;  // 16-byte chunk of the tile row's 128 bytes
+              *reinterpret_cast<uint4*>(sr + rl * 128 + ((j ^ (rl & 7)) << 4)) =
+                  make_uint4(h[4 * u], h[4 * u + 1], h[4 * u + 2], h[4 * u + 3]);
+            }
+          }
+          if (E.out16t) {
+            uint16_t* t = reinterpret_cast<uint16_t*>(st) + q * 16 * kBM + rl;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) t[i * kBM] = (uint16_t)(h[i >> 1] >> (16 * (i & 1)));
+          }
         }
       }
       fence_async_smem();
-      __syncthreads();
-      if (threadIdx.x == 0) {
+      named_bar(bar, kThreads);
+      if (threadIdx.x == lead) {
         if (E.out16) tma_store_2d(&tr, smem_addr(sr), g * 64, m0);
         if (E.out16t) tma_store_2d(&tt, smem_addr(st), m0, g * 64);
         bulk_commit();
       }
     }
-    if (threadIdx.x == 0) bulk_wait_read0();
+    if (threadIdx.x == lead) bulk_wait_read0();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -376,13 +414,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     return;
   }
+  // plain epilogue: the half's columns [c_lo, c_hi)
+  const int c_lo = half * (BN / kHalves), c_hi = c_lo + BN / kHalves;
   if (E.out16t && !row_ok && row < E.zpad)
-    for (int c = 0; c < E.N; ++c) E.out16t[(size_t)c * E.ld16t + row] = __float2bfloat16_rn(0.f);
+    for (int c = c_lo; c < c_hi && c < E.N; ++c) E.out16t[(size_t)c * E.ld16t + row] = __float2bfloat16_rn(0.f);
   float* out32 = E.out32 ? E.out32 + (size_t)blockIdx.y * (size_t)E.M * (size_t)E.ld32 : nullptr;
 #pragma unroll 1
-  for (int c0 = 0; c0 < BN; c0 += 16) {
+  for (int c0 = c_lo; c0 < c_hi; c0 += 16) {
     uint32_t r[16];
-    if (have) tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+    if (have) tmem_ld16(trow + (uint32_t)c0, r);
     float v[16];
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = have ? __uint_as_float(r[i]) : 0.f;
@@ -670,15 +710,16 @@ cudaError_t gemm_tn(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* 
     if (E.out16) ok = make_map(&tr, E.out16, M, N, E.ld16, kBM);
     if (ok && E.out16t) ok = zp <= E.ld16t && make_map_t(&tt, E.out16t, N, zp, E.ld16t);
     if (ok && E.mask) ok = (E.ldmask & 7) == 0 && ((uintptr_t)E.mask & 15) == 0;
+    if (ok && E.bias) ok = ((uintptr_t)E.bias & 15) == 0;
     E.staged = ok ? 1 : 0;
   }
   dim3 grid((M + kBM - 1) / kBM, splits);
   if (bn == 16) {
-    k_gemm_tn<16, 4><<<grid, kThreads, GemmShape<16, 4>::kSmem, s>>>(ta, tb, tr, tt, K, E);
+    k_gemm_tn<16, 4><<<grid, gemm_threads<16, 4>(), GemmShape<16, 4>::kSmem, s>>>(ta, tb, tr, tt, K, E);
   } else if (splits > 1) {
-    k_gemm_tn<256, 4><<<grid, kThreads, GemmShape<256, 4>::kSmem, s>>>(ta, tb, tr, tt, K, E);
+    k_gemm_tn<256, 4><<<grid, gemm_threads<256, 4>(), GemmShape<256, 4>::kSmem, s>>>(ta, tb, tr, tt, K, E);
   } else {
-    k_gemm_tn<256, 2><<<grid, kThreads, GemmShape<256, 2>::kSmem, s>>>(ta, tb, tr, tt, K, E);
+    k_gemm_tn<256, 2><<<grid, gemm_threads<256, 2>(), GemmShape<256, 2>::kSmem, s>>>(ta, tb, tr, tt, K, E);
   }
   return cudaGetLastError();
 }

@@ -60,9 +60,36 @@ namespace {
 #ifndef SPFOM_ROWS_MS_THREADS
 #define SPFOM_ROWS_MS_THREADS 1024
 #endif
-constexpr int kRowsThreads = SPFOM_ROWS_THREADS;     // block of the kernel without shared margins
+// binary64 with global sums: 2 x 768 threads (40 registers, 48 warps per SM)
+// ran 0.426 ms on a 2e6-segment instance of the huge instance's shape against
+// 0.469 ms at 2 x 512 (64 registers), 0.429 at 3 x 512, 0.428 at 4 x 384,
+// 0.442 at 2 x 1024 and 0.457 at 3 x 640; binary32 keeps 2 x 512 (0.210 ms;
+// 0.228-0.266 with more warps and fewer registers)
+#ifndef SPFOM_ROWS_G_THREADS
+#define SPFOM_ROWS_G_THREADS 768
+#endif
+#ifndef SPFOM_ROWS_G_MINB
+#define SPFOM_ROWS_G_MINB 2
+#endif
+#ifndef SPFOM_ROWS32_G_THREADS
+#define SPFOM_ROWS32_G_THREADS 512
+#endif
+#ifndef SPFOM_ROWS32_G_MINB
+#define SPFOM_ROWS32_G_MINB 2
+#endif
+constexpr int kRowsThreads = SPFOM_ROWS_THREADS;     // block of the kernel with shared sums only
 constexpr int kRowsMinBlocks = SPFOM_ROWS_MINB;      // its blocks per SM (register budget)
 constexpr int kRowsMsThreads = SPFOM_ROWS_MS_THREADS;  // block of the shared-margins kernel (one per SM)
+
+// Block size and blocks per SM (the register budget) of each form: shared
+// margins and sums (MS), shared sums only (SC = 1), global sums (SC = 2),
+// binary64 (F32 = 0) or binary32.
+template <int SC, int MS, int F32>
+struct RowsCfg {
+  static constexpr int threads =
+      MS ? kRowsMsThreads : (SC == 2 ? (F32 ? SPFOM_ROWS32_G_THREADS : SPFOM_ROWS_G_THREADS) : kRowsThreads);
+  static constexpr int minb = MS ? 1 : (SC == 2 ? (F32 ? SPFOM_ROWS32_G_MINB : SPFOM_ROWS_G_MINB) : kRowsMinBlocks);
+};
 
 // round(x 2^G) for binary64 x >= 0 with x 2^G < 2^62 (integer operations only,
 // no branch: shift counts are clamped and the cases chosen by selects).
@@ -431,7 +458,7 @@ __global__ void __launch_bounds__(256) k_rows_redo(FastArgs A) {
 // images into shared memory (one 1024-thread block per SM). SC = 2: global
 // atomics into the product sums, margin images read from global memory.
 template <int SC, int MS>
-__global__ void __launch_bounds__(MS ? kRowsMsThreads : kRowsThreads, MS ? 1 : kRowsMinBlocks) k_seg_rows(FastArgs A) {
+__global__ void __launch_bounds__(RowsCfg<SC, MS, 0>::threads, RowsCfg<SC, MS, 0>::minb) k_seg_rows(FastArgs A) {
   extern __shared__ unsigned long long acc[];  // SC == 1: [n] fixed-point sums; MS: + [n] binary32 margins
   if (A.st && A.st->converged) return;
   const int n = A.P.n;
@@ -586,7 +613,7 @@ __device__ __forceinline__ void rows32_dispatch_r(const F32Args& A, const float*
 }
 
 template <int SC, int MS>
-__global__ void __launch_bounds__(MS ? kRowsMsThreads : kRowsThreads, MS ? 1 : kRowsMinBlocks) k_seg_rows32(F32Args A) {
+__global__ void __launch_bounds__(RowsCfg<SC, MS, 1>::threads, RowsCfg<SC, MS, 1>::minb) k_seg_rows32(F32Args A) {
   extern __shared__ unsigned long long acc[];  // SC == 1: [n] fixed-point sums; MS: + [n] binary32 margins
   if (A.st->converged) return;
   const int n = A.n;
@@ -645,48 +672,39 @@ bool rows_plan(int n, int sms, FastPlan* plan) {
   plan->rows_ok = 0;
   plan->rows_redo_grid = sms;
   const long long sums = 8ll * n, ms = 12ll * n;
-  if (ms <= kTmaMaxSmem) {  // sums and binary32 margins in shared memory, one 1024-thread block per SM
-    const int nb = std::min(rows_blocks(k_seg_rows<1, 1>, (int)ms, kRowsMsThreads),
-                            rows_blocks(k_seg_rows32<1, 1>, (int)ms, kRowsMsThreads));
-    if (nb >= 1) {
-      plan->rows_ok = 1;
-      plan->rows_ms = 1;
-      plan->rows_smem = (int)ms;
-      plan->rows_grid = nb * sms;
-      return true;
-    }
-  }
-  if (sums <= kFastMaxSmem) {
-    const int nb = std::min(rows_blocks(k_seg_rows<1, 0>, (int)sums, kRowsThreads),
-                            rows_blocks(k_seg_rows32<1, 0>, (int)sums, kRowsThreads));
-    if (nb >= 1) {
-      plan->rows_ok = 1;
-      plan->rows_ms = 0;
-      plan->rows_smem = (int)sums;
-      plan->rows_grid = nb * sms;
-      return true;
-    }
-  }
-  const int nb = std::min(rows_blocks(k_seg_rows<2, 0>, 0, kRowsThreads), rows_blocks(k_seg_rows32<2, 0>, 0, kRowsThreads));
-  if (nb < 1) return false;
-  plan->rows_ok = 1;
-  plan->rows_ms = 0;
-  plan->rows_smem = 0;
-  plan->rows_grid = nb * sms;
-  return true;
+  // the form both precisions can run: grids from each kernel's own occupancy
+  auto take = [&](int nb64, int nb32, int msf, long long smem) {
+    if (nb64 < 1 || nb32 < 1) return false;
+    plan->rows_ok = 1;
+    plan->rows_ms = msf;
+    plan->rows_smem = (int)smem;
+    plan->rows_grid = nb64 * sms;
+    plan->rows_grid32 = nb32 * sms;
+    return true;
+  };
+  if (ms <= kTmaMaxSmem &&  // sums and binary32 margins in shared memory, one 1024-thread block per SM
+      take(rows_blocks(k_seg_rows<1, 1>, (int)ms, RowsCfg<1, 1, 0>::threads),
+           rows_blocks(k_seg_rows32<1, 1>, (int)ms, RowsCfg<1, 1, 1>::threads), 1, ms))
+    return true;
+  if (sums <= kFastMaxSmem &&
+      take(rows_blocks(k_seg_rows<1, 0>, (int)sums, RowsCfg<1, 0, 0>::threads),
+           rows_blocks(k_seg_rows32<1, 0>, (int)sums, RowsCfg<1, 0, 1>::threads), 0, sums))
+    return true;
+  return take(rows_blocks(k_seg_rows<2, 0>, 0, RowsCfg<2, 0, 0>::threads),
+              rows_blocks(k_seg_rows32<2, 0>, 0, RowsCfg<2, 0, 1>::threads), 0, 0);
 }
 
 cudaError_t launch_seg_rows(const FastArgs& A, const FastPlan& pl, cudaStream_t s) {
-  if (pl.rows_ms) k_seg_rows<1, 1><<<pl.rows_grid, kRowsMsThreads, pl.rows_smem, s>>>(A);
-  else if (pl.rows_smem > 0) k_seg_rows<1, 0><<<pl.rows_grid, kRowsThreads, pl.rows_smem, s>>>(A);
-  else k_seg_rows<2, 0><<<pl.rows_grid, kRowsThreads, 0, s>>>(A);
+  if (pl.rows_ms) k_seg_rows<1, 1><<<pl.rows_grid, RowsCfg<1, 1, 0>::threads, pl.rows_smem, s>>>(A);
+  else if (pl.rows_smem > 0) k_seg_rows<1, 0><<<pl.rows_grid, RowsCfg<1, 0, 0>::threads, pl.rows_smem, s>>>(A);
+  else k_seg_rows<2, 0><<<pl.rows_grid, RowsCfg<2, 0, 0>::threads, 0, s>>>(A);
   return cudaGetLastError();
 }
 
 cudaError_t launch_seg_rows32(const F32Args& A, const FastPlan& pl, cudaStream_t s) {
-  if (pl.rows_ms) k_seg_rows32<1, 1><<<pl.rows_grid, kRowsMsThreads, pl.rows_smem, s>>>(A);
-  else if (pl.rows_smem > 0) k_seg_rows32<1, 0><<<pl.rows_grid, kRowsThreads, pl.rows_smem, s>>>(A);
-  else k_seg_rows32<2, 0><<<pl.rows_grid, kRowsThreads, 0, s>>>(A);
+  if (pl.rows_ms) k_seg_rows32<1, 1><<<pl.rows_grid32, RowsCfg<1, 1, 1>::threads, pl.rows_smem, s>>>(A);
+  else if (pl.rows_smem > 0) k_seg_rows32<1, 0><<<pl.rows_grid32, RowsCfg<1, 0, 1>::threads, pl.rows_smem, s>>>(A);
+  else k_seg_rows32<2, 0><<<pl.rows_grid32, RowsCfg<2, 0, 1>::threads, 0, s>>>(A);
   return cudaGetLastError();
 }
 
