@@ -129,8 +129,8 @@ struct FastPlan {
   int fast_rows;      // 1: the binary64 pass runs k_seg_rows on the row-exact copy (tiling 4)
   int rows_ok;        // 1 when tiling 4 is available (single instance, path 0)
   int rows_ms;        // 1: k_seg_rows keeps the binary32 margin images in shared memory (12 n bytes)
-  int rows_grid, rows_smem;
-  int rows_grid32;     // blocks of the binary32 row-exact kernel
+  int rows_grid, rows_smem;  // its grid and shared memory (0: global sums)
+  int rows_ms32, rows_grid32, rows_smem32;  // the same for the binary32 row-exact kernel
   int rows_redo_grid;  // blocks of k_rows_redo (the SM count)
   int f32_rows;        // 1: the binary32 pass runs k_seg_rows32 on the row-exact copy (tiling 9)
 };

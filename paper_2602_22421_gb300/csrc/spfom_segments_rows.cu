@@ -51,8 +51,17 @@ namespace spfom {
 
 namespace {
 
+// Launch shapes of the forms other than shared margins (one 1024-thread block
+// per SM). Binary64 on the mid instance (shared sums): 2 x 768 threads (40
+// registers, 48 warps) 0.1323 ms, against 0.1397 ms with shared margins
+// (1024 threads, 64 registers), 0.1494 at 2 x 512, 0.1377 at 2 x 704 and 0.1355
+// at 2 x 1024; binary32 keeps shared margins (0.0556 ms; 0.0577-0.0680 in the
+// shared-sums shapes).
 #ifndef SPFOM_ROWS_THREADS
-#define SPFOM_ROWS_THREADS 512
+#define SPFOM_ROWS_THREADS 768
+#endif
+#ifndef SPFOM_ROWS32_THREADS
+#define SPFOM_ROWS32_THREADS 512
 #endif
 #ifndef SPFOM_ROWS_MINB
 #define SPFOM_ROWS_MINB 2
@@ -77,8 +86,7 @@ namespace {
 #ifndef SPFOM_ROWS32_G_MINB
 #define SPFOM_ROWS32_G_MINB 2
 #endif
-constexpr int kRowsThreads = SPFOM_ROWS_THREADS;     // block of the kernel with shared sums only
-constexpr int kRowsMinBlocks = SPFOM_ROWS_MINB;      // its blocks per SM (register budget)
+constexpr int kRowsMinBlocks = SPFOM_ROWS_MINB;      // blocks per SM of the shared-sums forms (register budget)
 constexpr int kRowsMsThreads = SPFOM_ROWS_MS_THREADS;  // block of the shared-margins kernel (one per SM)
 
 // Block size and blocks per SM (the register budget) of each form: shared
@@ -87,7 +95,9 @@ constexpr int kRowsMsThreads = SPFOM_ROWS_MS_THREADS;  // block of the shared-ma
 template <int SC, int MS, int F32>
 struct RowsCfg {
   static constexpr int threads =
-      MS ? kRowsMsThreads : (SC == 2 ? (F32 ? SPFOM_ROWS32_G_THREADS : SPFOM_ROWS_G_THREADS) : kRowsThreads);
+      MS ? kRowsMsThreads
+         : (SC == 2 ? (F32 ? SPFOM_ROWS32_G_THREADS : SPFOM_ROWS_G_THREADS)
+                    : (F32 ? SPFOM_ROWS32_THREADS : SPFOM_ROWS_THREADS));
   static constexpr int minb = MS ? 1 : (SC == 2 ? (F32 ? SPFOM_ROWS32_G_MINB : SPFOM_ROWS_G_MINB) : kRowsMinBlocks);
 };
 
@@ -409,7 +419,7 @@ __global__ void __launch_bounds__(256) k_reduce_redo(FastArgs A, int n, int npar
     const int per = (nparts + chunks - 1) / chunks;
     const int b0 = blockIdx.y * per, b1 = min(nparts, b0 + per);
     unsigned long long acc = 0ull;
-#pragma unroll 4
+#pragma unroll 8
     for (int b = b0; b < b1; ++b) acc += __ldcg(part + (size_t)b * n + j);
     if (acc) atomicAdd(A.s_fx + j, acc);
     return;
@@ -672,26 +682,34 @@ bool rows_plan(int n, int sms, FastPlan* plan) {
   plan->rows_ok = 0;
   plan->rows_redo_grid = sms;
   const long long sums = 8ll * n, ms = 12ll * n;
-  // the form both precisions can run: grids from each kernel's own occupancy
-  auto take = [&](int nb64, int nb32, int msf, long long smem) {
-    if (nb64 < 1 || nb32 < 1) return false;
-    plan->rows_ok = 1;
-    plan->rows_ms = msf;
-    plan->rows_smem = (int)smem;
-    plan->rows_grid = nb64 * sms;
-    plan->rows_grid32 = nb32 * sms;
-    return true;
-  };
-  if (ms <= kTmaMaxSmem &&  // sums and binary32 margins in shared memory, one 1024-thread block per SM
-      take(rows_blocks(k_seg_rows<1, 1>, (int)ms, RowsCfg<1, 1, 0>::threads),
-           rows_blocks(k_seg_rows32<1, 1>, (int)ms, RowsCfg<1, 1, 1>::threads), 1, ms))
-    return true;
-  if (sums <= kFastMaxSmem &&
-      take(rows_blocks(k_seg_rows<1, 0>, (int)sums, RowsCfg<1, 0, 0>::threads),
-           rows_blocks(k_seg_rows32<1, 0>, (int)sums, RowsCfg<1, 0, 1>::threads), 0, sums))
-    return true;
-  return take(rows_blocks(k_seg_rows<2, 0>, 0, RowsCfg<2, 0, 0>::threads),
-              rows_blocks(k_seg_rows32<2, 0>, 0, RowsCfg<2, 0, 1>::threads), 0, 0);
+  // Binary64: shared sums with the binary32 margins read through L1 when two
+  // blocks fit per SM (more warps at fewer registers), else shared sums and
+  // margins, else shared sums alone, else global sums.
+  const int s64 = sums <= kFastMaxSmem ? rows_blocks(k_seg_rows<1, 0>, (int)sums, RowsCfg<1, 0, 0>::threads) : 0;
+  const int m64 = ms <= kTmaMaxSmem ? rows_blocks(k_seg_rows<1, 1>, (int)ms, RowsCfg<1, 1, 0>::threads) : 0;
+  if (s64 >= 2 || (s64 >= 1 && m64 < 1)) {
+    plan->rows_ms = 0, plan->rows_smem = (int)sums, plan->rows_grid = s64 * sms;
+  } else if (m64 >= 1) {
+    plan->rows_ms = 1, plan->rows_smem = (int)ms, plan->rows_grid = m64 * sms;
+  } else {
+    const int g64 = rows_blocks(k_seg_rows<2, 0>, 0, RowsCfg<2, 0, 0>::threads);
+    if (g64 < 1) return false;
+    plan->rows_ms = 0, plan->rows_smem = 0, plan->rows_grid = g64 * sms;
+  }
+  // Binary32: shared sums and margins, else shared sums, else global sums.
+  const int m32 = ms <= kTmaMaxSmem ? rows_blocks(k_seg_rows32<1, 1>, (int)ms, RowsCfg<1, 1, 1>::threads) : 0;
+  const int s32 = sums <= kFastMaxSmem ? rows_blocks(k_seg_rows32<1, 0>, (int)sums, RowsCfg<1, 0, 1>::threads) : 0;
+  if (m32 >= 1) {
+    plan->rows_ms32 = 1, plan->rows_smem32 = (int)ms, plan->rows_grid32 = m32 * sms;
+  } else if (s32 >= 1) {
+    plan->rows_ms32 = 0, plan->rows_smem32 = (int)sums, plan->rows_grid32 = s32 * sms;
+  } else {
+    const int g32 = rows_blocks(k_seg_rows32<2, 0>, 0, RowsCfg<2, 0, 1>::threads);
+    if (g32 < 1) return false;
+    plan->rows_ms32 = 0, plan->rows_smem32 = 0, plan->rows_grid32 = g32 * sms;
+  }
+  plan->rows_ok = 1;
+  return true;
 }
 
 cudaError_t launch_seg_rows(const FastArgs& A, const FastPlan& pl, cudaStream_t s) {
@@ -702,8 +720,8 @@ cudaError_t launch_seg_rows(const FastArgs& A, const FastPlan& pl, cudaStream_t 
 }
 
 cudaError_t launch_seg_rows32(const F32Args& A, const FastPlan& pl, cudaStream_t s) {
-  if (pl.rows_ms) k_seg_rows32<1, 1><<<pl.rows_grid32, RowsCfg<1, 1, 1>::threads, pl.rows_smem, s>>>(A);
-  else if (pl.rows_smem > 0) k_seg_rows32<1, 0><<<pl.rows_grid32, RowsCfg<1, 0, 1>::threads, pl.rows_smem, s>>>(A);
+  if (pl.rows_ms32) k_seg_rows32<1, 1><<<pl.rows_grid32, RowsCfg<1, 1, 1>::threads, pl.rows_smem32, s>>>(A);
+  else if (pl.rows_smem32 > 0) k_seg_rows32<1, 0><<<pl.rows_grid32, RowsCfg<1, 0, 1>::threads, pl.rows_smem32, s>>>(A);
   else k_seg_rows32<2, 0><<<pl.rows_grid32, RowsCfg<2, 0, 1>::threads, 0, s>>>(A);
   return cudaGetLastError();
 }
@@ -711,8 +729,11 @@ cudaError_t launch_seg_rows32(const F32Args& A, const FastPlan& pl, cudaStream_t
 cudaError_t launch_reduce_redo(const FastArgs& A, const FastPlan& pl, int nparts, const unsigned long long* part,
                                cudaStream_t s) {
   const int n = A.P.n;
-  dim3 grid(n > 0 ? (n + 255) / 256 : 1, pl.reduce_chunks + 1);
-  k_reduce_redo<<<grid, 256, 0, s>>>(A, n, nparts, part, pl.reduce_chunks);
+  // about 8 partial rows per thread: one round of loads in flight (the fixed-point
+  // sums are exact in any order)
+  const int chunks = std::max(1, std::min(64, (nparts + 7) / 8));
+  dim3 grid(n > 0 ? (n + 255) / 256 : 1, chunks + 1);
+  k_reduce_redo<<<grid, 256, 0, s>>>(A, n, nparts, part, chunks);
   return cudaGetLastError();
 }
 
