@@ -370,9 +370,10 @@ def run_gpu(args):
     e2e = None
     if not args.no_e2e:
         pinned = pinned_arrays(inst)
-        # the measured tiling, except the slot-major and row-exact copies (each load would
-        # build them anew, a host sort of the segments by size): then the shared-margin tiling
-        e2e_tiling = 2 if m64["tiling"] in (3, 4) else m64["tiling"]
+        # the measured tiling (each load builds its copy anew: the row-exact copy on the
+        # device), except the slot-major copy, whose host sort of the segments by size costs
+        # more than it saves per step: then the shared-margin tiling
+        e2e_tiling = 2 if m64["tiling"] == 3 else m64["tiling"]
         se = Solver(None, stream=stream.cuda_stream, device=local, kkt_tol=0.0, tiling=e2e_tiling)
         ysink = np.empty(inst.m)
         se.load(pinned)

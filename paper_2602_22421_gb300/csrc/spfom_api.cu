@@ -250,18 +250,30 @@ spfom_status build_rows(spfom_ctx* ctx) {
   Work& W = ctx->W;
   if (W.rx.nchunks > 0 || !W.fast || !W.plan.rows_ok) return SPFOM_OK;
   const Problem& P = ctx->P;
-  std::vector<long long> seg_ptr((size_t)P.L + 1);
-  SPFOM_CUDA(ctx, cudaMemcpyAsync(seg_ptr.data(), P.seg_ptr, sizeof(long long) * seg_ptr.size(),
-                                  cudaMemcpyDeviceToHost, ctx->stream));
-  SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  std::vector<long long> perm, off;
-  spfom::SlView rx{};
-  const long long nch = spfom::rows_layout(seg_ptr.data(), P.L, &perm, &off, rx.cls_c, rx.cls_pos);
-  const size_t entries = (size_t)std::max(off[(size_t)nch], 1ll), npos = std::max<size_t>(perm.size(), 1);
-  long long* d_perm = nullptr;
 #define SPFOM_TRYS(x) do { spfom_status s_ = (x); if (s_ != SPFOM_OK) return s_; } while (0)
+  // the layout needs only the histogram of set sizes; the segments are placed
+  // on the device
+  constexpr int KN = spfom::kFastMaxSet + 1;
+  unsigned long long* d_cnt = nullptr;  // [KN] histogram, [KN] the scatter's cursors
+  SPFOM_TRYS(dalloc(ctx, &d_cnt, 2 * KN));
+  SPFOM_CUDA(ctx, cudaMemsetAsync(d_cnt, 0, 2 * KN * sizeof(unsigned long long), ctx->stream));
+  SPFOM_CUDA(ctx, spfom::launch_rows_hist(P, d_cnt, ctx->stream));
+  std::vector<unsigned long long> cnt(KN);
+  SPFOM_CUDA(ctx, cudaMemcpyAsync(cnt.data(), d_cnt, KN * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+  SPFOM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  std::vector<long long> off, pos_start(KN, 0);
+  spfom::SlView rx{};
+  const long long nch = spfom::rows_layout_counts(cnt.data(), &off, rx.cls_c, rx.cls_pos, pos_start.data());
+  const long long npos_l = rx.cls_pos[spfom::kRowsClasses];
+  const size_t entries = (size_t)std::max(off[(size_t)nch], 1ll), npos = (size_t)std::max(npos_l, 1ll);
+  long long* d_perm = nullptr;
+  long long* d_pos_start = nullptr;
   SPFOM_TRYS(upload(ctx, &rx.off, off.data(), off.size()));
-  if (!perm.empty()) SPFOM_TRYS(upload(ctx, &d_perm, perm.data(), perm.size()));
+  SPFOM_TRYS(upload(ctx, &d_pos_start, pos_start.data(), pos_start.size()));
+  SPFOM_TRYS(dalloc(ctx, &d_perm, npos));
+  SPFOM_CUDA(ctx, cudaMemsetAsync(d_perm, 0xFF, npos * sizeof(long long), ctx->stream));  // -1: padding
+  SPFOM_CUDA(ctx, spfom::launch_rows_scatter(P, d_pos_start, d_cnt + KN, d_perm, ctx->stream));
   SPFOM_TRYS(dalloc(ctx, &rx.prod, entries));
   if (W.v32) {
     SPFOM_TRYS(dalloc(ctx, &rx.v32, entries));

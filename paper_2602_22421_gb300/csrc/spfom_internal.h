@@ -428,10 +428,16 @@ long long sliced_layout(const long long* seg_ptr, long long L, int W8, std::vect
                         std::vector<long long>* off);
 cudaError_t launch_slice_items(const Problem& P, const Work& Wk, int W8, cudaStream_t s);
 cudaError_t launch_slice_segments(const Problem& P, const Work& Wk, int W8, cudaStream_t s);
-// row-exact copy (spfom_sliced.cu): host layout (positions, chunk offsets and
-// classes; returns the chunk count), the gather of the items and of lambda / vt_0
-long long rows_layout(const long long* seg_ptr, long long L, std::vector<long long>* perm,
-                      std::vector<long long>* off, long long cls_c[6], long long cls_pos[6]);
+// row-exact copy (spfom_sliced.cu): the histogram of set sizes (hist[kFastMaxSet
+// + 1], zeroed by the caller), the host layout from it (chunk offsets, classes,
+// each size's first position; returns the chunk count), the scatter of the
+// segments to their positions (perm preset to -1, cursor[kFastMaxSet + 1]
+// zeroed), the gather of the items and of lambda / vt_0
+cudaError_t launch_rows_hist(const Problem& P, unsigned long long* hist, cudaStream_t s);
+long long rows_layout_counts(const unsigned long long* cnt, std::vector<long long>* off, long long cls_c[6],
+                             long long cls_pos[6], long long* pos_start);
+cudaError_t launch_rows_scatter(const Problem& P, const long long* pos_start, unsigned long long* cursor,
+                                long long* perm, cudaStream_t s);
 cudaError_t launch_rows_items(const Problem& P, const SlView& S, const long long* perm, const float* v32,
                               const float* vt32, cudaStream_t s);
 cudaError_t launch_rows_segments(const Problem& P, const SlView& S, const long long* perm, const float* lam32,

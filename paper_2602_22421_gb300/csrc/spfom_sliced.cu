@@ -114,42 +114,93 @@ __global__ void k_rows_items(const Problem P, SlView S, const long long* __restr
   }
 }
 
+
+// Histogram of the set sizes (0..kFastMaxSet): shared-memory counts per block,
+// one global add per size and block; lanes with equal sizes add once.
+__global__ void k_rows_hist(const long long* __restrict__ seg_ptr, long long L, unsigned long long* __restrict__ hist) {
+  __shared__ unsigned int h[kFastMaxSet + 1];
+  for (int i = threadIdx.x; i <= kFastMaxSet; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < L; base += stride) {  // uniform over the block
+    const long long l = base + threadIdx.x;
+    long long K = -1;
+    if (l < L) {
+      K = seg_ptr[l + 1] - seg_ptr[l];
+      K = K < kFastMaxSet ? K : kFastMaxSet;  // the fast path's sets are no larger
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, K);
+    if (K >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&h[K], (unsigned)__popc(peers));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= kFastMaxSet; i += blockDim.x)
+    if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
+}
+
+// Each segment to a position of its size's run: pos_start[K] + a rank drawn
+// from cursor[K] (lanes with equal sizes draw together). The order within a
+// run is the arrival order; every segment's solve is independent of its
+// position and the sums are exact, so results do not depend on it.
+__global__ void k_rows_scatter(const long long* __restrict__ seg_ptr, long long L,
+                               const long long* __restrict__ pos_start, unsigned long long* __restrict__ cursor,
+                               long long* __restrict__ perm) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < L; base += stride) {  // uniform over the block
+    const long long l = base + threadIdx.x;
+    long long K = -1;
+    if (l < L) {
+      K = seg_ptr[l + 1] - seg_ptr[l];
+      K = K < kFastMaxSet ? K : kFastMaxSet;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, K);
+    const int leader = __ffs(peers) - 1;
+    unsigned long long b = 0ull;
+    if (K >= 0 && lane == leader) b = atomicAdd(cursor + K, (unsigned long long)__popc(peers));
+    b = __shfl_sync(0xffffffffu, b, leader);
+    if (K >= 0) perm[pos_start[K] + (long long)b + __popc(peers & ((1u << lane) - 1u))] = l;
+  }
+}
+
 }  // namespace
 
-long long rows_layout(const long long* seg_ptr, long long L, std::vector<long long>* perm,
-                      std::vector<long long>* off, long long cls_c[6], long long cls_pos[6]) {
-  // counting sort by set size (<= kFastMaxSet), descending; equal sizes keep segment order
-  const int KM = kFastMaxSet;
-  std::vector<long long> cnt((size_t)KM + 2, 0);
-  for (long long l = 0; l < L; ++l) ++cnt[(size_t)(KM - (seg_ptr[l + 1] - seg_ptr[l]))];
-  std::vector<long long> sorted((size_t)L), start((size_t)KM + 2, 0);
-  for (int k = 1; k <= KM + 1; ++k) start[(size_t)k] = start[(size_t)k - 1] + cnt[(size_t)k - 1];
-  for (long long l = 0; l < L; ++l) sorted[(size_t)start[(size_t)(KM - (seg_ptr[l + 1] - seg_ptr[l]))]++] = l;
-  auto size = [&](long long i) { return seg_ptr[sorted[(size_t)i] + 1] - seg_ptr[sorted[(size_t)i]]; };
+long long rows_layout_counts(const unsigned long long* cnt, std::vector<long long>* off, long long cls_c[6],
+                             long long cls_pos[6], long long* pos_start) {
+  // the segments in order of decreasing set size, split into the lane classes
+  // W = 16, 8, 4, 2, 1; a class's chunks take 32 / W positions each (the last
+  // one padded) and as many slot rows as their first (largest) set needs
   auto lanes = [](long long K) {
     int W = 1;
     while (W * kRowsMax < K) W <<= 1;
     return W;
   };
-  perm->clear();
   off->assign(1, 0);
-  long long i = 0, nch = 0;
-  for (int k = 0; k < kRowsClasses; ++k) {  // classes W = 16, 8, 4, 2, 1 in order of decreasing set size
+  long long nch = 0, npos = 0;
+  int K = kFastMaxSet;
+  for (int k = 0; k < kRowsClasses; ++k) {
     const int W = 16 >> k, C = 32 / W;
     cls_c[k] = nch;
-    cls_pos[k] = (long long)perm->size();
-    while (i < L && lanes(size(i)) == W) {
-      const long long K0 = size(i);  // the chunk's largest set
-      for (int g = 0; g < C; ++g) {
-        const bool in = i < L && lanes(size(i)) == W;
-        perm->push_back(in ? sorted[(size_t)i++] : -1);
-      }
-      off->push_back(off->back() + 32 * ((K0 + W - 1) / W));
-      ++nch;
+    cls_pos[k] = npos;
+    const int Ktop = K;
+    long long in_class = 0;
+    while (K >= 0 && lanes(K) == W) {
+      pos_start[K] = npos + in_class;
+      in_class += (long long)cnt[K];
+      --K;
     }
+    const long long chunks = (in_class + C - 1) / C;
+    long long seen = 0;
+    int Ks = Ktop;
+    for (long long c = 0; c < chunks; ++c) {
+      const long long first = c * C;  // the chunk's first (largest) segment within the class
+      while (seen + (long long)cnt[Ks] <= first) seen += (long long)cnt[Ks--];
+      off->push_back(off->back() + 32 * ((Ks + W - 1) / W));
+    }
+    nch += chunks;
+    npos += chunks * C;
   }
   cls_c[kRowsClasses] = nch;
-  cls_pos[kRowsClasses] = (long long)perm->size();
+  cls_pos[kRowsClasses] = npos;
   return nch;
 }
 
@@ -194,6 +245,21 @@ cudaError_t launch_rows_items(const Problem& P, const SlView& S, const long long
   if (S.nchunks <= 0) return cudaSuccess;
   const long long blocks = (S.nchunks + 7) / 8;  // 8 warps per block
   k_rows_items<<<(unsigned)(blocks < 65535 * 16 ? blocks : 65535 * 16), 256, 0, s>>>(P, S, perm, v32, vt32);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_hist(const Problem& P, unsigned long long* hist, cudaStream_t s) {
+  if (P.L <= 0) return cudaSuccess;
+  const long long blocks = (P.L + 255) / 256;
+  k_rows_hist<<<(unsigned)(blocks < 1216 ? blocks : 1216), 256, 0, s>>>(P.seg_ptr, P.L, hist);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rows_scatter(const Problem& P, const long long* pos_start, unsigned long long* cursor,
+                                long long* perm, cudaStream_t s) {
+  if (P.L <= 0) return cudaSuccess;
+  const long long blocks = (P.L + 255) / 256;
+  k_rows_scatter<<<(unsigned)(blocks < 1216 ? blocks : 1216), 256, 0, s>>>(P.seg_ptr, P.L, pos_start, cursor, perm);
   return cudaGetLastError();
 }
 

@@ -482,6 +482,37 @@ def test_row_exact_tiling_mixes_every_lane_class():
             assert st["z_sum"] == pytest.approx(ost["z_sum"], rel=ITER_RTOL)
 
 
+@pytest.mark.parametrize("n", [16_000, 22_000], ids=["f64_shared_margins", "f64_one_sums_block"])
+def test_row_exact_forms_by_product_count(n):
+    """The row-exact kernels take their form from the product count: the
+    binary64 pass keeps per-block sums in shared memory at two 768-thread
+    blocks per SM while two such blocks fit (n up to about 14 400), then the
+    sums and binary32 margins in one 1024-thread block (n = 16 000 here), then
+    one block of shared sums (n = 22 000), then global sums; the binary32 pass
+    keeps shared margins up to about 19 300 products and shared sums beyond.
+    The binary64 iterates track the oracle for 200 iterations, and the binary32
+    solve reaches the binary64 objective."""
+    inst = mid_gam(1, L=20_001, n=n, m=400)
+    run = Oracle(inst).run(OracleParams())
+    done = 0
+    with Solver(inst, tiling=4) as s:
+        for t in (1, 64, 65, 200):
+            while done < t:
+                run.step(1)
+                done += 1
+            st = s.step(t - st_iters(s))
+            ost = run.stats()
+            assert st["iters"] == ost["t"] == t and st["restarts"] == ost["restarts"]
+            assert nrel(s.duals(), run.y) <= ITER_RTOL, (t, nrel(s.duals(), run.y))
+            assert nrel(s.vector(5), run.s) <= ITER_RTOL
+        s.reset()
+        ref = s.solve()
+    with Solver(inst, precision=32, tiling=9) as s:
+        st = s.solve()
+    assert ref["converged"] == 1 and st["converged"] == 1 and st["kkt"] <= 1e-4
+    assert st["dual_avg"] == pytest.approx(ref["dual_avg"], rel=1e-4)
+
+
 def test_sets_of_100_products_binary32_solve():
     """The binary32 bulk mode (32 lanes x 4 slots, 16 x 8, or the row-exact
     layout) on sets of up to 100 products solves to KKT <= 1e-4 at the binary64
