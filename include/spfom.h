@@ -22,7 +22,10 @@
  *    spfom_last_error() gives a message for the last failing call on a ctx.
  *  - Host arrays passed in are read during the call only and copied; the
  *    library never keeps a caller pointer. Device memory is owned by the ctx
- *    and freed by spfom_destroy().
+ *    and freed by spfom_destroy(); it comes from the ctx's own stream-ordered
+ *    memory pool, which keeps the memory of an unloaded instance reserved for
+ *    the next load (the ctx holds its largest instance's footprint until
+ *    spfom_destroy).
  *  - One ctx per host thread. All device work of a ctx runs on one CUDA
  *    stream: the caller's (spfom_params.stream) or one the ctx creates.
  *  - All floating-point inputs and outputs are IEEE binary64.

@@ -36,6 +36,7 @@ struct spfom_ctx {
   double tau_init = 0.0;
   long long host_t = 0;
   std::vector<void*> bufs;  // device allocations of the loaded instance
+  cudaMemPool_t pool = nullptr;  // their stream-ordered pool: keeps its memory across loads (null: the default pool)
   DevState* d_state = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   std::vector<cudaEvent_t> prof_ev;  // event pairs of profiled segment launches
@@ -117,7 +118,8 @@ spfom_status dalloc(spfom_ctx* ctx, T** out, size_t count) {
   *out = nullptr;
   if (count == 0) count = 1;
   void* p = nullptr;
-  cudaError_t e = cudaMallocAsync(&p, count * sizeof(T), ctx->stream);
+  cudaError_t e = ctx->pool ? cudaMallocFromPoolAsync(&p, count * sizeof(T), ctx->pool, ctx->stream)
+                            : cudaMallocAsync(&p, count * sizeof(T), ctx->stream);
   if (e != cudaSuccess) return fail(ctx, SPFOM_ENOMEM, "device allocation of %zu bytes: %s", count * sizeof(T),
                                     cudaGetErrorString(e));
   ctx->bufs.push_back(p);
@@ -489,6 +491,24 @@ spfom_status spfom_create(const spfom_params* p, spfom_ctx** out) {
     e = cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking);
     ctx->own_stream = (e == cudaSuccess);
   }
+  if (e == cudaSuccess) {
+    // a private pool whose freed memory stays reserved (release threshold: all of it), so
+    // that reloading an instance of the same size maps no new memory
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = prm.device;
+    if (cudaMemPoolCreate(&ctx->pool, &props) == cudaSuccess) {
+      uint64_t keep = ~0ull;
+      if (cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+        cudaMemPoolDestroy(ctx->pool);
+        ctx->pool = nullptr;
+      }
+    } else {
+      ctx->pool = nullptr;
+    }
+    (void)cudaGetLastError();  // a refused pool leaves the default one in use
+  }
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->sms, cudaDevAttrMultiProcessorCount, prm.device);
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
   if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
@@ -506,6 +526,7 @@ void spfom_destroy(spfom_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->p.device);
   free_instance(ctx);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);  // its allocations are freed and the stream synchronized
   if (ctx->warm_buf) cudaFree(ctx->warm_buf);
   if (ctx->d_state) cudaFree(ctx->d_state);
   if (ctx->ev0) cudaEventDestroy(ctx->ev0);
