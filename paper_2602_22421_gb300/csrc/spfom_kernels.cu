@@ -471,6 +471,7 @@ __device__ __forceinline__ bool in_f32(double x, bool zero_ok) {
 
 __global__ void k_validate_items(const Problem P, const double* __restrict__ w, const double* __restrict__ v0,
                                  int f32, unsigned long long* __restrict__ keys) {
+  unsigned kmax = 0u;  // the largest set this thread saw (one atomic per warp at the end)
   for (long long l = blockIdx.x * (long long)blockDim.x + threadIdx.x; l < P.L;
        l += (long long)gridDim.x * blockDim.x) {
     const unsigned long long seg = (unsigned long long)l << kCheckSegShift;
@@ -480,7 +481,8 @@ __global__ void k_validate_items(const Problem P, const double* __restrict__ w, 
       continue;
     }
     if (b < 0 || e > P.nnz) continue;  // a decrease elsewhere reports it
-    atomicMax(keys + 2, (unsigned long long)(e - b));  // the largest set
+    const long long K = e - b;
+    kmax = max(kmax, (unsigned)(K < 0x7fffffffll ? K : 0x7fffffffll));
     const double lam = P.lam[l], v0l = v0[l];
     if (!(lam >= 0.0 && isfinite(lam))) {
       atomicMin(keys, seg | kSegLam);
@@ -512,6 +514,8 @@ __global__ void k_validate_items(const Problem P, const double* __restrict__ w, 
         atomicMin(keys + 1, (unsigned long long)p);
     }
   }
+  kmax = __reduce_max_sync(0xffffffffu, kmax);
+  if ((threadIdx.x & 31) == 0 && kmax) atomicMax(keys + 2, (unsigned long long)kmax);
 }
 
 }  // namespace
