@@ -352,6 +352,22 @@ struct RunConfig {
 enum ItemCheck { kBadId = 1, kRepeated = 2, kBadV = 3, kBadW = 4 };
 enum SegCheck { kSegOrder = 0, kSegLam = 1, kSegV0 = 2, kSegItems = 3 };
 constexpr int kCheckSegShift = 36;
+// A kernel's dynamic shared-memory limit and occupancy (spfom_kernels.cu),
+// remembered per CUDA context. kernel_smem raises the limit to `bytes` when it
+// is lower and never lowers it: a plan of another ctx in the same process may
+// launch the kernel with more. kernel_blocks returns the resident blocks per
+// SM at `threads` threads and `bytes` bytes of dynamic shared memory, raising
+// the limit first (0 when either call fails).
+cudaError_t kernel_smem(const void* kernel, int bytes);
+int kernel_blocks(const void* kernel, int threads, int bytes);
+template <class K>
+cudaError_t kernel_smem(K* kernel, int bytes) {
+  return kernel_smem(reinterpret_cast<const void*>(kernel), bytes);
+}
+template <class K>
+int kernel_blocks(K* kernel, int threads, int bytes) {
+  return kernel_blocks(reinterpret_cast<const void*>(kernel), threads, bytes);
+}
 cudaError_t launch_validate_items(const Problem& P, const double* w, const double* v0, bool f32,
                                   unsigned long long* keys, cudaStream_t s);
 cudaError_t launch_prep(const Problem& P, const double* w, const double* v0, double* vt, double* vt0,

@@ -27,13 +27,86 @@
 // int64 bit images (all candidate keys are positive doubles, others are -1),
 // keeping the comparisons off the binary64 pipe, which on GB300 runs at about
 // 1/60 of the binary32 rate.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <math_constants.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "spfom_device.cuh"
 #include "spfom_internal.h"
 
 namespace spfom {
+
+namespace {
+
+typedef CUresult (*CtxCurrentFn)(CUcontext*);
+
+// cuCtxGetCurrent through the runtime's driver entry-point query
+CtxCurrentFn ctx_current_fn() {
+  static std::once_flag once;
+  static CtxCurrentFn fn = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxCurrentFn>(p);
+  });
+  return fn;
+}
+
+// the current context (null when it cannot be told: nothing is remembered then)
+CUcontext current_context() {
+  CUcontext c = nullptr;
+  CtxCurrentFn fn = ctx_current_fn();
+  if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+  return c;
+}
+
+std::mutex g_kattr_mutex;
+std::map<std::pair<CUcontext, const void*>, int> g_kattr_smem;                   // limit set per kernel
+std::map<std::tuple<CUcontext, const void*, int, int>, int> g_kattr_blocks;      // occupancy answers
+
+}  // namespace
+
+cudaError_t kernel_smem(const void* kernel, int bytes) {
+  if (bytes <= 0) return cudaSuccess;
+  const CUcontext c = current_context();
+  std::lock_guard<std::mutex> lock(g_kattr_mutex);
+  if (c) {
+    auto it = g_kattr_smem.find({c, kernel});
+    if (it != g_kattr_smem.end() && it->second >= bytes) return cudaSuccess;
+  }
+  const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && c) g_kattr_smem[{c, kernel}] = bytes;
+  return e;
+}
+
+int kernel_blocks(const void* kernel, int threads, int bytes) {
+  if (kernel_smem(kernel, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const CUcontext c = current_context();
+  if (c) {
+    std::lock_guard<std::mutex> lock(g_kattr_mutex);
+    auto it = g_kattr_blocks.find(std::make_tuple(c, kernel, threads, bytes));
+    if (it != g_kattr_blocks.end()) return it->second;
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  if (c) {
+    std::lock_guard<std::mutex> lock(g_kattr_mutex);
+    g_kattr_blocks[std::make_tuple(c, kernel, threads, bytes)] = nb;
+  }
+  return nb;
+}
 
 namespace {
 

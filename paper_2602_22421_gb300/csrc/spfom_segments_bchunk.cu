@@ -136,10 +136,7 @@ bool bchunk_plan(int max_inst_products, int sms, FastPlan* plan) {
   const int smem = kBChunkProducts * (int)sizeof(unsigned long long);
   int nb = 0;
   auto occ = [&](auto k) {
-    int b = 0;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kFastThreads, smem) != cudaSuccess) return 0;
-    return b;
+    return kernel_blocks(k, kFastThreads, smem);
   };
   if (plan->W8 == 1) nb = occ(k_seg_f32_bchunk<1, 8>);
   if (plan->W8 == 2) nb = occ(k_seg_f32_bchunk<2, 8>);

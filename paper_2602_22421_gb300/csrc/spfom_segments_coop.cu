@@ -178,10 +178,7 @@ cudaError_t launch_coop_t(const F32Args& A, int W, int grid, int smem, cudaStrea
 
 template <class Kern>
 int coop_blocks(Kern k, int smem) {
-  int nb = 0;
-  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kFastThreads, smem) != cudaSuccess) return 0;
-  return nb;
+  return kernel_blocks(k, kFastThreads, smem);
 }
 
 }  // namespace

@@ -329,10 +329,7 @@ cudaError_t launch_dd_w(const DdArgs& A, const FastPlan& plan, int grid, int sme
 
 template <class Kern>
 int dd_blocks(Kern k, int smem) {
-  int nb = 0;
-  if (smem > 0 && cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, kFastThreads, smem) != cudaSuccess) return 0;
-  return nb;
+  return kernel_blocks(k, kFastThreads, smem);
 }
 
 // Blocks per SM of tiling v for scatter mode sc (shared memory smem when sc == 1).

@@ -871,16 +871,12 @@ template <int W>
 bool sl_attributes(const FastPlan& pl) {
   bool ok = true;
   if (pl.ms_ok) {
-    ok &= cudaFuncSetAttribute(k_seg_fast<W, 8, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               pl.ms_smem64) == cudaSuccess;
-    ok &= cudaFuncSetAttribute(k_seg_f32<W, 8, 1, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               pl.ms_smem32) == cudaSuccess;
+    ok &= kernel_smem(k_seg_fast<W, 8, 1, 1, 1>, pl.ms_smem64) == cudaSuccess;
+    ok &= kernel_smem(k_seg_f32<W, 8, 1, 1, 1>, pl.ms_smem32) == cudaSuccess;
   }
   if (pl.scatter == 1) {
-    ok &= cudaFuncSetAttribute(k_seg_fast<W, 8, 1, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem) ==
-          cudaSuccess;
-    ok &= cudaFuncSetAttribute(k_seg_f32<W, 8, 1, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem) ==
-          cudaSuccess;
+    ok &= kernel_smem(k_seg_fast<W, 8, 1, 0, 1>, pl.smem) == cudaSuccess;
+    ok &= kernel_smem(k_seg_f32<W, 8, 1, 0, 1>, pl.smem) == cudaSuccess;
   }
   return ok;
 }
@@ -898,11 +894,7 @@ cudaError_t launch_tma_w(const F32Args& A, int W, int grid, int smem, cudaStream
 
 template <class K>
 int blocks_per_sm(K kernel, int smem, int threads = kFastThreads) {
-  int nb = 0;
-  if (smem > 0 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) return 0;
-  return nb;
+  return kernel_blocks(kernel, threads, smem);
 }
 
 // The shared-memory limit of the variants that form segment values (a batch's
@@ -910,7 +902,7 @@ int blocks_per_sm(K kernel, int smem, int threads = kFastThreads) {
 bool zv_attributes(int W8, int smem, int ms_smem) {
   bool ok = true;
   auto set = [&](auto k, int bytes) {
-    if (bytes > 0) ok &= cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess;
+    if (bytes > 0) ok &= kernel_smem(k, bytes) == cudaSuccess;
   };
   if (W8 == 1) { set(k_seg_fast<1, 8, 1, 0, 0, true>, smem); set(k_seg_fast<1, 8, 1, 1, 0, true>, ms_smem); }
   if (W8 == 2) { set(k_seg_fast<2, 8, 1, 0, 0, true>, smem); set(k_seg_fast<2, 8, 1, 1, 0, true>, ms_smem); }
@@ -968,13 +960,13 @@ bool fast_plan(int n, int kmax, int sms, FastPlan* plan) {
   const int nbe = occupancy(W8, 0, 0, false);
   if (nb <= 0 || nbe <= 0 || nb32 <= 0) return false;
   if (sc == 1) {  // the 8- and 16-products-per-lane binary32 variants share the grid of the 4-per-lane one
-    cudaFuncSetAttribute(k_seg_f32<1, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_seg_f32<2, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_seg_f32<4, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_seg_f32<8, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_seg_f32<16, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_seg_f32<1, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    cudaFuncSetAttribute(k_seg_f32<2, 16, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    kernel_smem(k_seg_f32<1, 8, 1>, smem);
+    kernel_smem(k_seg_f32<2, 8, 1>, smem);
+    kernel_smem(k_seg_f32<4, 8, 1>, smem);
+    kernel_smem(k_seg_f32<8, 8, 1>, smem);
+    kernel_smem(k_seg_f32<16, 8, 1>, smem);
+    kernel_smem(k_seg_f32<1, 16, 1>, smem);
+    kernel_smem(k_seg_f32<2, 16, 1>, smem);
   }
   // margins in shared memory after the sums: 16 n (binary64) or 12 n (binary32) bytes
   plan->ms_ok = 0;
@@ -1054,11 +1046,9 @@ bool tma_plan(int n, int kmax, int sms, FastPlan* plan) {
 #define SPFOM_TMA_OCC(WW)                                                                                   \
   if (W8 == WW) {                                                                                           \
     if (plan->scatter == 1) {                                                                               \
-      cudaFuncSetAttribute(k_seg_f32_tma<WW, 8, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_f32_tma<WW, 8, 1>, kTmaThreads, smem);       \
+      nb = kernel_blocks(k_seg_f32_tma<WW, 8, 1>, kTmaThreads, smem);                                     \
     } else {                                                                                                \
-      cudaFuncSetAttribute(k_seg_f32_tma<WW, 8, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);     \
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_f32_tma<WW, 8, 2>, kTmaThreads, smem);       \
+      nb = kernel_blocks(k_seg_f32_tma<WW, 8, 2>, kTmaThreads, smem);                                     \
     }                                                                                                       \
   }
   SPFOM_TMA_OCC(1)
@@ -1083,10 +1073,7 @@ bool bchunk64_plan(int max_inst_products, int sms, FastPlan* plan) {
   int nb = 0;
 #define SPFOM_BC64(WW)                                                                                   \
   if (plan->W8 == WW) {                                                                                  \
-    if (cudaFuncSetAttribute(k_seg_fast_bchunk<WW, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != \
-        cudaSuccess)                                                                                     \
-      return false;                                                                                      \
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_seg_fast_bchunk<WW, 8>, kFastThreads, smem);    \
+    nb = kernel_blocks(k_seg_fast_bchunk<WW, 8>, kFastThreads, smem);                                    \
   }
   SPFOM_BC64(1)
   SPFOM_BC64(2)

@@ -669,11 +669,7 @@ __global__ void __launch_bounds__(RowsCfg<SC, MS, 1>::threads, RowsCfg<SC, MS, 1
 
 template <class K>
 int rows_blocks(K kernel, int smem, int threads) {
-  int nb = 0;
-  if (smem > 0 && cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
-    return 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) return 0;
-  return nb;
+  return kernel_blocks(kernel, threads, smem);
 }
 
 }  // namespace

@@ -276,10 +276,7 @@ cudaError_t launch_pipe_w(const FastArgs& A, int W, int grid, int smem, cudaStre
 
 template <class K>
 int pipe_blocks(K kernel, int smem) {
-  int nb = 0;
-  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, kPipeThreads, smem);
-  return nb;
+  return kernel_blocks(kernel, kPipeThreads, smem);
 }
 
 }  // namespace

@@ -513,6 +513,31 @@ def test_row_exact_forms_by_product_count(n):
     assert st["dual_avg"] == pytest.approx(ref["dual_avg"], rel=1e-4)
 
 
+@pytest.mark.parametrize("precision,tiling", [(64, 2), (64, 4), (32, 9)])
+def test_solvers_of_different_sizes_coexist(precision, tiling):
+    """A kernel's shared-memory limit is one setting per process and context.
+    Loading a smaller instance into a second solver (a smaller shared-memory
+    plan) must not lower the limit that the first solver's kernels launch
+    with: both go on with the iterates a solver alone computes."""
+    big = mid_gam(1, L=20_001, n=10_000, m=400)
+    small = mid_gam(2, L=5_001, n=1_000, m=100)
+    ref = {}
+    for name, inst in (("big", big), ("small", small)):
+        with Solver(inst, precision=precision, tiling=tiling) as s:
+            s.step(65)
+            ref[name] = s.duals()
+    a = Solver(big, precision=precision, tiling=tiling)
+    b = Solver(small, precision=precision, tiling=tiling)
+    try:
+        b.step(65)
+        a.step(65)
+        np.testing.assert_array_equal(a.duals(), ref["big"])
+        np.testing.assert_array_equal(b.duals(), ref["small"])
+    finally:
+        b.close()
+        a.close()
+
+
 def test_sets_of_100_products_binary32_solve():
     """The binary32 bulk mode (32 lanes x 4 slots, 16 x 8, or the row-exact
     layout) on sets of up to 100 products solves to KKT <= 1e-4 at the binary64
