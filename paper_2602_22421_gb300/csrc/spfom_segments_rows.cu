@@ -6,9 +6,9 @@
 // binary64 redo for uncertified segments; see spfom_segments_fast.cu), laid
 // out so that no lane issues work for a slot it does not hold:
 //
-//  * one lane per segment for sets of up to 12 products (32 segments per warp,
-//    no shuffles), 2 lanes for up to 24, 4 for up to 48, 8 for up to 96 and 16
-//    for up to 128 (kRowsMax = 12 slot rows per lane at most);
+//  * one lane per segment for sets of up to 8 products (32 segments per warp,
+//    no shuffles), 2 lanes for up to 16, 4 for up to 32, 8 for up to 64 and 16
+//    for up to 128 (kRowsMax = 8 slot rows per lane at most);
 //  * the row-exact copy (spfom_sliced.cu) sorts the segments by set size, so a
 //    chunk's segments have (nearly) equal sizes, and gives each chunk exactly
 //    ceil(largest set / W) slot rows of 32 entries; the kernel is instantiated
@@ -16,9 +16,9 @@
 //    a_j = m_j v_j, b_j = vt_j of just those rows in registers;
 //  * the certificate is tested once, at the converged ratio; a segment that
 //    does not pass it is not solved in the chunk loop but listed, and the
-//    kernel's last block to finish solves the listed segments in binary64
-//    (about 1e-4 of the segments), so the chunk loop carries no binary64
-//    decision code;
+//    block's warps solve its listed segments in binary64 after the chunk loop
+//    (about 1e-4 of the segments; beyond 64 in a block, a kernel after the
+//    pass), so the chunk loop carries no binary64 decision code;
 //  * the binary64 work is D* = vt_0 + sum_{S*} vt_j over the chosen slots and
 //    the quotient q = lambda / D*, whose warp instructions now serve 32 (or
 //    32 / W) segments; the chosen slots' ids, v and vt are read again (L1/L2)
@@ -36,7 +36,7 @@
 //
 // Error budget of the certificate (|a_j - R b_j| > 2^-16 (a_j + R b_j)): the
 // images carry at most 2^-23 relative error (v and vt truncated, m rounded),
-// a lane sums at most 12 slots in two interleaved partial sums (depth <= 7)
+// a lane sums at most 8 slots in two interleaved partial sums (depth <= 5)
 // and a group adds at most 4 shuffle levels, so N, D and R stay within about
 // 2e-6 of their exact values, below the 1.5e-5 margin: a certified set is the
 // exact-arithmetic optimum.
