@@ -482,17 +482,19 @@ def test_row_exact_tiling_mixes_every_lane_class():
             assert st["z_sum"] == pytest.approx(ost["z_sum"], rel=ITER_RTOL)
 
 
-@pytest.mark.parametrize("n", [16_000, 22_000], ids=["f64_shared_margins", "f64_one_sums_block"])
-def test_row_exact_forms_by_product_count(n):
-    """The row-exact kernels take their form from the product count: the
+@pytest.mark.parametrize("n,L", [(200, 100_000), (16_000, 20_001), (22_000, 20_001)],
+                         ids=["two_sums_blocks", "shared_margins", "one_sums_block"])
+def test_row_exact_forms_by_product_count(n, L):
+    """The row-exact kernels take their form from the product count. The
     binary64 pass keeps per-block sums in shared memory at two 768-thread
-    blocks per SM while two such blocks fit (n up to about 14 400), then the
-    sums and binary32 margins in one 1024-thread block (n = 16 000 here), then
-    one block of shared sums (n = 22 000), then global sums; the binary32 pass
-    keeps shared margins up to about 19 300 products and shared sums beyond.
-    The binary64 iterates track the oracle for 200 iterations, and the binary32
-    solve reaches the binary64 objective."""
-    inst = mid_gam(1, L=20_001, n=n, m=400)
+    blocks per SM while two such blocks fit (n up to about 14 400; n = 200
+    here, with 5000 slots per product), then the sums and binary32 margins in
+    one 1024-thread block (n = 16 000), then one block of shared sums
+    (n = 22 000), then global sums (the wide instance of the other tests). The
+    binary32 pass keeps shared margins up to about 19 300 products and shared
+    sums beyond. The binary64 iterates track the oracle for 200 iterations, and
+    the binary32 solve reaches the binary64 objective."""
+    inst = mid_gam(1, L=L, n=n, m=min(400, n // 2))
     run = Oracle(inst).run(OracleParams())
     done = 0
     with Solver(inst, tiling=4) as s:
