@@ -45,6 +45,7 @@ struct spfom_ctx {
   unsigned long long fallback_host = 0;
   bool polishing = false;  // precision 32: binary64 iterations after the first converged evaluation
   cudaGraphExec_t period[2] = {nullptr, nullptr};  // one evaluation period, [binary64, binary32 pass]
+  bool period_stale[2] = {false, false};           // its launches name buffers or values that changed
   bool period_failed = false;                      // capture unavailable on this stream
   cudaGraphExec_t loop[2] = {nullptr, nullptr};    // device loop over periods (params.device_loop)
   spfom::DevLoop* d_loop = nullptr;                // its state (device, per loaded instance)
@@ -86,12 +87,12 @@ spfom_status cuda_fail(spfom_ctx* ctx, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);     \
   } while (0)
 
+// The period graphs are kept but marked stale: the next capture updates them
+// in place (cheaper than a new instantiation when the kernels are the same,
+// as after a reload of an instance of the same shape); the loop graphs go.
 void drop_graphs(spfom_ctx* ctx) {
-  for (auto& g : ctx->period)
-    if (g) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
+  for (int k = 0; k < 2; ++k)
+    if (ctx->period[k]) ctx->period_stale[k] = true;
   for (auto& g : ctx->loop)
     if (g) {
       cudaGraphExecDestroy(g);
@@ -526,6 +527,11 @@ void spfom_destroy(spfom_ctx* ctx) {
   if (!ctx) return;
   cudaSetDevice(ctx->p.device);
   free_instance(ctx);
+  for (auto& g : ctx->period)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);  // its allocations are freed and the stream synchronized
   if (ctx->warm_buf) cudaFree(ctx->warm_buf);
   if (ctx->d_state) cudaFree(ctx->d_state);
@@ -931,11 +937,14 @@ namespace {
 // Capture one evaluation period (eval_every iterations, then the evaluation)
 // on the ctx stream into an executable graph. Returns null when the stream
 // cannot be captured (the caller then launches directly).
-cudaGraphExec_t capture_period(spfom_ctx* ctx) {
+// `old` (a stale executable graph of an earlier capture, or null) is updated
+// in place from the new capture when the update is possible, else destroyed.
+cudaGraphExec_t capture_period(spfom_ctx* ctx, cudaGraphExec_t old) {
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
   if (cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
     cudaGetLastError();
+    if (old) cudaGraphExecDestroy(old);
     return nullptr;
   }
   bool ok = true;
@@ -943,10 +952,19 @@ cudaGraphExec_t capture_period(spfom_ctx* ctx) {
     ok = spfom::launch_iteration(ctx->P, ctx->W, ctx->cfg, ctx->stream) == cudaSuccess;
   if (ok) ok = spfom::launch_eval(ctx->P, ctx->W, ctx->cfg, ctx->stream) == cudaSuccess;
   if (cudaStreamEndCapture(ctx->stream, &g) != cudaSuccess || !ok) ok = false;
-  if (ok && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+  if (ok && old) {
+    cudaGraphExecUpdateResultInfo info{};
+    if (cudaGraphExecUpdate(old, g, &info) == cudaSuccess) {
+      ex = old;
+      old = nullptr;
+    }
+    cudaGetLastError();
+  }
+  if (ok && !ex && cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
     ok = false;
     ex = nullptr;
   }
+  if (old) cudaGraphExecDestroy(old);
   if (g) cudaGraphDestroy(g);
   cudaGetLastError();
   return ok ? ex : nullptr;
@@ -1014,8 +1032,12 @@ spfom_status spfom_step(spfom_ctx* ctx, int64_t iters, spfom_stats* out) {
   long long t = ctx->host_t, launches = 0;
   for (int64_t k = 0; k < iters;) {
     if (graphs && t % E == 0 && iters - k >= E && !ctx->period_failed) {
-      cudaGraphExec_t& ex = ctx->period[ctx->cfg.f32 ? 1 : 0];
-      if (!ex) ex = capture_period(ctx);
+      const int pk = ctx->cfg.f32 ? 1 : 0;
+      cudaGraphExec_t& ex = ctx->period[pk];
+      if (!ex || ctx->period_stale[pk]) {
+        ex = capture_period(ctx, ex);
+        ctx->period_stale[pk] = false;
+      }
       if (ex) {
         SPFOM_CUDA(ctx, cudaGraphLaunch(ex, ctx->stream));
         launches += E * per_iter + spfom::kernel_launches_per_eval();
