@@ -45,7 +45,11 @@ struct spfom_ctx {
   unsigned long long fallback_host = 0;
   bool polishing = false;  // precision 32: binary64 iterations after the first converged evaluation
   cudaGraphExec_t period[2] = {nullptr, nullptr};  // one evaluation period, [binary64, binary32 pass]
-  bool period_stale[2] = {false, false};           // its launches name buffers or values that changed
+  bool period_stale[2] = {false, false};           // its launches may name buffers or values that changed
+  Problem period_P[2]{};                           // the problem, work and configuration it was captured
+  Work period_W[2]{};                              // with: identical ones (a reload of the same instance
+  RunConfig period_cfg[2]{};                       // into the same pool blocks) make it valid again as it is
+  long long period_E[2] = {0, 0};
   bool period_failed = false;                      // capture unavailable on this stream
   cudaGraphExec_t loop[2] = {nullptr, nullptr};    // device loop over periods (params.device_loop)
   spfom::DevLoop* d_loop = nullptr;                // its state (device, per loaded instance)
@@ -1034,9 +1038,20 @@ spfom_status spfom_step(spfom_ctx* ctx, int64_t iters, spfom_stats* out) {
     if (graphs && t % E == 0 && iters - k >= E && !ctx->period_failed) {
       const int pk = ctx->cfg.f32 ? 1 : 0;
       cudaGraphExec_t& ex = ctx->period[pk];
+      if (ex && ctx->period_stale[pk] && ctx->period_E[pk] == E &&
+          std::memcmp(&ctx->period_P[pk], &ctx->P, sizeof(Problem)) == 0 &&
+          std::memcmp(&ctx->period_W[pk], &ctx->W, sizeof(Work)) == 0 &&
+          std::memcmp(&ctx->period_cfg[pk], &ctx->cfg, sizeof(RunConfig)) == 0)
+        ctx->period_stale[pk] = false;  // every captured launch would be the same
       if (!ex || ctx->period_stale[pk]) {
         ex = capture_period(ctx, ex);
         ctx->period_stale[pk] = false;
+        if (ex) {
+          std::memcpy(&ctx->period_P[pk], &ctx->P, sizeof(Problem));
+          std::memcpy(&ctx->period_W[pk], &ctx->W, sizeof(Work));
+          std::memcpy(&ctx->period_cfg[pk], &ctx->cfg, sizeof(RunConfig));
+          ctx->period_E[pk] = E;
+        }
       }
       if (ex) {
         SPFOM_CUDA(ctx, cudaGraphLaunch(ex, ctx->stream));
