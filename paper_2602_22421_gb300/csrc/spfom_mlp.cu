@@ -157,6 +157,12 @@ struct Epi {
   int ld16t;
   int zpad;                      // rows M..zpad-1 of out16t are written as zeros (K padding of later products)
   int staged;                    // BN = 256: out16 / out16t leave through shared memory by tensor stores
+  // staged tiles only: dotout[r * lddot] = dotb[0] + sum_c bf16(C[r][c]) dotw[c] (the next layer
+  // when it is one output: its product need not read C back), or null
+  const __nv_bfloat16* dotw;
+  const float* dotb;
+  float* dotout;
+  int lddot;
   int* error;                    // set to 1 when a wait gives up
   unsigned wait_limit;           // polls of the producer's waits before they give up
 };
@@ -315,6 +321,8 @@ __global__ void __launch_bounds__(gemm_threads<BN, ST>(), gemm_threads<BN, ST>()
     // has its own buffer.
     constexpr int kGroups = BN / 64 / kHalves;
     const int lead = half * kThreads;
+    __shared__ float dot_half[kThreads];  // the second column half's part of the row's dot product
+    float dot = 0.f;
     const uint32_t bar = 1u + (uint32_t)half;
 #pragma unroll 1
     for (int gi = 0; gi < kGroups; ++gi) {
@@ -382,6 +390,16 @@ __global__ void __launch_bounds__(gemm_threads<BN, ST>(), gemm_threads<BN, ST>()
             const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
             h[i] = *reinterpret_cast<const uint32_t*>(&p2);
           }
+          if (E.dotout) {  // the rounded outputs against the next layer's BF16 weights
+            const uint4* wp = reinterpret_cast<const uint4*>(E.dotw + c0);
+            const uint4 wa = __ldg(wp), wb = __ldg(wp + 1);
+            const uint32_t w[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              dot = fmaf(__uint_as_float(h[i] << 16), __uint_as_float(w[i] << 16), dot);
+              dot = fmaf(__uint_as_float(h[i] & 0xFFFF0000u), __uint_as_float(w[i] & 0xFFFF0000u), dot);
+            }
+          }
           if (E.out16) {
 #pragma unroll
             for (int u = 0; u < 2; ++u) {
@@ -406,8 +424,11 @@ __global__ void __launch_bounds__(gemm_threads<BN, ST>(), gemm_threads<BN, ST>()
       }
     }
     if (threadIdx.x == lead) bulk_wait_read0();
+    if (E.dotout && kHalves == 2 && half == 1) dot_half[rl] = dot;
     tc_fence_before();
     __syncthreads();
+    if (E.dotout && half == 0 && row_ok)
+      E.dotout[(size_t)row * E.lddot] = (dot + (kHalves == 2 ? dot_half[rl] : 0.f)) + E.dotb[0];
     if (warp == 0) {
       tc_fence_after();
       tmem_dealloc(tmem, S::kCols);
@@ -685,7 +706,7 @@ long long round64(long long x) { return (x + 63) / 64 * 64; }
 // 16 (N <= 16) or 256 rows. splits > 1 splits K; the partial tiles then go to
 // E.out32 as [splits][M][ld32] and *splits_used (or NULL) gets their count.
 cudaError_t gemm_tn(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* B, long long ldb, int M, int N, int K,
-                    int splits, Epi E, cudaStream_t s, int* splits_used = nullptr) {
+                    int splits, Epi E, cudaStream_t s, int* splits_used = nullptr, int* staged_out = nullptr) {
   CUtensorMap ta, tb;
   const int bn = N <= 16 ? 16 : 256;
   const long long kcols = round64(K);
@@ -711,8 +732,11 @@ cudaError_t gemm_tn(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* 
     if (ok && E.out16t) ok = zp <= E.ld16t && make_map_t(&tt, E.out16t, N, zp, E.ld16t);
     if (ok && E.mask) ok = (E.ldmask & 7) == 0 && ((uintptr_t)E.mask & 15) == 0;
     if (ok && E.bias) ok = ((uintptr_t)E.bias & 15) == 0;
+    if (ok && E.dotout) ok = ((uintptr_t)E.dotw & 15) == 0;
     E.staged = ok ? 1 : 0;
   }
+  if (!E.staged) E.dotout = nullptr;  // only the staged epilogue forms the dot product
+  if (staged_out) *staged_out = E.staged;
   dim3 grid((M + kBM - 1) / kBM, splits);
   if (bn == 16) {
     k_gemm_tn<16, 4><<<grid, gemm_threads<16, 4>(), GemmShape<16, 4>::kSmem, s>>>(ta, tb, tr, tt, K, E);
@@ -872,8 +896,14 @@ cudaError_t forward_rows(spfom_mlp* n, long long rows, bool keep, cudaStream_t s
   E.bias = n->p + spfom::mlp::kOffB2;
   E.out16 = n->h2;
   E.out16t = keep ? n->h2t : nullptr;
-  e = gemm_tn(n->h1, H, n->w2, H, (int)rows, H, H, 1, E, s);
-  if (e != cudaSuccess) return e;
+  // the output layer (one unit) as the hidden product's epilogue: o = b3 + bf16(h2) . bf16(w3)
+  E.dotw = n->w3p;  // row 0 of the padded output weights
+  E.dotb = n->b3p;
+  E.dotout = n->o16;
+  E.lddot = 16;
+  int staged = 0;
+  e = gemm_tn(n->h1, H, n->w2, H, (int)rows, H, H, 1, E, s, nullptr, &staged);
+  if (e != cudaSuccess || staged) return e;
   Epi O = epi(n);
   O.bias = n->b3p;
   O.out32 = n->o16;
