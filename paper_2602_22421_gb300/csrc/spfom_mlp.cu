@@ -163,6 +163,11 @@ struct Epi {
   const float* dotb;
   float* dotout;
   int lddot;
+  // staged tiles only (N = 256): outbits[r * 8 + c / 32] bit c % 32 = (BF16 output > 0), the
+  // ReLU mask a later product reads in place of the outputs; maskbits: such a mask, used in
+  // place of `mask`
+  uint32_t* outbits;
+  const uint32_t* maskbits;
   int* error;                    // set to 1 when a wait gives up
   unsigned wait_limit;           // polls of the producer's waits before they give up
 };
@@ -341,7 +346,10 @@ __global__ void __launch_bounds__(gemm_threads<BN, ST>(), gemm_threads<BN, ST>()
         const int cs = g * 64 + sub * 32;
         // the mask's 32 columns in flight with the accumulator load
         uint4 mk[4];
-        const bool masked = E.mask != nullptr && row_ok;
+        const bool mbits = E.maskbits != nullptr && row_ok;
+        const bool masked = !mbits && E.mask != nullptr && row_ok;
+        const uint32_t mword = mbits ? __ldg(E.maskbits + (size_t)row * 8 + (cs >> 5)) : 0u;
+        uint32_t oword = 0u;
         if (masked) {
           const uint4* mp = reinterpret_cast<const uint4*>(E.mask + (size_t)row * E.ldmask + cs);
 #pragma unroll
@@ -383,12 +391,24 @@ __global__ void __launch_bounds__(gemm_threads<BN, ST>(), gemm_threads<BN, ST>()
               for (int i = 0; i < 16; ++i)  // BF16 > 0 iff its bits as a signed 16-bit integer are
                 if ((short)(uint16_t)(w[i >> 1] >> (16 * (i & 1))) <= 0) v[i] = 0.f;
             }
+            if (mbits) {
+#pragma unroll
+              for (int i = 0; i < 16; ++i)
+                if (!((mword >> (qq * 16 + i)) & 1u)) v[i] = 0.f;
+            }
           }
           uint32_t h[8];  // BF16 pairs (column 2i in the low half)
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
             const __nv_bfloat162 p2 = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
             h[i] = *reinterpret_cast<const uint32_t*>(&p2);
+          }
+          if (E.outbits) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              oword |= (uint32_t)((short)(uint16_t)(h[i] & 0xFFFFu) > 0) << (qq * 16 + 2 * i);
+              oword |= (uint32_t)((short)(uint16_t)(h[i] >> 16) > 0) << (qq * 16 + 2 * i + 1);
+            }
           }
           if (E.dotout) {  // the rounded outputs against the next layer's BF16 weights
             const uint4* wp = reinterpret_cast<const uint4*>(E.dotw + c0);
@@ -414,6 +434,7 @@ __global__ void __launch_bounds__(gemm_threads<BN, ST>(), gemm_threads<BN, ST>()
             for (int i = 0; i < 16; ++i) t[i * kBM] = (uint16_t)(h[i >> 1] >> (16 * (i & 1)));
           }
         }
+        if (E.outbits && row_ok) E.outbits[(size_t)row * 8 + (cs >> 5)] = oword;
       }
       fence_async_smem();
       named_bar(bar, kThreads);
@@ -735,7 +756,11 @@ cudaError_t gemm_tn(const __nv_bfloat16* A, long long lda, const __nv_bfloat16* 
     if (ok && E.dotout) ok = ((uintptr_t)E.dotw & 15) == 0;
     E.staged = ok ? 1 : 0;
   }
-  if (!E.staged) E.dotout = nullptr;  // only the staged epilogue forms the dot product
+  if (!E.staged) {  // only the staged epilogue forms the dot product and the bit masks
+    E.dotout = nullptr;
+    E.outbits = nullptr;
+    E.maskbits = nullptr;
+  }
   if (staged_out) *staged_out = E.staged;
   dim3 grid((M + kBM - 1) / kBM, splits);
   if (bn == 16) {
@@ -783,6 +808,8 @@ struct spfom_mlp {
   std::vector<void*> ws;
   __nv_bfloat16 *xb = nullptr, *xt = nullptr, *h1 = nullptr, *h1t = nullptr, *h2 = nullptr, *h2t = nullptr,
                 *d16 = nullptr, *d16t = nullptr, *dh2 = nullptr, *dh2t = nullptr, *dh1t = nullptr;
+  uint32_t *h1bits = nullptr, *h2bits = nullptr;  // ReLU masks of h1, h2 (8 words per row)
+  bool bits_ok = false;                           // the last forward pass with keep wrote them
   float* o16 = nullptr;
   float* part = nullptr;  // split-K partial tiles
   double* lpart = nullptr;
@@ -824,6 +851,8 @@ cudaError_t ensure_rows(spfom_mlp* n, long long rows) {
   A(&n->xt, (size_t)R * 16);
   A(&n->h1, (size_t)R * H);
   A(&n->h1t, (size_t)R * H);
+  A(&n->h1bits, (size_t)R * 8);
+  A(&n->h2bits, (size_t)R * 8);
   A(&n->h2, (size_t)R * H);
   A(&n->h2t, (size_t)R * H);
   A(&n->d16, (size_t)R * KP);
@@ -891,11 +920,14 @@ cudaError_t forward_rows(spfom_mlp* n, long long rows, bool keep, cudaStream_t s
   E.out16t = keep ? n->h1t : nullptr;
   E.ld16t = (int)ldt;
   E.zpad = (int)spfom::mlp::round64(rows);
-  cudaError_t e = gemm_tn(n->xb, KP, n->w1, KP, (int)rows, H, SPFOM_MLP_FEATURES, 1, E, s);
+  E.outbits = keep ? n->h1bits : nullptr;
+  int staged1 = 0;
+  cudaError_t e = gemm_tn(n->xb, KP, n->w1, KP, (int)rows, H, SPFOM_MLP_FEATURES, 1, E, s, nullptr, &staged1);
   if (e != cudaSuccess) return e;
   E.bias = n->p + spfom::mlp::kOffB2;
   E.out16 = n->h2;
   E.out16t = keep ? n->h2t : nullptr;
+  E.outbits = keep ? n->h2bits : nullptr;
   // the output layer (one unit) as the hidden product's epilogue: o = b3 + bf16(h2) . bf16(w3)
   E.dotw = n->w3p;  // row 0 of the padded output weights
   E.dotb = n->b3p;
@@ -903,6 +935,7 @@ cudaError_t forward_rows(spfom_mlp* n, long long rows, bool keep, cudaStream_t s
   E.lddot = 16;
   int staged = 0;
   e = gemm_tn(n->h1, H, n->w2, H, (int)rows, H, H, 1, E, s, nullptr, &staged);
+  n->bits_ok = keep && staged1 && staged;
   if (e != cudaSuccess || staged) return e;
   Epi O = epi(n);
   O.bias = n->b3p;
@@ -1100,6 +1133,7 @@ spfom_status spfom_mlp_loss_grad(spfom_mlp* n, const float* x, const float* t, i
   {
     Epi E = epi(n);
     E.mask = n->h2;
+    E.maskbits = n->bits_ok ? n->h2bits : nullptr;
     E.ldmask = H;
     E.out16 = n->dh2;
     E.ld16 = H;
@@ -1115,6 +1149,7 @@ spfom_status spfom_mlp_loss_grad(spfom_mlp* n, const float* x, const float* t, i
   {
     Epi E = epi(n);
     E.mask = n->h1;
+    E.maskbits = n->bits_ok ? n->h1bits : nullptr;
     E.ldmask = H;
     E.out16t = n->dh1t;
     E.ld16t = (int)ldt;
