@@ -11,15 +11,20 @@
 // product that makes the matrix (a transposed BF16 copy), so no separate
 // transpose runs.
 //
-// One CTA of 128 threads computes a 128 x BN tile (BN = 16 or 256); thread 0
-// issues the TMA loads of a 4-stage ring and the MMAs (K = 16 per instruction),
-// tcgen05.commit releases each stage back to the loads, and a final commit
-// signals the four warps, which read the accumulator rows of their 32 TMEM
-// lanes and apply the epilogue (bias, ReLU, ReLU-backward mask, FP32 and BF16
-// stores, transposed BF16 store). Products with a long K (the weight
-// gradients, K = rows) split K over grid.y and sum the partial tiles in a
-// fixed order. Every wait is bounded; a wait that gives up sets the network's
-// error flag, and the host reports SPFOM_ETIMEOUT.
+// One CTA computes a 128 x BN tile (BN = 16 or 256); thread 0 issues the TMA
+// loads of a ring of 2 (the 256-wide row tiles, two CTAs per SM) or 4 stages
+// and the MMAs (K = 16 per instruction), tcgen05.commit releases each stage
+// back to the loads, and a final commit signals the epilogue warps, which read
+// the accumulator rows of their TMEM lane quarter. The 256-wide row tiles run
+// eight warps (two per lane quarter, one per column half) and send their BF16
+// outputs through shared memory with tensor stores; their epilogue also forms
+// the output layer's dot product (the hidden layer) and one ReLU-mask bit per
+// output, which the masked backward products read instead of the outputs.
+// Products with a long K (the weight gradients, K = rows) split K over grid.y
+// and sum the partial tiles in a fixed order; the output layer's weight
+// gradient is a weighted column sum of the row-major hidden activations. Every
+// wait is bounded; a wait that gives up sets the network's error flag, and the
+// host reports SPFOM_ETIMEOUT.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -635,6 +640,37 @@ __global__ void k_bias_partial(const __nv_bfloat16* __restrict__ dt, long long l
   if (threadIdx.x == 0) part[(size_t)c * S + blockIdx.x] = (float)tot;
 }
 
+// Output-weight gradient from the row-major activations: block b sums the
+// rows [b per, (b + 1) per) of h [rows][256] (BF16, leading dimension ldh),
+// each weighted by d[r * ldd] (the BF16 output gradient), into
+// part[c * S + b]. A thread holds 8 columns of one row in 8 (FP32, in row
+// order), the block's 8 row groups are added in order in binary64.
+__global__ void __launch_bounds__(256) k_col_wsum(const __nv_bfloat16* __restrict__ h, long long ldh,
+                                                  const __nv_bfloat16* __restrict__ d, long long ldd, long long rows,
+                                                  long long per, float* __restrict__ part) {
+  __shared__ float sh[8][256];
+  const int cg = threadIdx.x & 31, rg = threadIdx.x >> 5;
+  const long long r0 = (long long)blockIdx.x * per, r1 = min(rows, r0 + per);
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  for (long long r = r0 + rg; r < r1; r += 8) {
+    const float dr = __uint_as_float((uint32_t)__bfloat16_as_ushort(d[r * ldd]) << 16);
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(h + r * ldh) + cg);
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc[2 * k] = fmaf(__uint_as_float(w[k] << 16), dr, acc[2 * k]);
+      acc[2 * k + 1] = fmaf(__uint_as_float(w[k] & 0xFFFF0000u), dr, acc[2 * k + 1]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) sh[rg][cg * 8 + k] = acc[k];
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int g = 0; g < 8; ++g) s += (double)sh[g][threadIdx.x];
+  part[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = (float)s;
+}
+
 // Second: g[c] = the column's S partial sums, one warp per column (lane k
 // adds the partials k, k + 32, ... in order, then a fixed shuffle tree).
 __global__ void k_bias_finish(const float* __restrict__ part, int S, int C, float* __restrict__ g) {
@@ -646,13 +682,11 @@ __global__ void k_bias_finish(const float* __restrict__ part, int S, int C, floa
   if (lane == 0) g[c] = (float)s;
 }
 
-// Split-K partial tiles [splits][M][N] -> g (optionally only column 0, strided).
-__global__ void k_splitk_sum(const float* __restrict__ part, int splits, int M, int N, float* __restrict__ g,
-                             int col0_only) {
+// Split-K partial tiles [splits][M][N] -> g [M][N].
+__global__ void k_splitk_sum(const float* __restrict__ part, int splits, int M, int N, float* __restrict__ g) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int cols = col0_only ? 1 : N;
-  if (i >= M * cols) return;
-  const int r = i / cols, c = col0_only ? 0 : i % cols;
+  if (i >= M * N) return;
+  const int r = i / N, c = i % N;
   float s = 0.f;
 #pragma unroll 8
   for (int k = 0; k < splits; ++k) s += __ldg(part + (size_t)k * M * N + (size_t)r * N + c);
@@ -806,7 +840,7 @@ struct spfom_mlp {
   // workspaces for `cap` rows
   long long cap = 0;
   std::vector<void*> ws;
-  __nv_bfloat16 *xb = nullptr, *xt = nullptr, *h1 = nullptr, *h1t = nullptr, *h2 = nullptr, *h2t = nullptr,
+  __nv_bfloat16 *xb = nullptr, *xt = nullptr, *h1 = nullptr, *h1t = nullptr, *h2 = nullptr,
                 *d16 = nullptr, *d16t = nullptr, *dh2 = nullptr, *dh2t = nullptr, *dh1t = nullptr;
   uint32_t *h1bits = nullptr, *h2bits = nullptr;  // ReLU masks of h1, h2 (8 words per row)
   bool bits_ok = false;                           // the last forward pass with keep wrote them
@@ -854,7 +888,6 @@ cudaError_t ensure_rows(spfom_mlp* n, long long rows) {
   A(&n->h1bits, (size_t)R * 8);
   A(&n->h2bits, (size_t)R * 8);
   A(&n->h2, (size_t)R * H);
-  A(&n->h2t, (size_t)R * H);
   A(&n->d16, (size_t)R * KP);
   A(&n->d16t, (size_t)R * 16);
   A(&n->dh2, (size_t)R * H);
@@ -926,7 +959,7 @@ cudaError_t forward_rows(spfom_mlp* n, long long rows, bool keep, cudaStream_t s
   if (e != cudaSuccess) return e;
   E.bias = n->p + spfom::mlp::kOffB2;
   E.out16 = n->h2;
-  E.out16t = keep ? n->h2t : nullptr;
+  E.out16t = nullptr;  // the output-weight gradient reads h2 row-major
   E.outbits = keep ? n->h2bits : nullptr;
   // the output layer (one unit) as the hidden product's epilogue: o = b3 + bf16(h2) . bf16(w3)
   E.dotw = n->w3p;  // row 0 of the padded output weights
@@ -961,9 +994,9 @@ spfom_status check_error(spfom_mlp* n, cudaStream_t s) {
 }
 
 // Weight gradient g = (d^T a) for d^T [256][ldt], a^T [N][ldt] over `rows`
-// rows (split K, fixed-order sum); col0 keeps only column 0 (N = 16 padded).
+// rows (split K, fixed-order sum).
 cudaError_t weight_grad(spfom_mlp* n, const __nv_bfloat16* dt, const __nv_bfloat16* at, int N, long long rows,
-                        float* g, bool col0, cudaStream_t s) {
+                        float* g, cudaStream_t s) {
   const int H = SPFOM_MLP_HIDDEN;
   Epi E = epi(n);
   E.out32 = n->part;
@@ -971,8 +1004,7 @@ cudaError_t weight_grad(spfom_mlp* n, const __nv_bfloat16* dt, const __nv_bfloat
   int used = 1;
   cudaError_t e = spfom::mlp::gemm_tn(dt, n->cap, at, n->cap, H, N, (int)rows, splits_for(rows, 2), E, s, &used);
   if (e != cudaSuccess) return e;
-  const int outs = col0 ? H : H * N;
-  spfom::mlp::k_splitk_sum<<<(outs + 255) / 256, 256, 0, s>>>(n->part, used, H, N, g, col0 ? 1 : 0);
+  spfom::mlp::k_splitk_sum<<<(H * N + 255) / 256, 256, 0, s>>>(n->part, used, H, N, g);
   return cudaGetLastError();
 }
 
@@ -989,6 +1021,20 @@ cudaError_t bias_grad(spfom_mlp* n, const __nv_bfloat16* dt, int C, long long ro
   S = (rows8 + per - 1) / per;
   spfom::mlp::k_bias_partial<<<dim3((unsigned)S, (unsigned)C), 256, 0, s>>>(dt, n->cap, rows8, per, n->part);
   spfom::mlp::k_bias_finish<<<(C * 32 + 255) / 256, 256, 0, s>>>(n->part, (int)S, C, g);
+  return cudaGetLastError();
+}
+
+// dw3 = h2^T dO over `rows` rows from the row-major h2 and the output gradient
+// (column 0 of d16): partial sums per block, then one warp per column.
+cudaError_t out_weight_grad(spfom_mlp* n, long long rows, float* g, cudaStream_t s) {
+  const int H = SPFOM_MLP_HIDDEN;
+  long long S = (rows + 255) / 256;
+  if (S > 4 * 152) S = 4 * 152;
+  if (S < 1) S = 1;
+  const long long per = (rows + S - 1) / S;
+  S = (rows + per - 1) / per;
+  spfom::mlp::k_col_wsum<<<(unsigned)S, 256, 0, s>>>(n->h2, H, n->d16, spfom::mlp::kKPad, rows, per, n->part);
+  spfom::mlp::k_bias_finish<<<(H * 32 + 255) / 256, 256, 0, s>>>(n->part, (int)S, H, g);
   return cudaGetLastError();
 }
 
@@ -1126,8 +1172,8 @@ spfom_status spfom_mlp_loss_grad(spfom_mlp* n, const float* x, const float* t, i
   spfom::mlp::k_loss_finish<<<1, 256, 0, s>>>(n->lpart, lb, rows, n->d_loss);
   MLP_TRY(cudaGetLastError());
   float* g = n->g;
-  // output layer: dw3 = h2^T dO (a [256][16] product, column 0), db3 = sum dO
-  MLP_TRY(weight_grad(n, n->h2t, n->d16t, 16, rows, g + spfom::mlp::kOffW3, true, s));
+  // output layer: dw3 = h2^T dO (a weighted column sum of h2), db3 = sum dO
+  MLP_TRY(out_weight_grad(n, rows, g + spfom::mlp::kOffW3, s));
   MLP_TRY(bias_grad(n, n->d16t, 1, rows, g + spfom::mlp::kOffB3, s));
   // dH2 = (dO w3^T) masked by h2 > 0
   {
@@ -1143,7 +1189,7 @@ spfom_status spfom_mlp_loss_grad(spfom_mlp* n, const float* x, const float* t, i
     MLP_TRY(gemm_tn(n->d16, KP, n->w3pt, KP, (int)rows, H, 16, 1, E, s));
   }
   // dW2 = dH2^T h1, db2 = sum dH2
-  MLP_TRY(weight_grad(n, n->dh2t, n->h1t, H, rows, g + spfom::mlp::kOffW2, false, s));
+  MLP_TRY(weight_grad(n, n->dh2t, n->h1t, H, rows, g + spfom::mlp::kOffW2, s));
   MLP_TRY(bias_grad(n, n->dh2t, H, rows, g + spfom::mlp::kOffB2, s));
   // dH1 = (dH2 W2) masked by h1 > 0 (transposed copy only)
   {
@@ -1157,7 +1203,7 @@ spfom_status spfom_mlp_loss_grad(spfom_mlp* n, const float* x, const float* t, i
     MLP_TRY(gemm_tn(n->dh2, H, n->w2t, H, (int)rows, H, H, 1, E, s));
   }
   // dW1 = dH1^T x, db1 = sum dH1
-  MLP_TRY(weight_grad(n, n->dh1t, n->xt, 16, rows, g + spfom::mlp::kOffW1, false, s));
+  MLP_TRY(weight_grad(n, n->dh1t, n->xt, 16, rows, g + spfom::mlp::kOffW1, s));
   MLP_TRY(bias_grad(n, n->dh1t, H, rows, g + spfom::mlp::kOffB1, s));
   MLP_TRY(cudaGetLastError());
   if (loss) MLP_TRY(cudaMemcpyAsync(loss, n->d_loss, sizeof(double), cudaMemcpyDeviceToHost, s));
