@@ -852,7 +852,7 @@ struct spfom_mlp {
 
 namespace {
 
-constexpr int kMaxSplits = 64;
+constexpr int kMaxSplits = 76;  // 2 x 76 = 152 CTAs for the 256-row weight gradients: one per SM
 
 void free_ws(spfom_mlp* n) {
   for (void* q : n->ws) cudaFree(q);
